@@ -1,0 +1,481 @@
+/*
+ * FP64 CPU oracle for the Cartesian-grid Active Flux method with AMR
+ * (Calhoun, Chudzik, Helzel, "The Cartesian Grid Active Flux Method with
+ * Adaptive Mesh Refinement", arXiv 2205.07572).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; the two meet only in the
+ * documented state layout.
+ *
+ * Everything is written in the order and notation of the paper, slow and
+ * plain: one node at a time, one face at a time, one cell at a time.
+ *
+ * State layout (the library's interface contract): per patch, per component,
+ * four planes (0 = cell average Q_{i,j}, 1 = left-edge midpoint Q_{i-1/2,j},
+ * 2 = lower-left corner Q_{i-1/2,j-1/2}, 3 = bottom-edge midpoint
+ * Q_{i,j-1/2}; Section 2, Fig. 1), each a (N+2g+1)^2 row-major lattice padded
+ * to a multiple of 8 entries, g = 2 ghost layers (Section 3.2).
+ *
+ * Parity status of each function is stated next to it; the pins live in
+ * tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NG 2 /* ghost layers (Section 3.2, "two layers of ghost cells") */
+
+enum { PL_AVG = 0, PL_XMID = 1, PL_CORNER = 2, PL_YMID = 3 };
+enum { EQ_ADVECTION = 0, EQ_ACOUSTICS = 1 };
+enum { ND_CORNER = 0, ND_XMID = 1, ND_YMID = 2 };
+
+typedef struct {
+    int32_t eq;     /* EQ_ADVECTION or EQ_ACOUSTICS */
+    int32_t n;      /* interior cells per patch side */
+    int32_t ncomp;  /* 1 or 3 */
+    int32_t pad_;
+    double dx, dy, dt;
+    double a, b;    /* advection velocity (Eq. advection2d) */
+    double c;       /* speed of sound (Eq. acoustics) */
+} orc_cfg;
+
+typedef struct {
+    int n, w;
+    long plane;
+    int ncomp;
+} lay_t;
+
+static lay_t lay_make(int n, int ncomp) {
+    lay_t L;
+    L.n = n;
+    L.w = n + 2 * NG + 1;
+    L.plane = ((long)L.w * L.w + 7) / 8 * 8;
+    L.ncomp = ncomp;
+    return L;
+}
+
+static long lay_patch_words(const lay_t *L) { return (long)L->ncomp * 4 * L->plane; }
+
+/* Lattice offset of cell / node-line index (i, j), i, j in [-g, N+g]. */
+static long IX(const lay_t *L, int i, int j) { return (long)(j + NG) * L->w + (i + NG); }
+
+static const double *PLc(const lay_t *L, const double *patch, int comp, int plane) {
+    return patch + ((long)comp * 4 + plane) * L->plane;
+}
+static double *PL(const lay_t *L, double *patch, int comp, int plane) {
+    return patch + ((long)comp * 4 + plane) * L->plane;
+}
+
+long orc_plane_stride(int n) { lay_t L = lay_make(n, 1); return L.plane; }
+
+/* ------------------------------------------------------------------ Eq. poly
+ * Reconstruction on the reference cell [-1,1]^2 (Section 2, Eq. poly).  The
+ * biquadratic space spanned by the nine monomials of Eq. poly is written in
+ * the tensor Lagrange basis on the nodes {-1,0,1}^2.  Eight nodal values are
+ * the point values on the cell boundary; the ninth (the centre) is fixed by
+ * requiring the cell average of the polynomial to equal Q_{i,j}.  The average
+ * of L_a(xi) L_b(eta) over the cell is w_a w_b with the Simpson weights
+ * w = (1/6, 2/3, 1/6), because Simpson's rule integrates quadratics exactly.
+ * Pinned by: biquadratics are reproduced exactly, average matches (P1).      */
+static const double SIMPSON_W[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+
+/* k-th Lagrange polynomial on nodes {-1,0,1} (k = 0,1,2), d-th derivative. */
+static double lag(int k, int d, double s) {
+    switch (k) {
+    case 0: return d == 0 ? 0.5 * s * (s - 1.0) : (d == 1 ? s - 0.5 : 1.0);
+    case 1: return d == 0 ? 1.0 - s * s : (d == 1 ? -2.0 * s : -2.0);
+    default: return d == 0 ? 0.5 * s * (s + 1.0) : (d == 1 ? s + 0.5 : 1.0);
+    }
+}
+
+/* Nodal values q[b][a] of cell (i, j) (a indexes xi = -1,0,1; b indexes eta). */
+static void cell_nodal(const lay_t *L, const double *patch, int comp, int i, int j, double q[3][3]) {
+    const double *avg = PLc(L, patch, comp, PL_AVG);
+    const double *xm = PLc(L, patch, comp, PL_XMID);
+    const double *co = PLc(L, patch, comp, PL_CORNER);
+    const double *ym = PLc(L, patch, comp, PL_YMID);
+    q[0][0] = co[IX(L, i, j)];
+    q[0][2] = co[IX(L, i + 1, j)];
+    q[2][0] = co[IX(L, i, j + 1)];
+    q[2][2] = co[IX(L, i + 1, j + 1)];
+    q[1][0] = xm[IX(L, i, j)];
+    q[1][2] = xm[IX(L, i + 1, j)];
+    q[0][1] = ym[IX(L, i, j)];
+    q[2][1] = ym[IX(L, i, j + 1)];
+    double rest = 0.0;
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a)
+            if (!(a == 1 && b == 1)) rest += SIMPSON_W[a] * SIMPSON_W[b] * q[b][a];
+    q[1][1] = (avg[IX(L, i, j)] - rest) / (SIMPSON_W[1] * SIMPSON_W[1]);
+}
+
+/* d^{mx}/dxi^{mx} d^{my}/deta^{my} of the reconstruction at (xi, eta). */
+static double recon_deriv(const double q[3][3], double xi, double eta, int mx, int my) {
+    double s = 0.0;
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) s += q[b][a] * lag(a, mx, xi) * lag(b, my, eta);
+    return s;
+}
+
+/* Exported for the pins: value (or derivative, in physical units) of the
+ * reconstruction of cell (i, j) of one patch at reference point (xi, eta). */
+double orc_recon_eval(int n, int ncomp, const double *patch, int comp, int i, int j,
+                      double xi, double eta, int mx, int my, double dx, double dy) {
+    lay_t L = lay_make(n, ncomp);
+    double q[3][3];
+    cell_nodal(&L, patch, comp, i, j, q);
+    return recon_deriv(q, xi, eta, mx, my) * pow(2.0 / dx, mx) * pow(2.0 / dy, my);
+}
+
+/* ------------------------------------------- Section 2.1, Eq. advection-update
+ * q(x, y, t + tau) = q(x - a tau, y - b tau, t): the point value at a node is
+ * the reconstruction q^n evaluated at the foot of the characteristic.  The
+ * foot is located relative to the node (in cell units) so the arithmetic does
+ * not depend on where the patch sits; with CFL <= 1 (Eq. cfl-adv) it lies in a
+ * cell adjacent to the node.  On a cell face either neighbour gives the same
+ * value because q^n is continuous.
+ * Pinned by: exact translation of polynomial data (P2, P3).                   */
+static double advect_node(const lay_t *L, const double *patch, int comp, const orc_cfg *cf,
+                          int type, int i, int j, double tau) {
+    /* node position in cell units relative to node line (i, j) */
+    double ox = (type == ND_YMID) ? 0.5 : 0.0;
+    double oy = (type == ND_XMID) ? 0.5 : 0.0;
+    double fx = ox - cf->a * tau / cf->dx; /* foot, relative to line i */
+    double fy = oy - cf->b * tau / cf->dy;
+    double kx = floor(fx), ky = floor(fy);
+    int ci = i + (int)kx, cj = j + (int)ky;
+    double xi = 2.0 * (fx - kx) - 1.0, eta = 2.0 * (fy - ky) - 1.0;
+    double q[3][3];
+    cell_nodal(L, patch, comp, ci, cj, q);
+    return recon_deriv(q, xi, eta, 0, 0);
+}
+
+/* ---------------------------------- Section 2.3, Eqs. ERFormula and sphe-mean
+ * p(t) = M_R{p} + R (d_R M_R{p} - M_R{div u}),
+ * u(t) = M_R{u} + R (d_R M_R{u} - M_R{grad p}),  R = c t,
+ * M_R{f}(x) = 1/(2 pi R) int_0^{2pi} int_0^R f(x + s(cos phi, sin phi))
+ *             s / sqrt(R^2 - s^2) ds dphi.
+ * With the time step restricted by Eq. cfl-acoustics the disc of radius R
+ * around a corner lies in the four cells sharing the corner (one quadrant
+ * each) and around an edge midpoint in the two cells sharing the edge (one
+ * half-plane each).  In each such sector the reconstruction is a polynomial;
+ * written in physical offsets (X, Y) from the node, f = sum t_mn X^m Y^n with
+ * Taylor coefficients t_mn (exact, m, n <= 2).  For one monomial
+ *   M_R{X^m Y^n}|_S = R^{m+n} J_{m+n+1} A_mn(S) / (2 pi),
+ *   J_k = int_0^1 t^k / sqrt(1 - t^2) dt,  A_mn(S) = int_S cos^m sin^n dphi,
+ * and R d_R of it is (m+n) times the same.  This is the exact evaluation the
+ * paper asks for ("the solution formula can be evaluated exactly").
+ * Pinned by: brute-force quadrature of Eq. sphe-mean (P4) and the exact wave
+ * solution for curl-free polynomial data (P5).                               */
+static double J_int(int k) {
+    double j0 = M_PI / 2.0, j1 = 1.0;
+    if (k == 0) return j0;
+    if (k == 1) return j1;
+    double jm2 = (k % 2 == 0) ? j0 : j1;
+    for (int s = (k % 2 == 0) ? 2 : 3; s <= k; s += 2) jm2 = jm2 * (double)(s - 1) / (double)s;
+    return jm2;
+}
+
+/* antiderivative of cos^m(phi) sin^n(phi), m, n in {0,1,2} */
+static double trig_prim(int m, int n, double f) {
+    double s = sin(f), c = cos(f);
+    switch (m * 3 + n) {
+    case 0: return f;
+    case 1: return -c;
+    case 2: return 0.5 * f - 0.25 * sin(2.0 * f);
+    case 3: return s;
+    case 4: return 0.5 * s * s;
+    case 5: return s * s * s / 3.0;
+    case 6: return 0.5 * f + 0.25 * sin(2.0 * f);
+    case 7: return -c * c * c / 3.0;
+    default: return f / 8.0 - sin(4.0 * f) / 32.0;
+    }
+}
+
+static double sector_A(int m, int n, double phi0, double phi1) {
+    return trig_prim(m, n, phi1) - trig_prim(m, n, phi0);
+}
+
+/* Taylor coefficients t[m][n] of the reconstruction of a cell about the
+ * reference point (xin, etan), in physical offsets. */
+static void taylor(const double q[3][3], double xin, double etan, double dx, double dy, double t[3][3]) {
+    static const double fact[3] = {1.0, 1.0, 2.0};
+    for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < 3; ++n)
+            t[m][n] = recon_deriv(q, xin, etan, m, n) * pow(2.0 / dx, m) * pow(2.0 / dy, n) /
+                      (fact[m] * fact[n]);
+}
+
+/* M_R and R d_R M_R of the polynomial sum t_mn X^m Y^n over one sector. */
+static void sector_mean(const double t[3][3], double R, double phi0, double phi1, double *M, double *RdM) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < 3; ++n) {
+            double mono = pow(R, m + n) * J_int(m + n + 1) * sector_A(m, n, phi0, phi1) / (2.0 * M_PI);
+            s0 += t[m][n] * mono;
+            s1 += (double)(m + n) * t[m][n] * mono;
+        }
+    *M = s0;
+    *RdM = s1;
+}
+
+typedef struct {
+    int di, dj;        /* cell offset from node line (i, j) */
+    double xin, etan;  /* node in that cell's reference coordinates */
+    double phi0, phi1; /* angular sector of the disc inside that cell */
+} sector_t;
+
+static int node_sectors(int type, sector_t s[4]) {
+    const double h = 0.5 * M_PI;
+    if (type == ND_CORNER) {
+        s[0] = (sector_t){0, 0, -1.0, -1.0, 0.0, h};
+        s[1] = (sector_t){-1, 0, 1.0, -1.0, h, 2.0 * h};
+        s[2] = (sector_t){-1, -1, 1.0, 1.0, 2.0 * h, 3.0 * h};
+        s[3] = (sector_t){0, -1, -1.0, 1.0, 3.0 * h, 4.0 * h};
+        return 4;
+    }
+    if (type == ND_XMID) {
+        s[0] = (sector_t){0, 0, -1.0, 0.0, -h, h};
+        s[1] = (sector_t){-1, 0, 1.0, 0.0, h, 3.0 * h};
+        return 2;
+    }
+    s[0] = (sector_t){0, 0, 0.0, -1.0, 0.0, 2.0 * h};
+    s[1] = (sector_t){0, -1, 0.0, 1.0, 2.0 * h, 4.0 * h};
+    return 2;
+}
+
+static void acoustic_node(const lay_t *L, const double *patch, const orc_cfg *cf, int type, int i, int j,
+                          double tau, double out[3]) {
+    double R = cf->c * tau;
+    sector_t sec[4];
+    int ns = node_sectors(type, sec);
+    double Mp = 0, RdMp = 0, Mu = 0, RdMu = 0, Mv = 0, RdMv = 0, Mdiv = 0, Mpx = 0, Mpy = 0;
+    for (int k = 0; k < ns; ++k) {
+        const sector_t *S = &sec[k];
+        double qp[3][3], qu[3][3], qv[3][3], tp[3][3], tu[3][3], tv[3][3];
+        cell_nodal(L, patch, 0, i + S->di, j + S->dj, qp);
+        cell_nodal(L, patch, 1, i + S->di, j + S->dj, qu);
+        cell_nodal(L, patch, 2, i + S->di, j + S->dj, qv);
+        taylor(qp, S->xin, S->etan, cf->dx, cf->dy, tp);
+        taylor(qu, S->xin, S->etan, cf->dx, cf->dy, tu);
+        taylor(qv, S->xin, S->etan, cf->dx, cf->dy, tv);
+        /* polynomial coefficients of div u = u_X + v_Y and of grad p */
+        double tdiv[3][3] = {{0}}, tpx[3][3] = {{0}}, tpy[3][3] = {{0}};
+        for (int m = 0; m < 3; ++m)
+            for (int n = 0; n < 3; ++n) {
+                double ux = (m + 1 < 3) ? (m + 1) * tu[m + 1][n] : 0.0;
+                double vy = (n + 1 < 3) ? (n + 1) * tv[m][n + 1] : 0.0;
+                tdiv[m][n] = ux + vy;
+                tpx[m][n] = (m + 1 < 3) ? (m + 1) * tp[m + 1][n] : 0.0;
+                tpy[m][n] = (n + 1 < 3) ? (n + 1) * tp[m][n + 1] : 0.0;
+            }
+        double M, RdM, dummy;
+        sector_mean(tp, R, S->phi0, S->phi1, &M, &RdM); Mp += M; RdMp += RdM;
+        sector_mean(tu, R, S->phi0, S->phi1, &M, &RdM); Mu += M; RdMu += RdM;
+        sector_mean(tv, R, S->phi0, S->phi1, &M, &RdM); Mv += M; RdMv += RdM;
+        sector_mean(tdiv, R, S->phi0, S->phi1, &M, &dummy); Mdiv += M;
+        sector_mean(tpx, R, S->phi0, S->phi1, &M, &dummy); Mpx += M;
+        sector_mean(tpy, R, S->phi0, S->phi1, &M, &dummy); Mpy += M;
+    }
+    /* Eq. ERFormula: M + R d_R M - R M{...} */
+    out[0] = Mp + RdMp - R * Mdiv;
+    out[1] = Mu + RdMu - R * Mpx;
+    out[2] = Mv + RdMv - R * Mpy;
+}
+
+/* Point value of node (type, i, j) of one patch evolved by tau. */
+static void evolve_node(const lay_t *L, const double *patch, const orc_cfg *cf, int type, int i, int j,
+                        double tau, double *out) {
+    if (cf->eq == EQ_ADVECTION) {
+        for (int c = 0; c < L->ncomp; ++c) out[c] = advect_node(L, patch, c, cf, type, i, j, tau);
+    } else {
+        acoustic_node(L, patch, cf, type, i, j, tau, out);
+    }
+}
+
+/* Exported for the pins. */
+void orc_node_evolve(const orc_cfg *cf, const double *patch, int type, int i, int j, double tau, double *out) {
+    lay_t L = lay_make(cf->n, cf->ncomp);
+    evolve_node(&L, patch, cf, type, i, j, tau, out);
+}
+
+/* Physical fluxes f(q), g(q): advection f = a q, g = b q (Eq. advection2d);
+ * acoustics for (p, u, v): f = c (u, p, 0), g = c (v, 0, p) (Eq. acoustics). */
+static void phys_flux(const orc_cfg *cf, int dir, const double *q, double *f) {
+    if (cf->eq == EQ_ADVECTION) {
+        for (int c = 0; c < cf->ncomp; ++c) f[c] = (dir == 0 ? cf->a : cf->b) * q[c];
+        return;
+    }
+    if (dir == 0) { f[0] = cf->c * q[1]; f[1] = cf->c * q[0]; f[2] = 0.0; }
+    else          { f[0] = cf->c * q[2]; f[1] = 0.0;         f[2] = cf->c * q[0]; }
+}
+
+/* ------------------------------------------------------------- one patch step
+ * One Active Flux step on one patch whose two ghost layers are filled
+ * (Section 2 and Section 3.2): the interior and the first ghost layer are
+ * advanced ("the first layer of ghost cells is updated along with all
+ * interior cells"), i.e. the averages of cells [-1, N+1)^2 and every point
+ * value on the boundary of those cells.
+ *   1. point values at t^{n+1/2} and t^{n+1} from q^n (Eq. advection-update /
+ *      Eq. ERFormula);
+ *   2. numerical fluxes by the space-time Simpson rule (Eq. Simpson-2d and
+ *      its analogue for G);
+ *   3. conservative update (Eq. 2dfv).
+ * `out` receives a copy of `in` with the updated entries replaced.  If freg is
+ * not NULL, dt * F (resp. dt * G) on the four patch faces is ADDED to it:
+ * freg[side][comp][k], side 0 = x-line 0, 1 = x-line N, 2 = y-line 0,
+ * 3 = y-line N, k in [0, N) (Section 3.2, conservative fix).                */
+void orc_step_patch(const orc_cfg *cf, const double *in, double *out, double *freg) {
+    lay_t L = lay_make(cf->n, cf->ncomp);
+    const int n = cf->n, nc = cf->ncomp;
+    const int nl = n + 3; /* node lines -1 .. N+1 */
+    memcpy(out, in, sizeof(double) * lay_patch_words(&L));
+
+    /* q_node[time][type][comp][(j+1)*nl + (i+1)] */
+    size_t per = (size_t)nl * nl;
+    double *qn = (double *)calloc((size_t)3 * 3 * nc * per, sizeof(double));
+#define QN(t, ty, c, i, j) qn[((((size_t)(t) * 3 + (ty)) * nc + (c)) * per) + (size_t)((j) + 1) * nl + ((i) + 1)]
+    static const int plane_of[3] = {PL_CORNER, PL_XMID, PL_YMID};
+    double v[3];
+    for (int ty = 0; ty < 3; ++ty) {
+        int imax = (ty == ND_YMID) ? n + 1 : n + 2; /* exclusive upper line / column */
+        int jmax = (ty == ND_XMID) ? n + 1 : n + 2;
+        for (int j = -1; j < jmax; ++j)
+            for (int i = -1; i < imax; ++i) {
+                for (int c = 0; c < nc; ++c) QN(0, ty, c, i, j) = PLc(&L, in, c, plane_of[ty])[IX(&L, i, j)];
+                evolve_node(&L, in, cf, ty, i, j, 0.5 * cf->dt, v);
+                for (int c = 0; c < nc; ++c) QN(1, ty, c, i, j) = v[c];
+                evolve_node(&L, in, cf, ty, i, j, cf->dt, v);
+                for (int c = 0; c < nc; ++c) QN(2, ty, c, i, j) = v[c];
+            }
+    }
+
+    /* Eq. Simpson-2d: F at x-line i, row j; G at y-line j, column i. */
+    const double wt[3] = {1.0, 4.0, 1.0};
+    double *F = (double *)calloc((size_t)nc * per, sizeof(double));
+    double *Gf = (double *)calloc((size_t)nc * per, sizeof(double));
+#define FX(c, i, j) F[(size_t)(c) * per + (size_t)((j) + 1) * nl + ((i) + 1)]
+#define GY(c, i, j) Gf[(size_t)(c) * per + (size_t)((j) + 1) * nl + ((i) + 1)]
+    double q[3], f[3];
+    for (int j = -1; j < n + 1; ++j)
+        for (int i = -1; i < n + 2; ++i) {
+            double acc[3] = {0, 0, 0};
+            for (int t = 0; t < 3; ++t) {
+                /* three face points: lower corner, midpoint, upper corner */
+                for (int s = 0; s < 3; ++s) {
+                    for (int c = 0; c < nc; ++c)
+                        q[c] = (s == 0) ? QN(t, ND_CORNER, c, i, j)
+                             : (s == 1) ? QN(t, ND_XMID, c, i, j)
+                                        : QN(t, ND_CORNER, c, i, j + 1);
+                    phys_flux(cf, 0, q, f);
+                    for (int c = 0; c < nc; ++c) acc[c] += wt[t] * wt[s] * f[c];
+                }
+            }
+            for (int c = 0; c < nc; ++c) FX(c, i, j) = acc[c] / 36.0;
+        }
+    for (int j = -1; j < n + 2; ++j)
+        for (int i = -1; i < n + 1; ++i) {
+            double acc[3] = {0, 0, 0};
+            for (int t = 0; t < 3; ++t) {
+                for (int s = 0; s < 3; ++s) {
+                    for (int c = 0; c < nc; ++c)
+                        q[c] = (s == 0) ? QN(t, ND_CORNER, c, i, j)
+                             : (s == 1) ? QN(t, ND_YMID, c, i, j)
+                                        : QN(t, ND_CORNER, c, i + 1, j);
+                    phys_flux(cf, 1, q, f);
+                    for (int c = 0; c < nc; ++c) acc[c] += wt[t] * wt[s] * f[c];
+                }
+            }
+            for (int c = 0; c < nc; ++c) GY(c, i, j) = acc[c] / 36.0;
+        }
+
+    /* Eq. 2dfv on cells [-1, N+1)^2 */
+    for (int c = 0; c < nc; ++c) {
+        const double *ain = PLc(&L, in, c, PL_AVG);
+        double *aout = PL(&L, out, c, PL_AVG);
+        for (int j = -1; j < n + 1; ++j)
+            for (int i = -1; i < n + 1; ++i)
+                aout[IX(&L, i, j)] = ain[IX(&L, i, j)] - cf->dt / cf->dx * (FX(c, i + 1, j) - FX(c, i, j)) -
+                                     cf->dt / cf->dy * (GY(c, i, j + 1) - GY(c, i, j));
+    }
+    /* new point values */
+    for (int ty = 0; ty < 3; ++ty) {
+        int imax = (ty == ND_YMID) ? n + 1 : n + 2;
+        int jmax = (ty == ND_XMID) ? n + 1 : n + 2;
+        for (int c = 0; c < nc; ++c) {
+            double *pl = PL(&L, out, c, plane_of[ty]);
+            for (int j = -1; j < jmax; ++j)
+                for (int i = -1; i < imax; ++i) pl[IX(&L, i, j)] = QN(2, ty, c, i, j);
+        }
+    }
+    if (freg) {
+        for (int c = 0; c < nc; ++c)
+            for (int k = 0; k < n; ++k) {
+                freg[(0 * nc + c) * n + k] += cf->dt * FX(c, 0, k);
+                freg[(1 * nc + c) * n + k] += cf->dt * FX(c, n, k);
+                freg[(2 * nc + c) * n + k] += cf->dt * GY(c, k, 0);
+                freg[(3 * nc + c) * n + k] += cf->dt * GY(c, k, n);
+            }
+    }
+#undef QN
+#undef FX
+#undef GY
+    free(qn);
+    free(F);
+    free(Gf);
+}
+
+/* --------------------------------------------------------- Section 3.1 (3.)
+ * Same-level ghost fill on a px x py array of patches tiling a periodic box:
+ * every ghost entry (lattice entries outside [g, g+N)^2 of every plane) is a
+ * copy of the entry owned by the neighbouring patch at the same position.   */
+void orc_fill_periodic(int n, int ncomp, int px, int py, double *state) {
+    lay_t L = lay_make(n, ncomp);
+    long pw = lay_patch_words(&L);
+    int gx = px * n, gy = py * n;
+    for (int p = 0; p < px * py; ++p) {
+        int ix = p % px, iy = p / px;
+        for (int c = 0; c < ncomp; ++c)
+            for (int k = 0; k < 4; ++k) {
+                double *dst = PL(&L, state + p * pw, c, k);
+                for (int J = 0; J < L.w; ++J)
+                    for (int I = 0; I < L.w; ++I) {
+                        int li = I - NG, lj = J - NG;
+                        if (li >= 0 && li < n && lj >= 0 && lj < n) continue;
+                        int gi = ((ix * n + li) % gx + gx) % gx;
+                        int gj = ((iy * n + lj) % gy + gy) % gy;
+                        int sp = (gj / n) * px + gi / n;
+                        const double *src = PLc(&L, state + sp * pw, c, k);
+                        dst[(long)J * L.w + I] = src[IX(&L, gi % n, gj % n)];
+                    }
+            }
+    }
+}
+
+/* Uniform periodic run: nsteps x (fill ghosts, step every patch).  `tmp` has
+ * the size of `state`.  OpenMP over patches with `nthreads` threads.        */
+void orc_run_uniform(const orc_cfg *cf, int px, int py, int nsteps, double *state, double *tmp, int nthreads) {
+    lay_t L = lay_make(cf->n, cf->ncomp);
+    long pw = lay_patch_words(&L);
+    int np = px * py;
+    (void)nthreads;
+    for (int s = 0; s < nsteps; ++s) {
+        orc_fill_periodic(cf->n, cf->ncomp, px, py, state);
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1)
+        for (int p = 0; p < np; ++p) orc_step_patch(cf, state + p * pw, tmp + p * pw, NULL);
+        memcpy(state, tmp, sizeof(double) * pw * np);
+    }
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,305 @@
+"""Seeded synthetic inputs for the Active Flux patch step.
+
+This module only *generates data*: initial conditions, exact solutions of the
+two linear PDEs (used as test references), cell averages of those functions by
+Gauss-Legendre quadrature, random degree-of-freedom fields, and the packing of
+all of it into the patch-state layout.  It contains none of the method's
+arithmetic (no reconstruction, evolution, flux or update) and is the only module
+shared by the CPU oracle's tests and the CUDA path.
+
+State layout (the interface contract of the library, Section 2 of the paper,
+degrees of freedom of Figure 1):
+
+    state[patch][comp][plane][plane_stride]
+
+plane 0 = cell average Q_{i,j}, plane 1 = left-edge midpoint Q_{i-1/2,j},
+plane 2 = lower-left corner Q_{i-1/2,j-1/2}, plane 3 = bottom-edge midpoint
+Q_{i,j-1/2}.  Each plane holds a (M+1) x (M+1) row-major lattice (x fastest),
+M = N + 2g, g = 2 ghost layers (Section 3.2); lattice index (I, J) = (i+g, j+g)
+for cell (i, j), i, j in [-g, N+g].  The plane stride is (M+1)^2 rounded up to
+a multiple of 8 elements so every plane starts 32-byte aligned.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+G = 2
+AVG, XMID, CORNER, YMID = 0, 1, 2, 3
+
+
+@dataclass(frozen=True)
+class Layout:
+    n: int            # interior cells per patch side
+    ncomp: int        # 1 (advection) or 3 (acoustics: p, u, v)
+
+    @property
+    def g(self) -> int:
+        return G
+
+    @property
+    def m(self) -> int:
+        return self.n + 2 * G
+
+    @property
+    def w(self) -> int:
+        return self.m + 1
+
+    @property
+    def plane(self) -> int:
+        return (self.w * self.w + 7) // 8 * 8
+
+    @property
+    def patch_words(self) -> int:
+        return self.ncomp * 4 * self.plane
+
+    def empty(self, npatch: int, fill=np.nan, dtype=np.float64) -> np.ndarray:
+        return np.full((npatch, self.ncomp, 4, self.plane), fill, dtype=dtype)
+
+    def lattice(self, arr: np.ndarray) -> np.ndarray:
+        """View [..., plane_stride] as [..., W, W] (row J, column I)."""
+        return arr[..., : self.w * self.w].reshape(arr.shape[:-1] + (self.w, self.w))
+
+
+# ---------------------------------------------------------------- quadrature
+def gauss_legendre(nq: int):
+    x, w = np.polynomial.legendre.leggauss(nq)
+    return x, w
+
+
+def cell_averages(f, xc: np.ndarray, yc: np.ndarray, dx: float, dy: float, nq: int = 5) -> np.ndarray:
+    """Average of f over [xc-dx/2, xc+dx/2] x [yc-dy/2, yc+dy/2] (tensor Gauss-Legendre)."""
+    gx, gw = gauss_legendre(nq)
+    acc = np.zeros(np.broadcast(xc, yc).shape)
+    for a in range(nq):
+        for b in range(nq):
+            acc += gw[a] * gw[b] * f(xc + 0.5 * dx * gx[a], yc + 0.5 * dy * gx[b])
+    return acc / 4.0
+
+
+# ------------------------------------------------------- initial conditions
+def gaussian(xc, yc, sigma):
+    return lambda x, y: np.exp(-((x - xc) ** 2 + (y - yc) ** 2) / (2.0 * sigma * sigma))
+
+
+def sinsin_plus_gaussian(x, y):
+    """Smooth advection datum: sin(2 pi x) sin(2 pi y) + Gaussian bump (amp 1, sigma 0.05)."""
+    return np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y) + gaussian(0.5, 0.5, 0.05)(x, y)
+
+
+def tanh_disc(x, y, x0=0.5, y0=0.5, r0=0.15, eps=0.02):
+    """Smoothed disc of Section 4.1: H(r + r0) - H(r - r0), H(r) = (tanh(r/eps)+1)/2."""
+    r = np.sqrt((x - x0) ** 2 + (y - y0) ** 2)
+    h = lambda s: 0.5 * (np.tanh(s / eps) + 1.0)
+    return h(r + r0) - h(r - r0)
+
+
+def vortex_velocity(xc=0.5, yc=0.5):
+    """Stationary vortex of Section 4.6 (speed 5r, 2-5r, 0 with kinks at r = 0.2, 0.4)."""
+    def speed_over_r(x, y):
+        r = np.sqrt((x - xc) ** 2 + (y - yc) ** 2)
+        s = np.where(r <= 0.2, 5.0 * r, np.where(r <= 0.4, 2.0 - 5.0 * r, 0.0))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            return np.where(r > 0, s / np.where(r > 0, r, 1.0), 5.0)
+    u = lambda x, y: -(y - yc) * speed_over_r(x, y)
+    v = lambda x, y: (x - xc) * speed_over_r(x, y)
+    return u, v
+
+
+def pulse_plus_vortex():
+    """Acoustic datum: Gaussian pressure pulse (sigma 0.05) at the centre + stationary vortex."""
+    u, v = vortex_velocity()
+    return [gaussian(0.5, 0.5, 0.05), u, v]
+
+
+def lukacova_exact(t: float, c: float = 1.0):
+    """Closed-form acoustic solution of Section 4.5.1 on [-1,1]^2 (periodic)."""
+    tp = 2 * np.pi
+    p = lambda x, y: -np.cos(tp * c * t) * (np.sin(tp * x) + np.sin(tp * y)) / c
+    u = lambda x, y: np.sin(tp * c * t) * np.cos(tp * x) / c
+    v = lambda x, y: np.sin(tp * c * t) * np.cos(tp * y) / c
+    return [p, u, v]
+
+
+def translated(f, a: float, b: float, t: float, lo=(0.0, 0.0), hi=(1.0, 1.0)):
+    """Exact advection solution q(x,y,t) = q0(x - a t, y - b t) on a periodic box."""
+    lx, ly = hi[0] - lo[0], hi[1] - lo[1]
+
+    def g(x, y):
+        xs = lo[0] + np.mod(x - a * t - lo[0], lx)
+        ys = lo[1] + np.mod(y - b * t - lo[1], ly)
+        return f(xs, ys)
+    return g
+
+
+def ring_wave(x, y):
+    """Ring-shaped high-frequency pressure wave exp(-(r-0.25)^2/0.001) cos(80 pi r)."""
+    r = np.sqrt(x * x + y * y)
+    return np.exp(-((r - 0.25) ** 2) / 0.001) * np.cos(80 * np.pi * r)
+
+
+def wave_packet(x, y):
+    """exp(-r^2/0.01) cos(60 pi x), centred at (0.5, 0.5)."""
+    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2
+    return np.exp(-r2 / 0.01) * np.cos(60 * np.pi * x)
+
+
+# ------------------------------------------------------------ state packing
+@dataclass(frozen=True)
+class UniformGrid:
+    """px x py same-level patches of n x n cells tiling [x0,x1] x [y0,y1]."""
+    layout: Layout
+    px: int
+    py: int
+    lo: tuple = (0.0, 0.0)
+    hi: tuple = (1.0, 1.0)
+
+    @property
+    def npatch(self) -> int:
+        return self.px * self.py
+
+    @property
+    def dx(self) -> float:
+        return (self.hi[0] - self.lo[0]) / (self.px * self.layout.n)
+
+    @property
+    def dy(self) -> float:
+        return (self.hi[1] - self.lo[1]) / (self.py * self.layout.n)
+
+    def patch_origin(self, p: int):
+        ix, iy = p % self.px, p // self.px
+        n = self.layout.n
+        return self.lo[0] + ix * n * self.dx, self.lo[1] + iy * n * self.dy
+
+    def periodic_neighbours(self) -> np.ndarray:
+        """[npatch, 8] same-level neighbour indices, order W, E, S, N, SW, SE, NW, NE."""
+        dirs = [(-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (1, -1), (-1, 1), (1, 1)]
+        out = np.zeros((self.npatch, 8), dtype=np.int32)
+        for p in range(self.npatch):
+            ix, iy = p % self.px, p // self.px
+            for k, (sx, sy) in enumerate(dirs):
+                out[p, k] = ((iy + sy) % self.py) * self.px + (ix + sx) % self.px
+        return out
+
+    def state(self, funcs, nq: int = 5, ghosts: bool = False, dtype=np.float64,
+              periodic: bool = True) -> np.ndarray:
+        """Pack cell averages and point values of funcs (one callable per component).
+
+        Interior-owned entries (lattice indices [g, g+N) in both directions) are
+        always filled; the ghost ring is filled from the (periodically wrapped)
+        analytic functions if ghosts=True, otherwise set to NaN.
+        """
+        lay = self.layout
+        assert len(funcs) == lay.ncomp
+        n, g, w = lay.n, G, lay.w
+        dx, dy = self.dx, self.dy
+        st = lay.empty(self.npatch, dtype=np.float64)
+        lat = lay.lattice(st)
+        idx = np.arange(w) - g                 # cell / node-line index i for lattice I
+        own = (idx >= 0) & (idx < n)
+        lx, ly = self.hi[0] - self.lo[0], self.hi[1] - self.lo[1]
+
+        def wrapx(x):
+            return self.lo[0] + np.mod(x - self.lo[0], lx) if periodic else x
+
+        def wrapy(y):
+            return self.lo[1] + np.mod(y - self.lo[1], ly) if periodic else y
+
+        for p in range(self.npatch):
+            ox, oy = self.patch_origin(p)
+            xl = ox + idx * dx                     # node lines x_{i-1/2}
+            yl = oy + idx * dy
+            xc = xl + 0.5 * dx                     # cell centres
+            yc = yl + 0.5 * dy
+            X_l, Y_l = np.meshgrid(xl, yl)         # [J, I]
+            X_c, Y_c = np.meshgrid(xc, yc)
+            for c, f in enumerate(funcs):
+                wf = lambda x, y, f=f: f(wrapx(x), wrapy(y))
+                lat[p, c, AVG] = cell_averages(wf, X_c, Y_c, dx, dy, nq)
+                lat[p, c, XMID] = wf(X_l, Y_c)
+                lat[p, c, CORNER] = wf(X_l, Y_l)
+                lat[p, c, YMID] = wf(X_c, Y_l)
+            if not ghosts:
+                mask = ~(own[None, :] & own[:, None])
+                lat[p][:, :, mask] = np.nan
+        return st.astype(dtype)
+
+    def interior_averages(self, st: np.ndarray, comp: int) -> np.ndarray:
+        """Global [py*N, px*N] array of interior cell averages of one component."""
+        lay = self.layout
+        n, g = lay.n, G
+        lat = lay.lattice(st)
+        out = np.zeros((self.py * n, self.px * n))
+        for p in range(self.npatch):
+            ix, iy = p % self.px, p // self.px
+            out[iy * n:(iy + 1) * n, ix * n:(ix + 1) * n] = lat[p, comp, AVG, g:g + n, g:g + n]
+        return out
+
+    def exact_averages(self, f, nq: int = 5) -> np.ndarray:
+        n = self.layout.n
+        xc = self.lo[0] + (np.arange(self.px * n) + 0.5) * self.dx
+        yc = self.lo[1] + (np.arange(self.py * n) + 0.5) * self.dy
+        X, Y = np.meshgrid(xc, yc)
+        return cell_averages(f, X, Y, self.dx, self.dy, nq)
+
+    def l1_error(self, st: np.ndarray, comp: int, f, nq: int = 5) -> float:
+        """sum |Q - Q_exact| dx dy over interior cell averages."""
+        d = self.interior_averages(st, comp) - self.exact_averages(f, nq)
+        return float(np.abs(d).sum() * self.dx * self.dy)
+
+
+def random_state(layout: Layout, npatch: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Uniform(-1, 1) values in every entry of every plane (all DOFs independent)."""
+    rng = np.random.default_rng(seed)
+    st = rng.uniform(-1.0, 1.0, size=(npatch, layout.ncomp, 4, layout.plane))
+    return st.astype(dtype)
+
+
+def cfl_dt(eq: str, cfl: float, dx: float, dy: float, a=1.0, b=0.0, c=1.0) -> float:
+    """Largest dt with the given CFL number (Eq. cfl-adv / Eq. cfl-acoustics form)."""
+    if eq == "advection":
+        return cfl / max(abs(a) / dx, abs(b) / dy)
+    return cfl / max(c / dx, c / dy)
+
+
+def steps_to(t_end: float, dt_max: float):
+    """Land exactly on t_end: n = ceil(T / dt_max), dt = T / n."""
+    n = int(math.ceil(t_end / dt_max - 1e-12))
+    return n, t_end / n
+
+
+def pack_owned(grid: UniformGrid, owned: np.ndarray, dtype=np.float64) -> np.ndarray:
+    """Scatter global owned DOFs owned[comp][plane][py*N][px*N] into a patch state.
+
+    Entry [c][k][J][I] of `owned` is the DOF of plane k owned by global cell
+    (I, J); ghost entries of the result are NaN.
+    """
+    lay = grid.layout
+    n, g = lay.n, G
+    st = lay.empty(grid.npatch)
+    lat = lay.lattice(st)
+    for p in range(grid.npatch):
+        ix, iy = p % grid.px, p // grid.px
+        lat[p, :, :, g:g + n, g:g + n] = owned[:, :, iy * n:(iy + 1) * n, ix * n:(ix + 1) * n]
+    return st.astype(dtype)
+
+
+def unpack_owned(grid: UniformGrid, st: np.ndarray) -> np.ndarray:
+    """Inverse of pack_owned: gather interior-owned entries into global arrays."""
+    lay = grid.layout
+    n, g = lay.n, G
+    lat = lay.lattice(st)
+    out = np.zeros((lay.ncomp, 4, grid.py * n, grid.px * n), dtype=st.dtype)
+    for p in range(grid.npatch):
+        ix, iy = p % grid.px, p // grid.px
+        out[:, :, iy * n:(iy + 1) * n, ix * n:(ix + 1) * n] = lat[p, :, :, g:g + n, g:g + n]
+    return out
+
+
+def random_owned(grid: UniformGrid, seed: int) -> np.ndarray:
+    """Uniform(-1, 1) global owned DOFs for every component and plane."""
+    rng = np.random.default_rng(seed)
+    n = grid.layout.n
+    return rng.uniform(-1.0, 1.0, size=(grid.layout.ncomp, 4, grid.py * n, grid.px * n))
