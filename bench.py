@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark of the Active Flux patch step on GB300.
+
+Workload (one bench step = one Active Flux time step of the whole grid, i.e.
+one af_patch_step launch over every patch):
+  2-D acoustics (p, u, v), c = 1, periodic unit square, Gaussian pressure pulse
+  (sigma 0.05) at the centre plus the stationary vortex, CFL 0.4, patches of
+  32 x 32 cells with 2 ghost layers.  The grid is 4096 x 4096 cells
+  (128 x 128 patches): the same patch shape as the 512 x 512 / 16 x 16-patch
+  configuration, scaled so the state (1.1 GB FP32, 2.2 GB FP64 per copy) is
+  larger than the 129 MB L2 and every step streams from HBM.
+
+Metric: interior cell updates per second (all three components).  Reported
+for the FP32 patch stencil (`value`) and the FP64 stencil (`fp64`).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+the method here) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS = 32
+P_SIDE = 128
+CFL = 0.4
+BYTES_PER_CELL = {"f32": 3 * 8 * 4, "f64": 3 * 8 * 8}   # 3 comps x (4 read + 4 written) words
+WORKLOAD = ("acoustics c=1, periodic unit square, 4096x4096 cells as 128x128 patches of 32x32 "
+            "(2 ghost layers), Gaussian pulse sigma 0.05 + stationary vortex, CFL 0.4")
+METRIC = "cell updates/sec (Active Flux patch step, acoustics, 32x32 patches)"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# --------------------------------------------------------------------- peaks
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = None
+    src = "fallback"
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+
+            def find(o, key):
+                if isinstance(o, dict):
+                    for k, v in o.items():
+                        if k == key and isinstance(v, (int, float)):
+                            return float(v)
+                        r = find(v, key)
+                        if r is not None:
+                            return r
+                return None
+            hbm = find(d, "hbm_gbs")
+            if hbm is not None:
+                src = "measured"
+        except Exception:
+            hbm = None
+    if hbm is None:
+        hbm = 6800.0
+    return hbm, src
+
+
+# -------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- setup
+def initial_state(prec: str):
+    import synth as S
+    grid = S.UniformGrid(S.Layout(N_CELLS, 3), P_SIDE, P_SIDE)
+    st = S.periodic_state(grid, S.pulse_plus_vortex(), nq=2,
+                          dtype=np.float32 if prec == "f32" else np.float64)
+    return grid, st
+
+
+def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
+    import torch
+    from paper_2205_07572_gb300 import af
+    from paper_2205_07572_gb300.uniform import UniformRun
+    grid, st = initial_state(prec)
+    dt = CFL * grid.dx
+    cfg = af.config(af.ACOUSTICS, af.F32 if prec == "f32" else af.F64, N_CELLS, c=1.0)
+    run = UniformRun(cfg, P_SIDE, P_SIDE, grid.dx, grid.dy, dt, state=st)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        run.step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        run.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / steps
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = grid.npatch * N_CELLS * N_CELLS
+    # sanity: the state stays finite
+    assert torch.isfinite(run.state).all().item()
+    return {"ms": ms, "cells": cells, "clocks": ck, "nwork": run.nwork, "run": run}
+
+
+def run_e2e(prec: str, steps: int, warmup: int):
+    """Same step through the public API with the state kept in pinned HOST
+    memory: every step copies it host->device, runs af_patch_step, and copies
+    the result back (host<->device copies inside the timed region)."""
+    import torch
+    from paper_2205_07572_gb300 import af
+    grid, st = initial_state(prec)
+    dt = CFL * grid.dx
+    cfg = af.config(af.ACOUSTICS, af.F32 if prec == "f32" else af.F64, N_CELLS, c=1.0)
+    from paper_2205_07572_gb300.uniform import UniformRun
+    run = UniformRun(cfg, P_SIDE, P_SIDE, grid.dx, grid.dy, dt, state=None)
+    host = torch.from_numpy(st.reshape(run.a.shape)).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def one():
+        run.a.copy_(host, non_blocking=True)
+        af.patch_step(cfg, run.work, run.nwork, run.a, run.b, dt, grid.dx, grid.dy, None, stream)
+        host.copy_(run.b, non_blocking=True)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        one()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    nbytes = host.numel() * host.element_size()
+    cells = grid.npatch * N_CELLS * N_CELLS
+    return {"value": cells / (ms * 1e-3), "unit": "cell updates/s", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "ms_per_step": ms}
+
+
+def literal_config2(prec: str, steps: int):
+    """The 512 x 512-cell (16 x 16 patches of 32^2) configuration itself: its
+    17-34 MB state is L2-resident, so this is reported beside the HBM-scaled
+    workload, not as the headline."""
+    import torch
+    import synth as S
+    from paper_2205_07572_gb300 import af
+    from paper_2205_07572_gb300.uniform import UniformRun
+    grid = S.UniformGrid(S.Layout(N_CELLS, 3), 16, 16)
+    st = np.nan_to_num(grid.state(S.pulse_plus_vortex(), nq=3))
+    dt = CFL * grid.dx
+    cfg = af.config(af.ACOUSTICS, af.F32 if prec == "f32" else af.F64, N_CELLS, c=1.0)
+    run = UniformRun(cfg, 16, 16, grid.dx, grid.dy, dt, state=st)
+    for _ in range(5):
+        run.step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        run.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    return {"value": grid.npatch * N_CELLS * N_CELLS / (ms * 1e-3), "ms_per_step": ms,
+            "steps_T0.5": 640, "run_ms_T0.5": 640 * ms}
+
+
+# ----------------------------------------------------------- CPU oracle arm
+def oracle_sample(steps: int, budget_s: float = 15.0):
+    """Time the FP64 oracle on a bounded sample of the workload: an 8 x 8 block
+    of the 32^2 patches treated as its own periodic grid (same patch shape,
+    same datum, same CFL)."""
+    import oracle as O
+    import synth as S
+    px = py = 8
+    grid = S.UniformGrid(S.Layout(N_CELLS, 3), px, py, (0.5 - 4 * N_CELLS / 4096, 0.5 - 4 * N_CELLS / 4096),
+                         (0.5 + 4 * N_CELLS / 4096, 0.5 + 4 * N_CELLS / 4096))
+    st = np.nan_to_num(grid.state(S.pulse_plus_vortex(), nq=2))
+    dt = CFL * grid.dx
+    cf = O.cfg(O.ACOUSTICS, N_CELLS, grid.dx, grid.dy, dt, c=1.0)
+    nt = O.max_threads()
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        st = O.run_uniform(cf, px, py, 1, st, nthreads=nt)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    cells = px * py * N_CELLS * N_CELLS
+    return {"value": cells * done / el, "unit": "cell updates/s", "cores": nt, "kind": "oracle",
+            "sample": f"8x8 patches of 32^2 (65536 cells) of the same workload, {done} FP64 steps, {el:.1f} s"}
+
+
+# ---------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    warm = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle as O
+        O.build()
+        per = []
+        for k in range(warm + args.steps):
+            r = oracle_sample(1, budget_s=60.0)
+            if k >= warm:
+                per.append(r)
+        v = statistics.median(x["value"] for x in per)
+        cpu = dict(per[0])
+        cpu["value"] = v
+        cpu["sample"] = cpu["sample"].replace("1 FP64 steps", "one FP64 step per bench step")
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell updates/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": warm,
+                "ms_per_step": 65536 / v * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD + " (oracle sample: 8x8 patches)", "l2": "inputs > L2 n/a (CPU)"},
+                "cpu_baseline": cpu,
+                "e2e": {"value": v, "unit": "cell updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    from paper_2205_07572_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+
+    r32 = run_ours("f32", args.steps, warm, rank, world, dist)
+    r64 = run_ours("f64", max(3, args.steps // 4), warm, rank, world, dist)
+    hbm, src = measured_peaks()
+    cells = r32["cells"]
+    value = world * cells / (r32["ms"] * 1e-3)
+    achieved = cells * BYTES_PER_CELL["f32"] / (r32["ms"] * 1e-3) / 1e9
+    line = None
+    if rank == 0:
+        e2e = run_e2e("f32", max(3, args.steps // 4), 2)
+        lit32 = literal_config2("f32", 50)
+        lit64 = literal_config2("f64", 10)
+        cpu = None if args.no_cpu_baseline else oracle_sample(20)
+        v64 = world * cells / (r64["ms"] * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": warm, "ms_per_step": r32["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "patches": P_SIDE * P_SIDE, "cells_per_step": cells,
+                       "l2": "inputs larger than L2 (1.1 GB FP32 state per copy)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "fp64": {"value": v64, "unit": "cell updates/s", "ms_per_step": r64["ms"],
+                     "achieved_gbs": cells * BYTES_PER_CELL["f64"] / (r64["ms"] * 1e-3) / 1e9,
+                     "clocks": r64["clocks"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "step_kernel<float, acoustics>",
+                         "peak_source": f"{src} HBM copy bandwidth",
+                         "algorithmic_bytes_per_launch": cells * BYTES_PER_CELL["f32"]},
+            "literal_512x512": {"f32": lit32, "f64": lit64, "note": "L2-resident (34 MB FP64 state)"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": r32["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,144 @@
+"""Thin Python binding of libaf.so (include/af.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts
+arguments (torch tensors -> device pointers, numpy arrays -> host pointers,
+torch streams -> cudaStream_t) and raises AFError on a non-zero status.
+There is no fallback: if libaf.so is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaf.so")
+
+ADVECTION, ACOUSTICS = 0, 1
+F64, F32 = 0, 1
+
+
+class AFError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)}" if what else status_string(status))
+
+
+class Config(C.Structure):
+    _fields_ = [("eq", C.c_int32), ("prec", C.c_int32), ("n", C.c_int32), ("ncomp", C.c_int32),
+                ("a", C.c_double), ("b", C.c_double), ("c", C.c_double)]
+
+
+class Work(C.Structure):
+    _fields_ = [("patch", C.c_int32), ("level", C.c_int32), ("nbr", C.c_int32 * 8),
+                ("x0", C.c_int16), ("x1", C.c_int16), ("y0", C.c_int16), ("y1", C.c_int16),
+                ("flags", C.c_int32), ("pad_", C.c_int32 * 3)]
+
+
+assert C.sizeof(Work) == 64
+
+_lib = None
+_VP, _DP, _IP = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)
+
+
+def lib():
+    """Load libaf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2205_07572_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        L.af_status_string.restype = C.c_char_p
+        L.af_status_string.argtypes = [C.c_int]
+        L.af_plane_stride.restype = C.c_int64
+        L.af_plane_stride.argtypes = [C.c_int32]
+        L.af_patch_words.restype = C.c_int64
+        L.af_patch_words.argtypes = [C.c_int32, C.c_int32]
+        L.af_build_step_work.restype = C.c_int
+        L.af_build_step_work.argtypes = [C.POINTER(Config), C.c_int32, _IP, _IP, _IP, C.POINTER(Work),
+                                         C.c_int32, _IP]
+        L.af_patch_step.restype = C.c_int
+        L.af_patch_step.argtypes = [C.POINTER(Config), C.c_int32, _VP, _VP, _VP, C.c_double, C.c_double,
+                                    C.c_double, _VP, _VP]
+        _register_more(L)
+        _lib = L
+    return _lib
+
+
+def _register_more(L):
+    """Signatures of the entry points added beside the step (fill, reflux, tag)."""
+    for name, res, args in _EXTRA:
+        if hasattr(L, name):
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+
+
+_EXTRA: list = []
+
+
+def status_string(s: int) -> str:
+    return lib().af_status_string(int(s)).decode()
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise AFError(st, what)
+
+
+def ptr(x):
+    """Device/host address of a torch tensor, numpy array or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def config(eq: int, prec: int, n: int, a: float = 0.0, b: float = 0.0, c: float = 1.0) -> Config:
+    return Config(eq, prec, n, 1 if eq == ADVECTION else 3, a, b, c)
+
+
+def plane_stride(n: int) -> int:
+    return int(lib().af_plane_stride(n))
+
+
+def patch_words(n: int, ncomp: int) -> int:
+    return int(lib().af_patch_words(n, ncomp))
+
+
+def build_step_work(cfg: Config, patches, levels=None, nbr=None) -> np.ndarray:
+    """Host work list of af_patch_step as a uint8 array (64 bytes per entry)."""
+    patches = np.ascontiguousarray(patches, dtype=np.int32)
+    lv = None if levels is None else np.ascontiguousarray(levels, dtype=np.int32)
+    nb = None if nbr is None else np.ascontiguousarray(nbr, dtype=np.int32).reshape(-1)
+    npatch = len(patches)
+    L = lib()
+    cnt = C.c_int32(0)
+    ip = lambda a: None if a is None else a.ctypes.data_as(_IP)
+    st = L.af_build_step_work(C.byref(cfg), npatch, ip(patches), ip(lv), ip(nb), None, 0, C.byref(cnt))
+    if st != 0 and cnt.value == 0:
+        _check(st, "af_build_step_work")
+    buf = (Work * max(cnt.value, 1))()
+    st = L.af_build_step_work(C.byref(cfg), npatch, ip(patches), ip(lv), ip(nb), buf, cnt.value, C.byref(cnt))
+    _check(st, "af_build_step_work")
+    return np.frombuffer(buf, dtype=np.uint8, count=64 * cnt.value).copy()
+
+
+def patch_step(cfg: Config, work, nwork: int, state_in, state_out, dt0: float, dx0: float, dy0: float,
+               flux_reg=None, stream=None) -> None:
+    st = lib().af_patch_step(C.byref(cfg), int(nwork), ptr(work), ptr(state_in), ptr(state_out),
+                             float(dt0), float(dx0), float(dy0), ptr(flux_reg), stream_handle(stream))
+    _check(st, "af_patch_step")

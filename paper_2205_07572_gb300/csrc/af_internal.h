@@ -1,0 +1,90 @@
+// Internal declarations shared by the host and device translation units of
+// libaf.so.  Not part of the public ABI (include/af.h is).
+#pragma once
+
+#include <cstdint>
+
+#include "af.h"
+
+namespace af {
+
+constexpr int kGhost = 2;      // ghost layers (Section 3.2)
+constexpr int kTileMax = 32;   // cells per tile side in af_patch_step
+constexpr int kPlanes = 4;     // avg, xmid, corner, ymid (Section 2, Fig. 1)
+enum Plane { kAvg = 0, kXmid = 1, kCorner = 2, kYmid = 3 };
+
+inline int64_t plane_stride(int n) {
+    const int64_t w = n + 2 * kGhost + 1;
+    return (w * w + 7) / 8 * 8;
+}
+
+// ---------------------------------------------------------------------------
+// Acoustic stencil weights (Eqs. ERFormula, sphe-mean).
+//
+// A node-cell work item (i, j) evolves the corner at node lines (i, j), the
+// left-edge midpoint of cell (i, j) and the bottom-edge midpoint of cell
+// (i, j).  All three discs lie in the 2 x 2 cell block (i-1..i, j-1..j), whose
+// 25 degrees of freedom per component are numbered
+//   k in [0, 4):   averages of cells (i-1+a, j-1+b),      k = 2b + a
+//   k in [4, 13):  corners at lines (i-1+a, j-1+b),       k = 4 + 3b + a
+//   k in [13, 19): left-edge mids (line i-1+a, row j-1+b), k = 13 + 3b + a
+//   k in [19, 25): bottom-edge mids (col i-1+a, line j-1+b), k = 19 + 2b + a
+// The corner uses all 25, the edge midpoints 15 each (x_idx / y_idx).
+// Component pairs (out <- in) with non-zero weights:
+//   0 p<-p, 1 p<-u, 2 p<-v, 3 u<-u, 4 u<-p, 5 v<-v, 6 v<-p.
+// Combination 0 is T = Q^n + 4 Q^{n+1/2} + Q^{n+1} (the time-Simpson sum
+// entering Eq. Simpson-2d), combination 1 is Q^{n+1}.
+#ifdef __CUDACC__
+#define AF_HD __host__ __device__
+#else
+#define AF_HD
+#endif
+AF_HD constexpr int x_idx(int k) {
+    constexpr int t[15] = {2, 3, 7, 8, 9, 10, 11, 12, 16, 17, 18, 21, 22, 23, 24};
+    return t[k];
+}
+AF_HD constexpr int y_idx(int k) {
+    constexpr int t[15] = {1, 3, 5, 6, 8, 9, 11, 12, 14, 15, 17, 18, 20, 22, 24};
+    return t[k];
+}
+
+template <typename T>
+struct AcousticWeights {
+    T wc[2][7][25];
+    T wx[2][7][15];
+    T wy[2][7][15];
+};
+
+// Advection weights (Eq. advection-update): for node type t (0 corner,
+// 1 left-edge mid, 2 bottom-edge mid) and time s (0: dt/2, 1: dt) the foot of
+// the characteristic lies in cell (line + off[t][s][0], line + off[t][s][1]);
+// the value there is sum_k w[t][s][k] * dof_k over that cell's nine degrees
+// of freedom ordered avg, corner(0,0), corner(1,0), corner(0,1), corner(1,1),
+// xmid(0), xmid(1), ymid(0), ymid(1).
+template <typename T>
+struct AdvectionWeights {
+    T w[3][2][9];
+    int32_t off[3][2][2];
+};
+
+// Double-precision derivations on the host (af_weights.cpp).
+void acoustic_weights(double rho_x, double rho_y, AcousticWeights<double> &w);
+void advection_weights(double nu_x, double nu_y, AdvectionWeights<double> &w);
+
+}  // namespace af
+
+namespace af {
+
+// Split `w` cells into ceil(w / kTileMax) tiles of near-equal size.
+inline int tiles_for(int w) { return (w + kTileMax - 1) / kTileMax; }
+inline int tile_size_max(int w) {
+    const int t = tiles_for(w);
+    return (w + t - 1) / t;
+}
+// Largest tile side af_build_step_work produces for patches of n cells.
+inline int tile_max_for(int n) {
+    const int a = tile_size_max(n), b = tile_size_max(n + 2);
+    return a > b ? a : b;
+}
+
+}  // namespace af

@@ -1,0 +1,54 @@
+"""Host driver of a uniform, periodic array of same-level patches.
+
+Holds two device state buffers and the device work list; every step is one
+af_patch_step call (the same-level ghost copy is fused into the kernel's halo
+load, Section 3.1 case 3), after which the buffers swap.  Host orchestration
+only: all arithmetic runs in libaf.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import af
+
+
+def periodic_neighbours(px: int, py: int) -> np.ndarray:
+    """[px*py, 8] neighbour indices (W, E, S, N, SW, SE, NW, NE) on a torus."""
+    dirs = [(-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (1, -1), (-1, 1), (1, 1)]
+    out = np.zeros((px * py, 8), dtype=np.int32)
+    for p in range(px * py):
+        ix, iy = p % px, p // px
+        for k, (sx, sy) in enumerate(dirs):
+            out[p, k] = ((iy + sy) % py) * px + (ix + sx) % px
+    return out
+
+
+class UniformRun:
+    """px x py patches of n x n cells, periodic, advanced by af_patch_step."""
+
+    def __init__(self, cfg: af.Config, px: int, py: int, dx: float, dy: float, dt: float, device="cuda",
+                 state=None, flux_reg: bool = False):
+        import torch
+        self.cfg, self.px, self.py = cfg, px, py
+        self.dx, self.dy, self.dt = dx, dy, dt
+        self.npatch = px * py
+        self.words = af.patch_words(cfg.n, cfg.ncomp)
+        dtype = torch.float64 if cfg.prec == af.F64 else torch.float32
+        self.a = torch.zeros((self.npatch, self.words), dtype=dtype, device=device)
+        if state is not None:
+            self.a.copy_(torch.as_tensor(np.asarray(state).reshape(self.npatch, self.words)).to(dtype))
+        self.b = self.a.clone()
+        w = af.build_step_work(cfg, np.arange(self.npatch), nbr=periodic_neighbours(px, py))
+        self.nwork = len(w) // 64
+        self.work = torch.from_numpy(w).to(device)
+        self.freg = (torch.zeros((self.npatch, 4, cfg.ncomp, cfg.n), dtype=torch.float64, device=device)
+                     if flux_reg else None)
+
+    def step(self, stream=None):
+        af.patch_step(self.cfg, self.work, self.nwork, self.a, self.b, self.dt, self.dx, self.dy,
+                      self.freg, stream)
+        self.a, self.b = self.b, self.a
+
+    @property
+    def state(self):
+        return self.a

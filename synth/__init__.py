@@ -303,3 +303,38 @@ def random_owned(grid: UniformGrid, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     n = grid.layout.n
     return rng.uniform(-1.0, 1.0, size=(grid.layout.ncomp, 4, grid.py * n, grid.px * n))
+
+
+def periodic_state(grid: UniformGrid, funcs, nq: int = 2, dtype=np.float64) -> np.ndarray:
+    """Vectorised packing for a periodic grid: every entry (ghost ring
+    included) holds the value of the periodically wrapped functions.  Used for
+    large synthetic inputs."""
+    lay = grid.layout
+    n, g, w = lay.n, G, lay.w
+    PX, PY = grid.px * n, grid.py * n
+    kx = np.arange(-g, PX + g + 1)
+    ky = np.arange(-g, PY + g + 1)
+    lx, ly = grid.hi[0] - grid.lo[0], grid.hi[1] - grid.lo[1]
+    wrap_x = lambda x: grid.lo[0] + np.mod(x - grid.lo[0], lx)
+    wrap_y = lambda y: grid.lo[1] + np.mod(y - grid.lo[1], ly)
+    xl = grid.lo[0] + kx * grid.dx
+    yl = grid.lo[1] + ky * grid.dy
+    xc, yc = xl + 0.5 * grid.dx, yl + 0.5 * grid.dy
+    st = np.empty((grid.npatch, lay.ncomp, 4, lay.plane), dtype=dtype)
+    st[..., w * w:] = 0
+    lat = lay.lattice(st).reshape(grid.py, grid.px, lay.ncomp, 4, w, w)
+    for c, f in enumerate(funcs):
+        wf = lambda x, y, f=f: f(wrap_x(x), wrap_y(y))
+        planes = [
+            cell_averages(wf, xc[None, :], yc[:, None], grid.dx, grid.dy, nq),
+            wf(xl[None, :], yc[:, None]),
+            wf(xl[None, :], yl[:, None]),
+            wf(xc[None, :], yl[:, None]),
+        ]
+        for k, arr in enumerate(planes):
+            arr = np.ascontiguousarray(arr, dtype=dtype)
+            s0, s1 = arr.strides
+            win = np.lib.stride_tricks.as_strided(arr, shape=(grid.py, grid.px, w, w),
+                                                  strides=(n * s0, n * s1, s0, s1))
+            lat[:, :, c, k] = win
+    return st

@@ -1,0 +1,81 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry
+point, and rejects bad arguments on the host before touching the GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def af():
+    from paper_2205_07572_gb300 import af as _af, build
+    build.build()
+    return _af
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(af_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol(af):
+    L = af.lib()
+    names = _declared()
+    assert "af_patch_step" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_layout_sizes(af):
+    for n in (8, 16, 32, 64):
+        w = n + 5
+        assert af.plane_stride(n) == (w * w + 7) // 8 * 8
+        assert af.patch_words(n, 3) == 12 * af.plane_stride(n)
+
+
+def test_work_builder_tiles(af):
+    cfg = af.config(af.ACOUSTICS, af.F32, 32)
+    nbr = np.zeros((3, 8), np.int32)
+    w = np.frombuffer(af.build_step_work(cfg, [0, 1, 2], nbr=nbr).tobytes(), dtype=np.int16).reshape(-1, 32)
+    assert len(w) == 3                       # interior patches: one 32^2 tile each
+    assert (w[:, 20:24] == [0, 32, 0, 32]).all()
+    nbr[1, 5] = -1                           # patch 1 misses its SE neighbour
+    w = np.frombuffer(af.build_step_work(cfg, [0, 1, 2], nbr=nbr).tobytes(), dtype=np.int16).reshape(-1, 32)
+    assert len(w) == 1 + 4 + 1               # extended patch: [-1, 33) in 2 x 2 tiles
+    ext = w[1:5, 20:24]
+    assert ext[:, 0].min() == -1 and ext[:, 1].max() == 33
+    cfg64 = af.config(af.ADVECTION, af.F64, 64)
+    w = af.build_step_work(cfg64, [0])
+    assert len(w) // 64 == 9                 # [-1, 65) -> 3 x 3 tiles of 22
+
+
+def test_host_side_errors(af):
+    cfg = af.config(af.ACOUSTICS, af.F64, 16, c=1.0)
+    buf_a, buf_b, work = 1 << 20, 2 << 20, 3 << 20  # fake, aligned, never dereferenced
+    dx = 1.0 / 16
+    with pytest.raises(af.AFError) as e:
+        af.patch_step(cfg, work, 1, buf_a, buf_b, 0.6 * dx, dx, dx, stream=0)
+    assert e.value.status == 2               # AF_ERR_CFL (Eq. cfl-acoustics)
+    with pytest.raises(af.AFError) as e:
+        af.patch_step(cfg, work, 1, buf_a, buf_a, 0.4 * dx, dx, dx, stream=0)
+    assert e.value.status == 1               # in == out
+    with pytest.raises(af.AFError) as e:
+        af.patch_step(cfg, work, 1, buf_a + 8, buf_b, 0.4 * dx, dx, dx, stream=0)
+    assert e.value.status == 3               # misaligned state
+    bad = af.config(af.ACOUSTICS, af.F64, 16, c=1.0)
+    bad.ncomp = 1
+    with pytest.raises(af.AFError):
+        af.patch_step(bad, work, 1, buf_a, buf_b, 0.4 * dx, dx, dx, stream=0)
+    adv = af.config(af.ADVECTION, af.F32, 16, a=1.0, b=0.5)
+    with pytest.raises(af.AFError) as e:
+        af.patch_step(adv, work, 1, buf_a, buf_b, 1.1 * dx, dx, dx, stream=0)
+    assert e.value.status == 2               # Eq. cfl-adv
+    af.patch_step(adv, work, 0, buf_a, buf_b, 0.5 * dx, dx, dx, stream=0)  # nothing to do: OK
