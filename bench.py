@@ -264,6 +264,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="both", choices=["both", "f32", "f64"],
+                    help="which stencil precision(s) to time (profiling runs use one)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the end-to-end, literal-size and CPU-baseline measurements")
     args = ap.parse_args()
     warm = max(3, args.warmup)
 
@@ -308,6 +312,13 @@ def main():
     if dist is not None:
         dist.barrier()
 
+    if args.prec != "both":
+        r = run_ours(args.prec, args.steps, warm, rank, world, dist)
+        if rank == 0:
+            print(json.dumps({"prec": args.prec, "ms_per_step": r["ms"],
+                              "value": world * r["cells"] / (r["ms"] * 1e-3), "unit": "cell updates/s",
+                              "clocks": r["clocks"]}), flush=True)
+        return
     r32 = run_ours("f32", args.steps, warm, rank, world, dist)
     r64 = run_ours("f64", max(3, args.steps // 4), warm, rank, world, dist)
     hbm, src = measured_peaks()
@@ -316,10 +327,11 @@ def main():
     achieved = cells * BYTES_PER_CELL["f32"] / (r32["ms"] * 1e-3) / 1e9
     line = None
     if rank == 0:
-        e2e = run_e2e("f32", max(3, args.steps // 4), 2)
-        lit32 = literal_config2("f32", 50)
-        lit64 = literal_config2("f64", 10)
-        cpu = None if args.no_cpu_baseline else oracle_sample(20)
+        extras = not args.no_extras
+        e2e = run_e2e("f32", max(3, args.steps // 4), 2) if extras else None
+        lit32 = literal_config2("f32", 50) if extras else None
+        lit64 = literal_config2("f64", 10) if extras else None
+        cpu = None if (args.no_cpu_baseline or not extras) else oracle_sample(20)
         v64 = world * cells / (r64["ms"] * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": "cell updates/s", "n_gpus": world,

@@ -61,6 +61,21 @@ def lib():
         L.orc_run_uniform.restype = None
         L.orc_run_uniform.argtypes = [C.POINTER(Cfg), C.c_int, C.c_int, C.c_int, dp, dp, C.c_int]
         L.orc_max_threads.restype = C.c_int
+        ip = C.POINTER(C.c_int32)
+        L.orc_fill_amr.restype = None
+        L.orc_fill_amr.argtypes = [C.c_int, C.c_int, C.c_int, ip, ip, ip, C.c_int, C.c_int, C.c_uint32,
+                                   C.c_uint32, C.c_int, dp, dp]
+        L.orc_reflux_amr.restype = None
+        L.orc_reflux_amr.argtypes = [C.c_int, C.c_int, C.c_int, ip, ip, ip, C.c_int, C.c_int, C.c_uint32,
+                                     C.c_double, C.c_double, dp, dp]
+        L.orc_tag.restype = None
+        L.orc_tag.argtypes = [C.c_int, C.c_int, C.c_int, ip, dp, C.c_int, C.c_int, C.c_double, C.c_double,
+                              C.c_double, C.c_double, C.POINTER(C.c_int8), dp]
+        L.orc_mass.restype = None
+        L.orc_mass.argtypes = [C.c_int, C.c_int, C.c_int, ip, dp, C.c_double, C.c_double, dp]
+        L.orc_transfer.restype = None
+        L.orc_transfer.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, ip, dp, C.c_int, ip, ip,
+                                   ip, dp]
         _lib = L
     return _lib
 

@@ -479,3 +479,359 @@ int orc_max_threads(void) {
     return 1;
 #endif
 }
+
+/* =========================================================================
+ * Adaptive mesh refinement (Section 3): a forest of quadtrees over a B x B
+ * brick of level-0 patches, periodic in both directions.  Every leaf is a
+ * patch of N x N cells; level l+1 halves the mesh width (2:1 ratio).
+ *
+ * Positions are integers: the unit is half the cell width of level lmax, so
+ * a level-l cell is 2^(lmax-l+1) units wide and every node, cell centre and
+ * Simpson point used below is an exact integer (no rounding in lookups).
+ * ========================================================================= */
+typedef struct {
+    int n, ncomp, nleaf, B, lmax;
+    const int32_t *level, *ix, *iy;
+    int32_t **map; /* map[l][iy * (B << l) + ix] = leaf index or -1 */
+    long D;        /* domain width in units */
+} forest_t;
+
+static long hw_of(const forest_t *F, int l) { return 2L << (F->lmax - l); }
+
+static int forest_init(forest_t *F, int n, int ncomp, int nleaf, const int32_t *level, const int32_t *ix,
+                       const int32_t *iy, int B, int lmax) {
+    F->n = n; F->ncomp = ncomp; F->nleaf = nleaf; F->B = B; F->lmax = lmax;
+    F->level = level; F->ix = ix; F->iy = iy;
+    F->D = (long)B * n * hw_of(F, 0);
+    F->map = (int32_t **)calloc((size_t)lmax + 1, sizeof(int32_t *));
+    for (int l = 0; l <= lmax; ++l) {
+        long side = (long)B << l;
+        F->map[l] = (int32_t *)malloc(sizeof(int32_t) * side * side);
+        for (long k = 0; k < side * side; ++k) F->map[l][k] = -1;
+    }
+    for (int p = 0; p < nleaf; ++p) {
+        if (level[p] < 0 || level[p] > lmax) return -1;
+        long side = (long)B << level[p];
+        F->map[level[p]][(long)iy[p] * side + ix[p]] = p;
+    }
+    return 0;
+}
+
+static void forest_free(forest_t *F) {
+    for (int l = 0; l <= F->lmax; ++l) free(F->map[l]);
+    free(F->map);
+}
+
+static long wrapD(const forest_t *F, long x) { long r = x % F->D; return r < 0 ? r + F->D : r; }
+
+/* Leaf covering the point (x, y) with half-open patch extents [x0, x1). */
+static int forest_lookup(const forest_t *F, long x, long y) {
+    x = wrapD(F, x); y = wrapD(F, y);
+    for (int l = F->lmax; l >= 0; --l) {
+        long pw = (long)F->n * hw_of(F, l), side = (long)F->B << l;
+        int q = F->map[l][(y / pw) * side + (x / pw)];
+        if (q >= 0) return q;
+    }
+    return -1;
+}
+
+static long leaf_x0(const forest_t *F, int p) { return (long)F->ix[p] * F->n * hw_of(F, F->level[p]); }
+static long leaf_y0(const forest_t *F, int p) { return (long)F->iy[p] * F->n * hw_of(F, F->level[p]); }
+
+/* offset of (x) relative to the origin of leaf q, unwrapping the periodic box */
+static long rel(const forest_t *F, long x, long x0) {
+    long d = wrapD(F, x - x0);
+    if (d > F->D / 2) d -= F->D;
+    return d;
+}
+
+/* Value of the reconstruction (Eq. poly) of leaf q, component c, at (x, y).
+ * The cell is found with the half-open rule, clamped into q's interior;
+ * the reconstruction is continuous, so a point on a cell face may use
+ * either neighbour. */
+static double leaf_eval(const forest_t *F, const double *state, int q, int c, long x, long y) {
+    lay_t L = lay_make(F->n, F->ncomp);
+    const double *patch = state + (long)q * lay_patch_words(&L);
+    long hw = hw_of(F, F->level[q]);
+    long dx = rel(F, x, leaf_x0(F, q)), dy = rel(F, y, leaf_y0(F, q));
+    long ci = dx >= 0 ? dx / hw : -((-dx + hw - 1) / hw);
+    long cj = dy >= 0 ? dy / hw : -((-dy + hw - 1) / hw);
+    if (ci < 0) ci = 0;
+    if (ci > F->n - 1) ci = F->n - 1;
+    if (cj < 0) cj = 0;
+    if (cj > F->n - 1) cj = F->n - 1;
+    double xi = 2.0 * (double)(dx - ci * hw) / (double)hw - 1.0;
+    double eta = 2.0 * (double)(dy - cj * hw) / (double)hw - 1.0;
+    double qn[3][3];
+    cell_nodal(&L, patch, c, (int)ci, (int)cj, qn);
+    return recon_deriv(qn, xi, eta, 0, 0);
+}
+
+/* Entry of leaf q in `plane` at the lattice position of point (x, y) (which
+ * must be a lattice point of that plane for q). */
+static double leaf_entry(const forest_t *F, const double *state, int q, int c, int plane, long x, long y) {
+    lay_t L = lay_make(F->n, F->ncomp);
+    const double *patch = state + (long)q * lay_patch_words(&L);
+    long hw = hw_of(F, F->level[q]);
+    long dx = rel(F, x, leaf_x0(F, q)), dy = rel(F, y, leaf_y0(F, q));
+    if (plane == PL_AVG || plane == PL_YMID) dx -= hw / 2;
+    if (plane == PL_AVG || plane == PL_XMID) dy -= hw / 2;
+    int i = (int)(dx / hw), j = (int)(dy / hw);
+    return PLc(&L, patch, c, plane)[IX(&L, i, j)];
+}
+
+/* Position (units) of lattice entry (plane, i, j) of leaf p. */
+static void entry_pos(const forest_t *F, int p, int plane, int i, int j, long *x, long *y) {
+    long hw = hw_of(F, F->level[p]);
+    *x = leaf_x0(F, p) + (long)i * hw + ((plane == PL_AVG || plane == PL_YMID) ? hw / 2 : 0);
+    *y = leaf_y0(F, p) + (long)j * hw + ((plane == PL_AVG || plane == PL_XMID) ? hw / 2 : 0);
+}
+
+/* Section 3.1: value of a ghost entry of leaf p from the leaf q covering it.
+ *  same level: copy;
+ *  q finer (fine -> coarse): the average is the mean of the four fine cell
+ *    averages, a point value is copied from the coinciding fine vertex;
+ *  q coarser (coarse -> fine): point values are the coarse reconstruction
+ *    evaluated at the point, the average is Simpson's rule over the fine
+ *    cell applied to that reconstruction (exact for it). */
+static double transfer_value(const forest_t *F, const double *state, int lp, int q, int c, int plane, long x,
+                             long y) {
+    int lq = F->level[q];
+    if (lq == lp) return leaf_entry(F, state, q, c, plane, x, y);
+    if (lq > lp) {
+        if (plane == PL_AVG) {
+            long h = hw_of(F, lq) / 2; /* fine half width: fine centres at x +- h */
+            return 0.25 * (leaf_entry(F, state, q, c, PL_AVG, x - h, y - h) +
+                           leaf_entry(F, state, q, c, PL_AVG, x + h, y - h) +
+                           leaf_entry(F, state, q, c, PL_AVG, x - h, y + h) +
+                           leaf_entry(F, state, q, c, PL_AVG, x + h, y + h));
+        }
+        return leaf_entry(F, state, q, c, PL_CORNER, x, y);
+    }
+    if (plane != PL_AVG) return leaf_eval(F, state, q, c, x, y);
+    long h = hw_of(F, lp) / 2; /* half width of the fine (destination) cell */
+    double s = 0.0;
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a)
+            s += SIMPSON_W[a] * SIMPSON_W[b] * leaf_eval(F, state, q, c, x + (a - 1) * h, y + (b - 1) * h);
+    return s;
+}
+
+/* Which leaf's value a point value takes.  A node on the boundary between
+ * leaves of different levels takes the value of the finest leaf touching it
+ * (Section 3.2: the fluxes, and hence the face values, of "the more resolved
+ * grid" are used at coarse-fine interfaces); among equally fine leaves the
+ * one above-right, above-left, below-right, below-left of the point is used,
+ * in that order.  A cell average belongs to the leaf covering its centre.  */
+static int node_owner(const forest_t *F, long x, long y) {
+    int cand[4] = {forest_lookup(F, x, y), forest_lookup(F, x - 1, y), forest_lookup(F, x, y - 1),
+                   forest_lookup(F, x - 1, y - 1)};
+    int best = cand[0];
+    for (int k = 1; k < 4; ++k)
+        if (cand[k] >= 0 && (best < 0 || F->level[cand[k]] > F->level[best])) best = cand[k];
+    return best;
+}
+
+static int entry_owner(const forest_t *F, int plane, long x, long y) {
+    return plane == PL_AVG ? forest_lookup(F, x, y) : node_owner(F, x, y);
+}
+
+/* Ghost exchange of Section 3.1 / 3.2 on a forest.
+ * Destination leaves: those whose level bit is set in dst_levels.  Every
+ * entry of a destination leaf whose owner (entry_owner) is another leaf is
+ * replaced by the owner's data, transferred by transfer_value, provided the
+ * owner's level bit is set in src_levels (time-synchronised levels) and, if
+ * same_only, the owner has the destination's level (the copy done before
+ * every step of a level).  This covers the ghost ring and the nodes on a
+ * leaf's left / bottom face that a finer neighbour owns.  Entries the step
+ * never reads (the average and bottom-mid of the far column, the average and
+ * left-mid of the far row) are skipped.  Results are written to `out`, a copy
+ * of `in` on entry.                                                         */
+void orc_fill_amr(int n, int ncomp, int nleaf, const int32_t *level, const int32_t *ix, const int32_t *iy,
+                  int B, int lmax, uint32_t dst_levels, uint32_t src_levels, int same_only, const double *in,
+                  double *out) {
+    forest_t F;
+    lay_t L = lay_make(n, ncomp);
+    long pw = lay_patch_words(&L);
+    memcpy(out, in, sizeof(double) * pw * nleaf);
+    if (forest_init(&F, n, ncomp, nleaf, level, ix, iy, B, lmax) != 0) { forest_free(&F); return; }
+    for (int p = 0; p < nleaf; ++p) {
+        int lp = level[p];
+        if (!((dst_levels >> lp) & 1u)) continue;
+        for (int k = 0; k < 4; ++k)
+            for (int j = -NG; j <= n + NG; ++j)
+                for (int i = -NG; i <= n + NG; ++i) {
+                    if (i > 0 && i < n && j > 0 && j < n) continue; /* strictly inside: own */
+                    if (i == n + NG && (k == PL_AVG || k == PL_YMID)) continue;
+                    if (j == n + NG && (k == PL_AVG || k == PL_XMID)) continue;
+                    long x, y;
+                    entry_pos(&F, p, k, i, j, &x, &y);
+                    int q = entry_owner(&F, k, x, y);
+                    if (q < 0 || q == p) continue;
+                    int lq = level[q];
+                    if (!((src_levels >> lq) & 1u)) continue;
+                    if (same_only && lq != lp) continue;
+                    for (int c = 0; c < ncomp; ++c)
+                        PL(&L, out + p * pw, c, k)[IX(&L, i, j)] = transfer_value(&F, in, lp, q, c, k, x, y);
+                }
+    }
+    forest_free(&F);
+}
+
+/* Section 3.2, "Global conservation property": Berger-Colella correction.
+ * For every coarse leaf C at level l with l and l+1 both synchronised, and
+ * every face k of C whose neighbour across is a finer leaf F, the coarse
+ * average next to the face is corrected so that it has used the fine fluxes:
+ *   right/top face:  dQ = (R_C - (R_F,a + R_F,b) / 2) / h_C
+ *   left/bottom face: dQ = ((R_F,a + R_F,b) / 2 - R_C) / h_C
+ * where R = sum over the steps since the last synchronisation of dt * F
+ * (registers filled by orc_step_patch; the fine one spans two fine steps and
+ * two fine faces), h_C the coarse mesh width normal to the face.  Consumed
+ * register entries (both sides) are reset to zero.                        */
+void orc_reflux_amr(int n, int ncomp, int nleaf, const int32_t *level, const int32_t *ix, const int32_t *iy,
+                    int B, int lmax, uint32_t sync_levels, double dx0, double dy0, double *freg, double *state) {
+    forest_t F;
+    lay_t L = lay_make(n, ncomp);
+    long pw = lay_patch_words(&L);
+    if (forest_init(&F, n, ncomp, nleaf, level, ix, iy, B, lmax) != 0) { forest_free(&F); return; }
+    long rw = 4L * ncomp * n; /* register words per patch */
+    /* collect corrections first so consumption order does not matter */
+    double *dq = (double *)calloc((size_t)nleaf * ncomp * n * n, sizeof(double));
+    unsigned char *used = (unsigned char *)calloc((size_t)nleaf * rw, 1);
+    for (int p = 0; p < nleaf; ++p) {
+        int l = level[p];
+        if (!((sync_levels >> l) & 1u) || !((sync_levels >> (l + 1)) & 1u)) continue;
+        long hw = hw_of(&F, l), x0 = leaf_x0(&F, p), y0 = leaf_y0(&F, p);
+        long x1 = x0 + (long)n * hw, y1 = y0 + (long)n * hw;
+        double hx = dx0 / (double)(1L << l), hy = dy0 / (double)(1L << l);
+        for (int side = 0; side < 4; ++side)
+            for (int k = 0; k < n; ++k) {
+                long px, py; /* a point just across the middle of face k */
+                if (side == 0) { px = x0 - 1; py = y0 + k * hw + hw / 2; }
+                else if (side == 1) { px = x1; py = y0 + k * hw + hw / 2; }
+                else if (side == 2) { px = x0 + k * hw + hw / 2; py = y0 - 1; }
+                else { px = x0 + k * hw + hw / 2; py = y1; }
+                int q = forest_lookup(&F, px, py);
+                if (q < 0 || level[q] != l + 1) continue;
+                long hf = hw_of(&F, l + 1);
+                int fside = side ^ 1; /* opposite side of the fine leaf */
+                long start = (side < 2) ? rel(&F, y0 + k * hw, leaf_y0(&F, q)) : rel(&F, x0 + k * hw, leaf_x0(&F, q));
+                int kf = (int)(start / hf);
+                int ci = (side == 0) ? 0 : (side == 1 ? n - 1 : k);
+                int cj = (side == 2) ? 0 : (side == 3 ? n - 1 : k);
+                double h = (side < 2) ? hx : hy;
+                for (int c = 0; c < ncomp; ++c) {
+                    double rc = freg[p * rw + ((long)side * ncomp + c) * n + k];
+                    double rf = 0.5 * (freg[q * rw + ((long)fside * ncomp + c) * n + kf] +
+                                       freg[q * rw + ((long)fside * ncomp + c) * n + kf + 1]);
+                    double d = (side == 1 || side == 3) ? (rc - rf) / h : (rf - rc) / h;
+                    dq[(((long)p * ncomp + c) * n + cj) * n + ci] += d;
+                    used[p * rw + ((long)side * ncomp + c) * n + k] = 1;
+                    used[q * rw + ((long)fside * ncomp + c) * n + kf] = 1;
+                    used[q * rw + ((long)fside * ncomp + c) * n + kf + 1] = 1;
+                }
+            }
+    }
+    for (int p = 0; p < nleaf; ++p)
+        for (int c = 0; c < ncomp; ++c) {
+            double *avg = PL(&L, state + p * pw, c, PL_AVG);
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) avg[IX(&L, i, j)] += dq[(((long)p * ncomp + c) * n + j) * n + i];
+        }
+    for (long e = 0; e < (long)nleaf * rw; ++e)
+        if (used[e]) freg[e] = 0.0;
+    free(dq);
+    free(used);
+    forest_free(&F);
+}
+
+/* Refinement indicator of every patch (Section 3: criteria applied to the
+ * solution on each quadrant).  kind 0: max - min of the interior cell
+ * averages of component `comp` (Section 4.1, Section 4.5.2); kind 1: largest
+ * centred difference quotient |Q_{i+1,j} - Q_{i-1,j}| / (2 dx) or
+ * |Q_{i,j+1} - Q_{i,j-1}| / (2 dy) over cells whose two neighbours are both
+ * interior (Section 4.4).  tag = 1 if indicator >= refine_thr, -1 if
+ * indicator < coarsen_thr, else 0.                                           */
+void orc_tag(int n, int ncomp, int nleaf, const int32_t *level, const double *state, int comp, int kind,
+             double dx0, double dy0, double refine_thr, double coarsen_thr, int8_t *tags, double *ind) {
+    lay_t L = lay_make(n, ncomp);
+    long pw = lay_patch_words(&L);
+    for (int p = 0; p < nleaf; ++p) {
+        const double *a = PLc(&L, state + p * pw, comp, PL_AVG);
+        double v;
+        if (kind == 0) {
+            double mx = -INFINITY, mn = INFINITY;
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    double q = a[IX(&L, i, j)];
+                    if (q > mx) mx = q;
+                    if (q < mn) mn = q;
+                }
+            v = mx - mn;
+        } else {
+            double hx = dx0 / (double)(1L << level[p]), hy = dy0 / (double)(1L << level[p]);
+            v = 0.0;
+            for (int j = 1; j < n - 1; ++j)
+                for (int i = 1; i < n - 1; ++i) {
+                    double gx = fabs(a[IX(&L, i + 1, j)] - a[IX(&L, i - 1, j)]) / (2.0 * hx);
+                    double gy = fabs(a[IX(&L, i, j + 1)] - a[IX(&L, i, j - 1)]) / (2.0 * hy);
+                    if (gx > v) v = gx;
+                    if (gy > v) v = gy;
+                }
+        }
+        if (ind) ind[p] = v;
+        tags[p] = (int8_t)(v >= refine_thr ? 1 : (v < coarsen_thr ? -1 : 0));
+    }
+}
+
+/* Total of every component: sum over patches and interior cells of
+ * Q_{i,j} dx_l dy_l (the conserved quantity of Eq. 2dfv). */
+void orc_mass(int n, int ncomp, int nleaf, const int32_t *level, const double *state, double dx0, double dy0,
+              double *out) {
+    lay_t L = lay_make(n, ncomp);
+    long pw = lay_patch_words(&L);
+    for (int c = 0; c < ncomp; ++c) {
+        double s = 0.0;
+        for (int p = 0; p < nleaf; ++p) {
+            const double *a = PLc(&L, state + p * pw, c, PL_AVG);
+            double area = (dx0 / (double)(1L << level[p])) * (dy0 / (double)(1L << level[p]));
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) s += a[IX(&L, i, j)] * area;
+        }
+        out[c] = s;
+    }
+}
+
+/* Regrid transfer (Section 3.1, cases 1 and 2): every leaf of the new forest
+ * that is also a leaf of the old one is copied; every other new leaf gets its
+ * interior-owned entries from the old leaf covering each entry (coarse ->
+ * fine interpolation if that leaf is coarser, fine -> coarse averaging if it
+ * is finer).  Ghost entries of new leaves are left for the next exchange.  */
+void orc_transfer(int n, int ncomp, int B, int lmax, int nold, const int32_t *olevel, const int32_t *oix,
+                  const int32_t *oiy, const double *old_state, int nnew, const int32_t *nlevel, const int32_t *nix,
+                  const int32_t *niy, double *new_state) {
+    forest_t F;
+    lay_t L = lay_make(n, ncomp);
+    long pw = lay_patch_words(&L);
+    if (forest_init(&F, n, ncomp, nold, olevel, oix, oiy, B, lmax) != 0) { forest_free(&F); return; }
+    for (int p = 0; p < nnew; ++p) {
+        long side = (long)B << nlevel[p];
+        int same = F.map[nlevel[p]][(long)niy[p] * side + nix[p]];
+        double *dst = new_state + p * pw;
+        if (same >= 0) { memcpy(dst, old_state + same * pw, sizeof(double) * pw); continue; }
+        for (long e = 0; e < pw; ++e) dst[e] = 0.0;
+        long hw = hw_of(&F, nlevel[p]);
+        long x0 = (long)nix[p] * n * hw, y0 = (long)niy[p] * n * hw;
+        for (int k = 0; k < 4; ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    long x = x0 + (long)i * hw + ((k == PL_AVG || k == PL_YMID) ? hw / 2 : 0);
+                    long y = y0 + (long)j * hw + ((k == PL_AVG || k == PL_XMID) ? hw / 2 : 0);
+                    int q = entry_owner(&F, k, x, y);
+                    if (q < 0) continue;
+                    for (int c = 0; c < ncomp; ++c)
+                        PL(&L, dst, c, k)[IX(&L, i, j)] = transfer_value(&F, old_state, nlevel[p], q, c, k, x, y);
+                }
+    }
+    forest_free(&F);
+}

@@ -338,3 +338,76 @@ def periodic_state(grid: UniformGrid, funcs, nq: int = 2, dtype=np.float64) -> n
                                                   strides=(n * s0, n * s1, s0, s1))
             lat[:, :, c, k] = win
     return st
+
+
+# ------------------------------------------------------------ forest inputs
+def _region_has_level(leafset, l, ix, iy, lmin_needed, lmax):
+    """True if the level-l region (ix, iy) holds a leaf of level >= lmin_needed."""
+    for lv in range(max(lmin_needed, l + 1), lmax + 1):
+        s = 1 << (lv - l)
+        for dy in range(s):
+            for dx in range(s):
+                if (lv, ix * s + dx, iy * s + dy) in leafset:
+                    return True
+    return False
+
+
+def balanced_forest(B: int, lmin: int, lmax: int, refine) -> list:
+    """Leaves (level, ix, iy) of a periodic forest over a B x B brick.
+
+    Starts from all level-lmin patches, refines every leaf for which
+    refine(level, ix, iy) is true (up to lmax), then enforces the 2:1 balance
+    across faces and corners (a leaf whose neighbour region at its own level
+    holds a leaf two or more levels finer is split).  Leaves are returned
+    sorted by level, then row-major.  Input generator for tests and benchmarks.
+    """
+    leaves = {(lmin, ix, iy) for iy in range(B << lmin) for ix in range(B << lmin)}
+    changed = True
+    while changed:
+        changed = False
+        for (l, ix, iy) in sorted(leaves):
+            if l < lmax and refine(l, ix, iy):
+                leaves.remove((l, ix, iy))
+                leaves |= {(l + 1, 2 * ix + a, 2 * iy + b) for a in (0, 1) for b in (0, 1)}
+                changed = True
+    changed = True
+    while changed:
+        changed = False
+        for (l, ix, iy) in sorted(leaves):
+            side = B << l
+            bad = False
+            for sy in (-1, 0, 1):
+                for sx in (-1, 0, 1):
+                    if sx == 0 and sy == 0:
+                        continue
+                    if _region_has_level(leaves, l, (ix + sx) % side, (iy + sy) % side, l + 2, lmax):
+                        bad = True
+            if bad:
+                leaves.remove((l, ix, iy))
+                leaves |= {(l + 1, 2 * ix + a, 2 * iy + b) for a in (0, 1) for b in (0, 1)}
+                changed = True
+    return sorted(leaves, key=lambda t: (t[0], t[2], t[1]))
+
+
+def diagonal_refine(width: float = 0.0):
+    """Refine patches that touch the diagonal y = x of the unit brick."""
+    def pred(l, ix, iy):
+        return abs(ix - iy) <= 0 + width
+    return pred
+
+
+def forest_state(n: int, ncomp: int, B: int, lmax: int, leaves, funcs, lo=(0.0, 0.0), hi=(1.0, 1.0),
+                 nq: int = 3, dtype=np.float64) -> np.ndarray:
+    """Pack the initial data of every leaf (all entries, ghosts from the
+    periodically wrapped functions)."""
+    lay = Layout(n, ncomp)
+    out = np.empty((len(leaves), ncomp, 4, lay.plane))
+    for k, (l, ix, iy) in enumerate(leaves):
+        side = B << l
+        w = (hi[0] - lo[0]) / side
+        h = (hi[1] - lo[1]) / side
+        g1 = UniformGrid(lay, 1, 1, (lo[0] + ix * w, lo[1] + iy * h), (lo[0] + (ix + 1) * w, lo[1] + (iy + 1) * h))
+        lx, ly = hi[0] - lo[0], hi[1] - lo[1]
+        wrapped = [lambda x, y, f=f: f(lo[0] + np.mod(x - lo[0], lx), lo[1] + np.mod(y - lo[1], ly)) for f in funcs]
+        out[k] = g1.state(wrapped, nq=nq, ghosts=True, periodic=False)[0]
+    return out.astype(dtype)
