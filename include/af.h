@@ -120,8 +120,11 @@ af_status af_build_step_work(const af_config *cfg, int32_t npatch, const int32_t
  * d_work     device copy of the af_build_step_work output (nwork entries)
  * d_in       state at t^n (npatch_total patches, layout above)
  * d_out      receives the new averages and point values of every advanced
- *            cell; entries not advanced are left untouched.  Must not
- *            overlap d_in (AF_ERR_ARG).
+ *            cell.  A patch that advances its first ghost layer (one with a
+ *            non-same-level neighbour) is written whole: its other entries
+ *            are copied from d_in (same-level directions: from the
+ *            neighbours).  For other patches entries not advanced are left
+ *            untouched.  Must not be the same buffer as d_in (AF_ERR_ARG).
  * dt0, dx0, dy0   time step and mesh widths of level 0 (level l uses /2^l).
  *            AF_ERR_CFL if max(|a| dt/dx, |b| dt/dy) > 1 (Eq. cfl-adv) or
  *            max(c dt/dx, c dt/dy) > 1/2 (Eq. cfl-acoustics).
@@ -132,6 +135,104 @@ af_status af_build_step_work(const af_config *cfg, int32_t npatch, const int32_t
 af_status af_patch_step(const af_config *cfg, int32_t nwork, const af_work *d_work,
                         const void *d_in, void *d_out, double dt0, double dx0, double dy0,
                         double *d_flux_reg, void *stream);
+
+
+/* ======================================================================
+ * Adaptive mesh refinement (Section 3): a forest of quadtrees over a B x B
+ * brick of level-0 patches, periodic in x and y.  Every leaf is one patch
+ * (N x N cells) of the state array; level l has mesh width dx0 / 2^l.
+ * ====================================================================== */
+
+#define AF_MAX_LEVEL 15
+
+/* Forest description.  The struct itself lives in host memory; the arrays it
+ * points to are DEVICE arrays owned by the caller. */
+typedef struct {
+    int32_t nleaf;          /* leaves = patches of the state array, in this order */
+    int32_t B;              /* level-0 patches per side of the periodic brick, >= 1 */
+    int32_t lmax;           /* finest level that may occur, 0 .. AF_MAX_LEVEL */
+    int32_t pad_;
+    const int32_t *d_level; /* [nleaf] level of each leaf */
+    const int32_t *d_ix;    /* [nleaf] column of the leaf among the B << level of its level */
+    const int32_t *d_iy;    /* [nleaf] row */
+    const int32_t *d_map;   /* per level l: (B << l)^2 entries starting at
+                               af_forest_map_offset(B, l), row-major; entry
+                               (iy, ix) is the leaf index of region (l, ix, iy)
+                               if that region is a leaf, else -1 */
+} af_forest;
+
+/* Offset of level l in d_map: sum over m < l of (B << m)^2. */
+int64_t af_forest_map_offset(int32_t B, int32_t level);
+
+/* Fill h_map (af_forest_map_offset(B, lmax + 1) entries, host memory) from
+ * host copies of the leaf arrays.  AF_ERR_ARG on an out-of-range leaf or two
+ * leaves claiming one region. */
+af_status af_forest_build_map(int32_t nleaf, int32_t B, int32_t lmax, const int32_t *h_level,
+                              const int32_t *h_ix, const int32_t *h_iy, int32_t *h_map);
+
+/* Flags of af_fill_ghosts. */
+#define AF_FILL_SAME_LEVEL_ONLY 1 /* copy from same-level leaves only */
+#define AF_FILL_ALL_PATCHES 2     /* also fill leaves whose 8 neighbours are all same-level */
+
+/* Ghost exchange (Section 3.1 cases 1-3, Section 3.2 "whenever two levels are
+ * time synchronized"), in place on d_state.
+ * Ownership: a cell average belongs to the leaf covering the cell centre; a
+ * point value belongs to the finest leaf touching the point (ties: the leaf
+ * above-right, above-left, below-right, below-left of it), so values on a
+ * coarse-fine face come from the finer leaf.  Every entry of a destination
+ * leaf (level bit set in dst_levels) whose owner is another leaf with its
+ * level bit set in src_levels is replaced: copy from a same-level owner;
+ * from a finer owner the mean of the four fine averages, or the coinciding
+ * fine vertex; from a coarser owner the value of its reconstruction, or for
+ * an average Simpson's rule over the fine cell (exact).  Three passes run in
+ * order -- finer owners, same-level owners, coarser owners -- each seeing the
+ * previous one's results.  Unless AF_FILL_ALL_PATCHES is set, leaves whose
+ * eight neighbours are all same-level leaves are skipped (af_patch_step
+ * reads their halo from the neighbours directly). */
+af_status af_fill_ghosts(const af_config *cfg, const af_forest *forest, uint32_t dst_levels,
+                         uint32_t src_levels, int32_t flags, void *d_state, void *stream);
+
+/* Regrid transfer (Section 3.1 cases 1 and 2): every leaf of new_forest that
+ * is a leaf of old_forest is copied whole from d_old; every other new leaf
+ * gets its interior-owned entries from the owners in old_forest (coarse ->
+ * fine interpolation, fine -> coarse averaging, one level of coarsening at
+ * most) and zeros in its ghost ring.  d_old and d_new must not overlap. */
+af_status af_transfer(const af_config *cfg, const af_forest *old_forest, const void *d_old,
+                      const af_forest *new_forest, void *d_new, void *stream);
+
+/* Conservative fix (Section 3.2, Berger-Colella).  For every leaf C whose
+ * level l and l+1 are both set in sync_levels and every face k of C whose
+ * neighbour across is a level-(l+1) leaf F, the average of the coarse cell at
+ * that face is corrected so that it has used the fine fluxes:
+ *   right/top face:  dQ = (R_C[k] - (R_F[a] + R_F[a+1]) / 2) / h_C
+ *   left/bottom face: dQ = ((R_F[a] + R_F[a+1]) / 2 - R_C[k]) / h_C
+ * with R the flux registers of af_patch_step (sum of dt * F since they were
+ * last consumed) and h_C = dx0 / 2^l (x faces) or dy0 / 2^l (y faces).
+ * Consumed register entries (coarse and fine) are reset to zero. */
+af_status af_reflux(const af_config *cfg, const af_forest *forest, uint32_t sync_levels, double dx0,
+                    double dy0, double *d_flux_reg, void *d_state, void *stream);
+
+/* Refinement indicator per leaf (Section 3: "we apply coarsening and
+ * refinement criteria to the solution on each quadrant").
+ * kind 0: max - min of the interior averages of component comp (Sections 4.1,
+ * 4.5.2); kind 1: largest |Q_{i+1,j} - Q_{i-1,j}| / (2 dx) or
+ * |Q_{i,j+1} - Q_{i,j-1}| / (2 dy) over interior cells whose two neighbours
+ * are interior (Section 4.4).  d_tags[p] = 1 if indicator >= refine_thr, -1 if
+ * indicator < coarsen_thr, else 0.  d_indicator (FP64) may be NULL. */
+af_status af_tag(const af_config *cfg, const af_forest *forest, const void *d_state, int32_t comp,
+                 int32_t kind, double dx0, double dy0, double refine_thr, double coarsen_thr, int8_t *d_tags,
+                 double *d_indicator, void *stream);
+
+/* Bytes of device scratch af_mass needs for nleaf leaves and ncomp components. */
+int64_t af_mass_scratch_bytes(int32_t nleaf, int32_t ncomp);
+
+/* Total of every component, sum over leaves and interior cells of
+ * Q_{i,j} dx_l dy_l, in FP64 whatever the state precision (the conserved
+ * quantity of Eq. 2dfv).  Deterministic two-pass reduction: per-block partial
+ * sums go to d_scratch (af_mass_scratch_bytes, 8-byte aligned), the final sums
+ * to d_mass[ncomp]. */
+af_status af_mass(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0, double dy0,
+                  void *d_scratch, double *d_mass, void *stream);
 
 #ifdef __cplusplus
 }

@@ -545,15 +545,21 @@ static long rel(const forest_t *F, long x, long x0) {
     return d;
 }
 
+static int node_owner(const forest_t *F, long x, long y);
+static double leaf_entry(const forest_t *F, const double *state, int q, int c, int plane, long x, long y);
+
 /* Value of the reconstruction (Eq. poly) of leaf q, component c, at (x, y).
  * The cell is found with the half-open rule, clamped into q's interior;
  * the reconstruction is continuous, so a point on a cell face may use
- * either neighbour. */
+ * either neighbour.  Every point value of the cell is its owner's (see
+ * node_owner), so nodes on q's boundary lines are read from the leaf that
+ * owns them. */
 static double leaf_eval(const forest_t *F, const double *state, int q, int c, long x, long y) {
     lay_t L = lay_make(F->n, F->ncomp);
     const double *patch = state + (long)q * lay_patch_words(&L);
     long hw = hw_of(F, F->level[q]);
-    long dx = rel(F, x, leaf_x0(F, q)), dy = rel(F, y, leaf_y0(F, q));
+    long x0 = leaf_x0(F, q), y0 = leaf_y0(F, q);
+    long dx = rel(F, x, x0), dy = rel(F, y, y0);
     long ci = dx >= 0 ? dx / hw : -((-dx + hw - 1) / hw);
     long cj = dy >= 0 ? dy / hw : -((-dy + hw - 1) / hw);
     if (ci < 0) ci = 0;
@@ -563,7 +569,21 @@ static double leaf_eval(const forest_t *F, const double *state, int q, int c, lo
     double xi = 2.0 * (double)(dx - ci * hw) / (double)hw - 1.0;
     double eta = 2.0 * (double)(dy - cj * hw) / (double)hw - 1.0;
     double qn[3][3];
-    cell_nodal(&L, patch, c, (int)ci, (int)cj, qn);
+    /* nodes at reference (a-1, b-1): positions x0 + ci hw + a hw/2 */
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+            if (a == 1 && b == 1) continue;
+            long px = x0 + ci * hw + a * hw / 2, py = y0 + cj * hw + b * hw / 2;
+            int o = node_owner(F, px, py);
+            int plane = (a == 1) ? PL_YMID : (b == 1 ? PL_XMID : PL_CORNER);
+            if (o >= 0 && F->level[o] > F->level[q]) plane = PL_CORNER; /* finer owner: its vertex */
+            qn[b][a] = leaf_entry(F, state, o >= 0 ? o : q, c, plane, px, py);
+        }
+    double rest = 0.0;
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a)
+            if (!(a == 1 && b == 1)) rest += SIMPSON_W[a] * SIMPSON_W[b] * qn[b][a];
+    qn[1][1] = (PLc(&L, patch, c, PL_AVG)[IX(&L, (int)ci, (int)cj)] - rest) / (SIMPSON_W[1] * SIMPSON_W[1]);
     return recon_deriv(qn, xi, eta, 0, 0);
 }
 
@@ -645,8 +665,12 @@ static int entry_owner(const forest_t *F, int plane, long x, long y) {
  * every step of a level).  This covers the ghost ring and the nodes on a
  * leaf's left / bottom face that a finer neighbour owns.  Entries the step
  * never reads (the average and bottom-mid of the far column, the average and
- * left-mid of the far row) are skipped.  Results are written to `out`, a copy
- * of `in` on entry.                                                         */
+ * left-mid of the far row) are skipped.
+ * The exchange runs in three passes, each reading the result of the one
+ * before: entries owned by finer leaves, then by same-level leaves, then by
+ * coarser leaves; so a coarse reconstruction used for interpolation already
+ * carries the fine values on its coarse-fine faces.  Results are written to
+ * `out` (a copy of `in` on entry).                                          */
 void orc_fill_amr(int n, int ncomp, int nleaf, const int32_t *level, const int32_t *ix, const int32_t *iy,
                   int B, int lmax, uint32_t dst_levels, uint32_t src_levels, int same_only, const double *in,
                   double *out) {
@@ -655,26 +679,33 @@ void orc_fill_amr(int n, int ncomp, int nleaf, const int32_t *level, const int32
     long pw = lay_patch_words(&L);
     memcpy(out, in, sizeof(double) * pw * nleaf);
     if (forest_init(&F, n, ncomp, nleaf, level, ix, iy, B, lmax) != 0) { forest_free(&F); return; }
-    for (int p = 0; p < nleaf; ++p) {
-        int lp = level[p];
-        if (!((dst_levels >> lp) & 1u)) continue;
-        for (int k = 0; k < 4; ++k)
-            for (int j = -NG; j <= n + NG; ++j)
-                for (int i = -NG; i <= n + NG; ++i) {
-                    if (i > 0 && i < n && j > 0 && j < n) continue; /* strictly inside: own */
-                    if (i == n + NG && (k == PL_AVG || k == PL_YMID)) continue;
-                    if (j == n + NG && (k == PL_AVG || k == PL_XMID)) continue;
-                    long x, y;
-                    entry_pos(&F, p, k, i, j, &x, &y);
-                    int q = entry_owner(&F, k, x, y);
-                    if (q < 0 || q == p) continue;
-                    int lq = level[q];
-                    if (!((src_levels >> lq) & 1u)) continue;
-                    if (same_only && lq != lp) continue;
-                    for (int c = 0; c < ncomp; ++c)
-                        PL(&L, out + p * pw, c, k)[IX(&L, i, j)] = transfer_value(&F, in, lp, q, c, k, x, y);
-                }
+    double *prev = (double *)malloc(sizeof(double) * pw * nleaf);
+    for (int pass = 0; pass < 3; ++pass) { /* 0: finer owner, 1: same level, 2: coarser */
+        memcpy(prev, out, sizeof(double) * pw * nleaf);
+        for (int p = 0; p < nleaf; ++p) {
+            int lp = level[p];
+            if (!((dst_levels >> lp) & 1u)) continue;
+            for (int k = 0; k < 4; ++k)
+                for (int j = -NG; j <= n + NG; ++j)
+                    for (int i = -NG; i <= n + NG; ++i) {
+                        if (i > 0 && i < n && j > 0 && j < n) continue; /* strictly inside: own */
+                        if (i == n + NG && (k == PL_AVG || k == PL_YMID)) continue;
+                        if (j == n + NG && (k == PL_AVG || k == PL_XMID)) continue;
+                        long x, y;
+                        entry_pos(&F, p, k, i, j, &x, &y);
+                        int q = entry_owner(&F, k, x, y);
+                        if (q < 0 || q == p) continue;
+                        int lq = level[q];
+                        int rel_pass = lq > lp ? 0 : (lq == lp ? 1 : 2);
+                        if (rel_pass != pass) continue;
+                        if (!((src_levels >> lq) & 1u)) continue;
+                        if (same_only && lq != lp) continue;
+                        for (int c = 0; c < ncomp; ++c)
+                            PL(&L, out + p * pw, c, k)[IX(&L, i, j)] = transfer_value(&F, prev, lp, q, c, k, x, y);
+                    }
+        }
     }
+    free(prev);
     forest_free(&F);
 }
 

@@ -142,3 +142,77 @@ def patch_step(cfg: Config, work, nwork: int, state_in, state_out, dt0: float, d
     st = lib().af_patch_step(C.byref(cfg), int(nwork), ptr(work), ptr(state_in), ptr(state_out),
                              float(dt0), float(dx0), float(dy0), ptr(flux_reg), stream_handle(stream))
     _check(st, "af_patch_step")
+
+
+# ------------------------------------------------------------------- forest
+FILL_SAME_LEVEL_ONLY = 1
+FILL_ALL_PATCHES = 2
+
+
+class ForestC(C.Structure):
+    _fields_ = [("nleaf", C.c_int32), ("B", C.c_int32), ("lmax", C.c_int32), ("pad_", C.c_int32),
+                ("d_level", C.c_void_p), ("d_ix", C.c_void_p), ("d_iy", C.c_void_p), ("d_map", C.c_void_p)]
+
+
+_FP = C.POINTER(ForestC)
+_EXTRA += [
+    ("af_forest_map_offset", C.c_int64, [C.c_int32, C.c_int32]),
+    ("af_forest_build_map", C.c_int, [C.c_int32, C.c_int32, C.c_int32, _IP, _IP, _IP, _IP]),
+    ("af_fill_ghosts", C.c_int, [C.POINTER(Config), _FP, C.c_uint32, C.c_uint32, C.c_int32, _VP, _VP]),
+    ("af_transfer", C.c_int, [C.POINTER(Config), _FP, _VP, _FP, _VP, _VP]),
+    ("af_reflux", C.c_int, [C.POINTER(Config), _FP, C.c_uint32, C.c_double, C.c_double, _VP, _VP, _VP]),
+    ("af_tag", C.c_int, [C.POINTER(Config), _FP, _VP, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                         C.c_double, _VP, _VP, _VP]),
+    ("af_mass_scratch_bytes", C.c_int64, [C.c_int32, C.c_int32]),
+    ("af_mass", C.c_int, [C.POINTER(Config), _FP, _VP, C.c_double, C.c_double, _VP, _VP, _VP]),
+]
+if _lib is not None:
+    _register_more(_lib)
+
+
+def forest_map_offset(B: int, level: int) -> int:
+    return int(lib().af_forest_map_offset(B, level))
+
+
+def forest_build_map(B: int, lmax: int, level, ix, iy) -> np.ndarray:
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    out = np.empty(forest_map_offset(B, lmax + 1), dtype=np.int32)
+    ip = lambda a: a.ctypes.data_as(_IP)
+    _check(lib().af_forest_build_map(len(level), B, lmax, ip(level), ip(ix), ip(iy), ip(out)), "af_forest_build_map")
+    return out
+
+
+def forest_struct(nleaf: int, B: int, lmax: int, d_level, d_ix, d_iy, d_map) -> ForestC:
+    return ForestC(nleaf, B, lmax, 0, ptr(d_level), ptr(d_ix), ptr(d_iy), ptr(d_map))
+
+
+def fill_ghosts(cfg: Config, forest: ForestC, dst_levels: int, src_levels: int, flags: int, state, stream=None):
+    _check(lib().af_fill_ghosts(C.byref(cfg), C.byref(forest), dst_levels, src_levels, flags, ptr(state),
+                                stream_handle(stream)), "af_fill_ghosts")
+
+
+def transfer(cfg: Config, old: ForestC, d_old, new: ForestC, d_new, stream=None):
+    _check(lib().af_transfer(C.byref(cfg), C.byref(old), ptr(d_old), C.byref(new), ptr(d_new),
+                             stream_handle(stream)), "af_transfer")
+
+
+def reflux(cfg: Config, forest: ForestC, sync_levels: int, dx0: float, dy0: float, flux_reg, state, stream=None):
+    _check(lib().af_reflux(C.byref(cfg), C.byref(forest), sync_levels, dx0, dy0, ptr(flux_reg), ptr(state),
+                           stream_handle(stream)), "af_reflux")
+
+
+def tag(cfg: Config, forest: ForestC, state, comp: int, kind: int, dx0: float, dy0: float, refine_thr: float,
+        coarsen_thr: float, tags, indicator=None, stream=None):
+    _check(lib().af_tag(C.byref(cfg), C.byref(forest), ptr(state), comp, kind, dx0, dy0, refine_thr, coarsen_thr,
+                        ptr(tags), ptr(indicator), stream_handle(stream)), "af_tag")
+
+
+def mass_scratch_bytes(nleaf: int, ncomp: int) -> int:
+    return int(lib().af_mass_scratch_bytes(nleaf, ncomp))
+
+
+def mass(cfg: Config, forest: ForestC, state, dx0: float, dy0: float, scratch, out, stream=None):
+    _check(lib().af_mass(C.byref(cfg), C.byref(forest), ptr(state), dx0, dy0, ptr(scratch), ptr(out),
+                         stream_handle(stream)), "af_mass")

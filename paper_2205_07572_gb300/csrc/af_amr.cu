@@ -1,0 +1,567 @@
+// Adaptive-mesh kernels of libaf.so (Section 3 of arXiv 2205.07572):
+// ghost exchange, regrid transfer, conservative fix, tagging, mass totals.
+//
+// Positions are exact integers: one unit is half the cell width of level
+// lmax, so a level-l cell is 2^(lmax-l+1) units wide and every node, cell
+// centre and Simpson point is a lattice point of that unit.  The forest is
+// located through per-level region maps (af_forest.d_map), which stay in L2.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "af_internal.h"
+
+namespace af {
+namespace {
+
+struct DevForest {
+    int nleaf, B, lmax, n;
+    const int32_t *level, *ix, *iy, *map;
+    long long D;  // domain width in units
+};
+
+DevForest make_dev(const af_forest &f, int n) {
+    DevForest d;
+    d.nleaf = f.nleaf;
+    d.B = f.B;
+    d.lmax = f.lmax;
+    d.n = n;
+    d.level = f.d_level;
+    d.ix = f.d_ix;
+    d.iy = f.d_iy;
+    d.map = f.d_map;
+    d.D = (long long)f.B * n * (2LL << f.lmax);
+    return d;
+}
+
+__host__ __device__ inline long long map_offset(int B, int l) {
+    // sum_{m<l} (B << m)^2 = B^2 (4^l - 1) / 3
+    return (long long)B * B * (((1LL << (2 * l)) - 1) / 3);
+}
+
+__device__ __forceinline__ long long hwid(const DevForest &F, int l) { return 2LL << (F.lmax - l); }
+
+__device__ __forceinline__ long long wrapd(const DevForest &F, long long x) {
+    long long r = x % F.D;
+    return r < 0 ? r + F.D : r;
+}
+
+// Leaf whose half-open extent contains (x, y).
+__device__ int lookup(const DevForest &F, long long x, long long y) {
+    x = wrapd(F, x);
+    y = wrapd(F, y);
+    for (int l = F.lmax; l >= 0; --l) {
+        const long long pw = (long long)F.n * hwid(F, l);
+        const long long side = (long long)F.B << l;
+        const int q = __ldg(F.map + map_offset(F.B, l) + (y / pw) * side + (x / pw));
+        if (q >= 0) return q < F.nleaf ? q : -1;
+    }
+    return -1;
+}
+
+// Owner of a point value: the finest leaf touching the point, ties in the
+// order above-right, above-left, below-right, below-left.
+__device__ int node_owner(const DevForest &F, long long x, long long y) {
+    int best = lookup(F, x, y);
+    int bl = best >= 0 ? __ldg(F.level + best) : -1;
+    const long long dx[3] = {-1, 0, -1}, dy[3] = {0, -1, -1};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = lookup(F, x + dx[k], y + dy[k]);
+        if (q >= 0) {
+            const int lq = __ldg(F.level + q);
+            if (lq > bl) {
+                best = q;
+                bl = lq;
+            }
+        }
+    }
+    return best;
+}
+
+__device__ __forceinline__ int entry_owner(const DevForest &F, int plane, long long x, long long y) {
+    return plane == kAvg ? lookup(F, x, y) : node_owner(F, x, y);
+}
+
+__device__ __forceinline__ long long leaf_x0(const DevForest &F, int q) {
+    return (long long)__ldg(F.ix + q) * F.n * hwid(F, __ldg(F.level + q));
+}
+__device__ __forceinline__ long long leaf_y0(const DevForest &F, int q) {
+    return (long long)__ldg(F.iy + q) * F.n * hwid(F, __ldg(F.level + q));
+}
+
+// x - x0 unwrapped across the periodic box
+__device__ __forceinline__ long long reld(const DevForest &F, long long x, long long x0) {
+    long long d = wrapd(F, x - x0);
+    return d > F.D / 2 ? d - F.D : d;
+}
+
+template <typename T>
+struct StateView {
+    T *base;
+    int64_t plane;  // plane stride
+    int ncomp, W;   // components, lattice width
+    __device__ __forceinline__ T *at(int q, int c, int k, int i, int j) const {
+        return base + ((int64_t)q * ncomp * kPlanes + c * kPlanes + k) * plane + (int64_t)(j + kGhost) * W +
+               (i + kGhost);
+    }
+};
+
+// Lattice indices (i, j) of point (x, y) in plane k of leaf q.
+__device__ __forceinline__ void lattice_of(const DevForest &F, int q, int k, long long x, long long y, int &i,
+                                           int &j) {
+    const long long hw = hwid(F, __ldg(F.level + q));
+    long long dx = reld(F, x, leaf_x0(F, q)), dy = reld(F, y, leaf_y0(F, q));
+    if (k == kAvg || k == kYmid) dx -= hw / 2;
+    if (k == kAvg || k == kXmid) dy -= hw / 2;
+    i = (int)(dx >= 0 ? dx / hw : -((-dx + hw - 1) / hw));
+    j = (int)(dy >= 0 ? dy / hw : -((-dy + hw - 1) / hw));
+    // owners are always within two cells of the lattice; clamp defensively
+    const int lo = -kGhost, hi = F.n + kGhost;
+    i = i < lo ? lo : (i > hi ? hi : i);
+    j = j < lo ? lo : (j > hi ? hi : j);
+}
+
+// Value of the reconstruction (Eq. poly) of leaf q, component c, at (x, y):
+// tensor Lagrange interpolant on {-1,0,1}^2 whose centre value follows from
+// the average, (9/4) Q - (1/16) sum(corners) - (1/4) sum(edge midpoints).
+template <typename T>
+__device__ double recon_at(const DevForest &F, const StateView<T> &S, int q, int c, long long x, long long y) {
+    const long long hw = hwid(F, __ldg(F.level + q));
+    const long long dx = reld(F, x, leaf_x0(F, q)), dy = reld(F, y, leaf_y0(F, q));
+    long long ci = dx >= 0 ? dx / hw : -1, cj = dy >= 0 ? dy / hw : -1;
+    ci = ci < 0 ? 0 : (ci > F.n - 1 ? F.n - 1 : ci);
+    cj = cj < 0 ? 0 : (cj > F.n - 1 ? F.n - 1 : cj);
+    const double xi = 2.0 * (double)(dx - ci * hw) / (double)hw - 1.0;
+    const double eta = 2.0 * (double)(dy - cj * hw) / (double)hw - 1.0;
+    const int i = (int)ci, j = (int)cj;
+    // Point values on the leaf's boundary lines are read from their owner:
+    // a leaf whose neighbours are all same-level does not keep the copies in
+    // its ghost ring current (its step reads the neighbours directly).
+    auto node = [&](int k, int ii, int jj) -> double {
+        if (ii > 0 && ii < F.n && jj > 0 && jj < F.n) return *S.at(q, c, k, ii, jj);
+        long long nx, ny;
+        const long long x0 = leaf_x0(F, q), y0 = leaf_y0(F, q);
+        nx = x0 + (long long)ii * hw + (k == kYmid ? hw / 2 : 0);
+        ny = y0 + (long long)jj * hw + (k == kXmid ? hw / 2 : 0);
+        const int o = node_owner(F, nx, ny);
+        if (o < 0 || o == q) return *S.at(q, c, k, ii, jj);
+        const int lo = __ldg(F.level + o);
+        int oi, oj;
+        lattice_of(F, o, lo == __ldg(F.level + q) ? k : kCorner, nx, ny, oi, oj);
+        return *S.at(o, c, lo == __ldg(F.level + q) ? k : kCorner, oi, oj);
+    };
+    const double c00 = node(kCorner, i, j), c10 = node(kCorner, i + 1, j);
+    const double c01 = node(kCorner, i, j + 1), c11 = node(kCorner, i + 1, j + 1);
+    const double xl = node(kXmid, i, j), xr = node(kXmid, i + 1, j);
+    const double yb = node(kYmid, i, j), yt = node(kYmid, i, j + 1);
+    const double avg = *S.at(q, c, kAvg, i, j);
+    const double cen = 2.25 * avg - 0.0625 * (c00 + c10 + c01 + c11) - 0.25 * (xl + xr + yb + yt);
+    const double lx0 = 0.5 * xi * (xi - 1.0), lx1 = 1.0 - xi * xi, lx2 = 0.5 * xi * (xi + 1.0);
+    const double ly0 = 0.5 * eta * (eta - 1.0), ly1 = 1.0 - eta * eta, ly2 = 0.5 * eta * (eta + 1.0);
+    return ly0 * (lx0 * c00 + lx1 * yb + lx2 * c10) + ly1 * (lx0 * xl + lx1 * cen + lx2 * xr) +
+           ly2 * (lx0 * c01 + lx1 * yt + lx2 * c11);
+}
+
+// Value for an entry of plane k of a destination at level lp from owner q
+// (Section 3.1: copy, fine -> coarse, coarse -> fine).
+template <typename T>
+__device__ double transfer(const DevForest &F, const StateView<T> &S, int lp, int q, int c, int k, long long x,
+                           long long y) {
+    const int lq = __ldg(F.level + q);
+    int i, j;
+    if (lq == lp) {
+        lattice_of(F, q, k, x, y, i, j);
+        return *S.at(q, c, k, i, j);
+    }
+    if (lq > lp) {
+        if (k == kAvg) {
+            const long long h = hwid(F, lq) / 2;
+            double s = 0.0;
+#pragma unroll
+            for (int b = -1; b <= 1; b += 2)
+#pragma unroll
+                for (int a = -1; a <= 1; a += 2) {
+                    lattice_of(F, q, kAvg, x + a * h, y + b * h, i, j);
+                    s += *S.at(q, c, kAvg, i, j);
+                }
+            return 0.25 * s;
+        }
+        lattice_of(F, q, kCorner, x, y, i, j);
+        return *S.at(q, c, kCorner, i, j);
+    }
+    if (k != kAvg) return recon_at<T>(F, S, q, c, x, y);
+    // Simpson's rule over the destination cell (half width h), exact for the
+    // coarse biquadratic
+    const long long h = hwid(F, lp) / 2;
+    const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+    double s = 0.0;
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) s += w[a] * w[b] * recon_at<T>(F, S, q, c, x + (a - 1) * h, y + (b - 1) * h);
+    return s;
+}
+
+__device__ __forceinline__ void entry_xy(const DevForest &F, int p, int k, int i, int j, long long &x, long long &y) {
+    const long long hw = hwid(F, __ldg(F.level + p));
+    x = leaf_x0(F, p) + (long long)i * hw + ((k == kAvg || k == kYmid) ? hw / 2 : 0);
+    y = leaf_y0(F, p) + (long long)j * hw + ((k == kAvg || k == kXmid) ? hw / 2 : 0);
+}
+
+// True if some neighbour region of leaf p at its own level is not a leaf.
+__device__ bool has_other_level_neighbour(const DevForest &F, int p) {
+    const int l = __ldg(F.level + p);
+    const long long side = (long long)F.B << l;
+    const long long px = __ldg(F.ix + p), py = __ldg(F.iy + p);
+    for (int sy = -1; sy <= 1; ++sy)
+        for (int sx = -1; sx <= 1; ++sx) {
+            if (sx == 0 && sy == 0) continue;
+            const long long nx = ((px + sx) % side + side) % side, ny = ((py + sy) % side + side) % side;
+            if (__ldg(F.map + map_offset(F.B, l) + ny * side + nx) < 0) return true;
+        }
+    return false;
+}
+
+// One pass of the exchange: pass 0 = finer owners, 1 = same level, 2 = coarser.
+template <typename T>
+__global__ void fill_kernel(DevForest F, StateView<T> S, uint32_t dst, uint32_t src, int flags, int pass) {
+    const int p = blockIdx.x;
+    const int lp = __ldg(F.level + p);
+    if (!((dst >> lp) & 1u)) return;
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = !(flags & AF_FILL_ALL_PATCHES) && !has_other_level_neighbour(F, p);
+    __syncthreads();
+    if (s_skip) return;
+    const int n = F.n, W = n + 2 * kGhost + 1;
+    const int total = kPlanes * W * W;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int k = e / (W * W), r = e - k * W * W;
+        const int j = r / W - kGhost, i = r % W - kGhost;
+        if (i > 0 && i < n && j > 0 && j < n) continue;  // strictly inside: the leaf's own
+        if (i == n + kGhost && (k == kAvg || k == kYmid)) continue;  // never read by the step
+        if (j == n + kGhost && (k == kAvg || k == kXmid)) continue;
+        long long x, y;
+        entry_xy(F, p, k, i, j, x, y);
+        const int q = entry_owner(F, k, x, y);
+        if (q < 0 || q == p) continue;
+        const int lq = __ldg(F.level + q);
+        const int rel_pass = lq > lp ? 0 : (lq == lp ? 1 : 2);
+        if (rel_pass != pass || !((src >> lq) & 1u)) continue;
+        if ((flags & AF_FILL_SAME_LEVEL_ONLY) && lq != lp) continue;
+        for (int c = 0; c < S.ncomp; ++c) *S.at(p, c, k, i, j) = (T)transfer<T>(F, S, lp, q, c, k, x, y);
+    }
+}
+
+template <typename T>
+__global__ void transfer_kernel(DevForest Fo, StateView<T> So, DevForest Fn, StateView<T> Sn) {
+    const int p = blockIdx.x;
+    const int l = __ldg(Fn.level + p), px = __ldg(Fn.ix + p), py = __ldg(Fn.iy + p);
+    const int64_t words = (int64_t)Sn.ncomp * kPlanes * Sn.plane;
+    T *dst = Sn.base + (int64_t)p * words;
+    int same = -1;
+    if (l <= Fo.lmax) {
+        const long long side = (long long)Fo.B << l;
+        same = __ldg(Fo.map + map_offset(Fo.B, l) + (long long)py * side + px);
+    }
+    if (same >= 0) {
+        const T *srcp = So.base + (int64_t)same * words;
+        for (int64_t e = threadIdx.x; e < words; e += blockDim.x) dst[e] = srcp[e];
+        return;
+    }
+    for (int64_t e = threadIdx.x; e < words; e += blockDim.x) dst[e] = T(0);
+    __syncthreads();
+    const int n = Fn.n;
+    const long long hwn = 2LL << (Fn.lmax - l);
+    const long long x0 = (long long)px * n * hwn, y0 = (long long)py * n * hwn;
+    for (int e = threadIdx.x; e < kPlanes * n * n; e += blockDim.x) {
+        const int k = e / (n * n), r = e - k * n * n, j = r / n, i = r % n;
+        const long long x = x0 + (long long)i * hwn + ((k == kAvg || k == kYmid) ? hwn / 2 : 0);
+        const long long y = y0 + (long long)j * hwn + ((k == kAvg || k == kXmid) ? hwn / 2 : 0);
+        const int q = entry_owner(Fo, k, x, y);
+        if (q < 0) continue;
+        if (__ldg(Fo.level + q) > l + 1) continue;  // at most one level of coarsening
+        for (int c = 0; c < Sn.ncomp; ++c) *Sn.at(p, c, k, i, j) = (T)transfer<T>(Fo, So, l, q, c, k, x, y);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void atomic_add_state(T *p, double v);
+template <>
+__device__ __forceinline__ void atomic_add_state<double>(double *p, double v) { atomicAdd(p, v); }
+template <>
+__device__ __forceinline__ void atomic_add_state<float>(float *p, double v) { atomicAdd(p, (float)v); }
+
+template <typename T>
+__global__ void reflux_kernel(DevForest F, StateView<T> S, uint32_t sync, double dx0, double dy0, double *freg) {
+    const int n = F.n, nc = S.ncomp;
+    const int64_t total = (int64_t)F.nleaf * 4 * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(t / (4 * n)), side = (int)((t / n) % 4), k = (int)(t % n);
+        const int l = __ldg(F.level + p);
+        if (l >= AF_MAX_LEVEL || !((sync >> l) & 1u) || !((sync >> (l + 1)) & 1u)) continue;
+        const long long hw = hwid(F, l), x0 = leaf_x0(F, p), y0 = leaf_y0(F, p);
+        const long long x1 = x0 + (long long)n * hw, y1 = y0 + (long long)n * hw;
+        long long px, py;
+        if (side == 0) { px = x0 - 1; py = y0 + k * hw + hw / 2; }
+        else if (side == 1) { px = x1; py = y0 + k * hw + hw / 2; }
+        else if (side == 2) { px = x0 + k * hw + hw / 2; py = y0 - 1; }
+        else { px = x0 + k * hw + hw / 2; py = y1; }
+        const int q = lookup(F, px, py);
+        if (q < 0 || __ldg(F.level + q) != l + 1) continue;
+        const long long hf = hwid(F, l + 1);
+        const int fside = side ^ 1;
+        const long long start = side < 2 ? reld(F, y0 + k * hw, leaf_y0(F, q)) : reld(F, x0 + k * hw, leaf_x0(F, q));
+        const int kf = (int)(start / hf);
+        if (kf < 0 || kf + 1 >= n) continue;
+        const int ci = side == 0 ? 0 : (side == 1 ? n - 1 : k);
+        const int cj = side == 2 ? 0 : (side == 3 ? n - 1 : k);
+        const double h = (side < 2 ? dx0 : dy0) / (double)(1LL << l);
+        const int64_t rw = 4LL * nc * n;
+        for (int c = 0; c < nc; ++c) {
+            double *rc = freg + p * rw + ((int64_t)side * nc + c) * n + k;
+            double *rf = freg + q * rw + ((int64_t)fside * nc + c) * n + kf;
+            const double fine = 0.5 * (rf[0] + rf[1]);
+            const double d = (side == 1 || side == 3) ? (*rc - fine) / h : (fine - *rc) / h;
+            atomic_add_state<T>(S.at(p, c, kAvg, ci, cj), d);
+            *rc = 0.0;
+            rf[0] = 0.0;
+            rf[1] = 0.0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void tag_kernel(DevForest F, StateView<T> S, int comp, int kind, double dx0, double dy0, double rthr,
+                           double cthr, int8_t *tags, double *ind) {
+    const int p = blockIdx.x, n = F.n;
+    const int l = __ldg(F.level + p);
+    const double hx = dx0 / (double)(1LL << l), hy = dy0 / (double)(1LL << l);
+    double a = -INFINITY, b = INFINITY;  // kind 0: max, min; kind 1: max gradient in a
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int j = e / n, i = e % n;
+        if (kind == 0) {
+            const double q = *S.at(p, comp, kAvg, i, j);
+            a = fmax(a, q);
+            b = fmin(b, q);
+        } else if (i >= 1 && i < n - 1 && j >= 1 && j < n - 1) {
+            const double gx = fabs((double)*S.at(p, comp, kAvg, i + 1, j) - (double)*S.at(p, comp, kAvg, i - 1, j)) / (2.0 * hx);
+            const double gy = fabs((double)*S.at(p, comp, kAvg, i, j + 1) - (double)*S.at(p, comp, kAvg, i, j - 1)) / (2.0 * hy);
+            a = fmax(a, fmax(gx, gy));
+        }
+    }
+    __shared__ double sa[256], sb[256];
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            sa[threadIdx.x] = fmax(sa[threadIdx.x], sa[threadIdx.x + s]);
+            sb[threadIdx.x] = fmin(sb[threadIdx.x], sb[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double v = kind == 0 ? sa[0] - sb[0] : fmax(sa[0], 0.0);
+        if (ind) ind[p] = v;
+        tags[p] = (int8_t)(v >= rthr ? 1 : (v < cthr ? -1 : 0));
+    }
+}
+
+constexpr int kMassBlocks = 256;
+constexpr int kMassThreads = 256;
+
+// Pass 1: block b sums leaves [b * chunk, (b+1) * chunk) in a fixed order.
+template <typename T>
+__global__ void mass_partial(DevForest F, StateView<T> S, double dx0, double dy0, int chunk, double *part) {
+    const int n = F.n, nc = S.ncomp;
+    __shared__ double sm[kMassThreads];
+    for (int c = 0; c < nc; ++c) {
+        double acc = 0.0;
+        const int p0 = blockIdx.x * chunk, p1 = min(F.nleaf, p0 + chunk);
+        for (int p = p0; p < p1; ++p) {
+            const int l = __ldg(F.level + p);
+            const double area = (dx0 / (double)(1LL << l)) * (dy0 / (double)(1LL << l));
+            double s = 0.0;
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) s += (double)*S.at(p, c, kAvg, e % n, e / n);
+            acc += s * area;
+        }
+        sm[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x * nc + c] = sm[0];
+        __syncthreads();
+    }
+}
+
+__global__ void mass_final(const double *part, int nblocks, int nc, double *out) {
+    __shared__ double sm[kMassThreads];
+    for (int c = 0; c < nc; ++c) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += part[b * nc + c];
+        sm[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c] = sm[0];
+        __syncthreads();
+    }
+}
+
+bool check_cfg(const af_config *cfg) {
+    return cfg && cfg->n >= 2 && cfg->n <= 64 && (cfg->eq == AF_ADVECTION || cfg->eq == AF_ACOUSTICS) &&
+           (cfg->prec == AF_F64 || cfg->prec == AF_F32) && cfg->ncomp == (cfg->eq == AF_ADVECTION ? 1 : 3);
+}
+
+bool check_forest(const af_forest *f) {
+    return f && f->nleaf >= 0 && f->B >= 1 && f->lmax >= 0 && f->lmax <= AF_MAX_LEVEL &&
+           (f->nleaf == 0 || (f->d_level && f->d_ix && f->d_iy && f->d_map));
+}
+
+template <typename T>
+StateView<T> view(const af_config &cfg, void *base) {
+    StateView<T> s;
+    s.base = static_cast<T *>(base);
+    s.plane = plane_stride(cfg.n);
+    s.ncomp = cfg.ncomp;
+    s.W = cfg.n + 2 * kGhost + 1;
+    return s;
+}
+
+inline af_status launched() { return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ERR_CUDA; }
+
+int mass_blocks(int nleaf) { return nleaf < kMassBlocks ? (nleaf < 1 ? 1 : nleaf) : kMassBlocks; }
+
+}  // namespace
+}  // namespace af
+
+using namespace af;
+
+extern "C" int64_t af_forest_map_offset(int32_t B, int32_t level) {
+    if (B < 1 || level < 0 || level > AF_MAX_LEVEL + 1) return -1;
+    return map_offset(B, level);
+}
+
+extern "C" af_status af_forest_build_map(int32_t nleaf, int32_t B, int32_t lmax, const int32_t *h_level,
+                                         const int32_t *h_ix, const int32_t *h_iy, int32_t *h_map) {
+    if (nleaf < 0 || B < 1 || lmax < 0 || lmax > AF_MAX_LEVEL || !h_map) return AF_ERR_ARG;
+    if (nleaf > 0 && (!h_level || !h_ix || !h_iy)) return AF_ERR_ARG;
+    const long long total = map_offset(B, lmax + 1);
+    for (long long e = 0; e < total; ++e) h_map[e] = -1;
+    for (int p = 0; p < nleaf; ++p) {
+        const int l = h_level[p];
+        if (l < 0 || l > lmax) return AF_ERR_ARG;
+        const long long side = (long long)B << l;
+        if (h_ix[p] < 0 || h_ix[p] >= side || h_iy[p] < 0 || h_iy[p] >= side) return AF_ERR_ARG;
+        int32_t &slot = h_map[map_offset(B, l) + (long long)h_iy[p] * side + h_ix[p]];
+        if (slot >= 0) return AF_ERR_ARG;
+        slot = p;
+    }
+    return AF_OK;
+}
+
+extern "C" af_status af_fill_ghosts(const af_config *cfg, const af_forest *forest, uint32_t dst_levels,
+                                    uint32_t src_levels, int32_t flags, void *d_state, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
+    if (forest->nleaf == 0) return AF_OK;
+    if (!d_state) return AF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(d_state) & 31u) return AF_ERR_LAYOUT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevForest F = make_dev(*forest, cfg->n);
+    for (int pass = 0; pass < 3; ++pass) {
+        if ((flags & AF_FILL_SAME_LEVEL_ONLY) && pass != 1) continue;
+        if (cfg->prec == AF_F64)
+            fill_kernel<double><<<forest->nleaf, 256, 0, s>>>(F, view<double>(*cfg, d_state), dst_levels, src_levels,
+                                                              flags, pass);
+        else
+            fill_kernel<float><<<forest->nleaf, 256, 0, s>>>(F, view<float>(*cfg, d_state), dst_levels, src_levels,
+                                                             flags, pass);
+        if (launched() != AF_OK) return AF_ERR_CUDA;
+    }
+    return AF_OK;
+}
+
+extern "C" af_status af_transfer(const af_config *cfg, const af_forest *old_forest, const void *d_old,
+                                 const af_forest *new_forest, void *d_new, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(old_forest) || !check_forest(new_forest)) return AF_ERR_ARG;
+    if (old_forest->B != new_forest->B || old_forest->lmax != new_forest->lmax) return AF_ERR_ARG;
+    if (new_forest->nleaf == 0) return AF_OK;
+    if (!d_old || !d_new || d_old == d_new) return AF_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_old) | reinterpret_cast<uintptr_t>(d_new)) & 31u) return AF_ERR_LAYOUT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevForest Fo = make_dev(*old_forest, cfg->n), Fn = make_dev(*new_forest, cfg->n);
+    if (cfg->prec == AF_F64)
+        transfer_kernel<double><<<new_forest->nleaf, 256, 0, s>>>(Fo, view<double>(*cfg, const_cast<void *>(d_old)), Fn,
+                                                                 view<double>(*cfg, d_new));
+    else
+        transfer_kernel<float><<<new_forest->nleaf, 256, 0, s>>>(Fo, view<float>(*cfg, const_cast<void *>(d_old)), Fn,
+                                                                view<float>(*cfg, d_new));
+    return launched();
+}
+
+extern "C" af_status af_reflux(const af_config *cfg, const af_forest *forest, uint32_t sync_levels, double dx0,
+                               double dy0, double *d_flux_reg, void *d_state, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
+    if (!(dx0 > 0.0) || !(dy0 > 0.0)) return AF_ERR_ARG;
+    if (forest->nleaf == 0) return AF_OK;
+    if (!d_flux_reg || !d_state) return AF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(d_state) & 31u) return AF_ERR_LAYOUT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevForest F = make_dev(*forest, cfg->n);
+    const long long total = (long long)forest->nleaf * 4 * cfg->n;
+    const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    if (cfg->prec == AF_F64)
+        reflux_kernel<double><<<blocks, 256, 0, s>>>(F, view<double>(*cfg, d_state), sync_levels, dx0, dy0, d_flux_reg);
+    else
+        reflux_kernel<float><<<blocks, 256, 0, s>>>(F, view<float>(*cfg, d_state), sync_levels, dx0, dy0, d_flux_reg);
+    return launched();
+}
+
+extern "C" af_status af_tag(const af_config *cfg, const af_forest *forest, const void *d_state, int32_t comp,
+                            int32_t kind, double dx0, double dy0, double refine_thr, double coarsen_thr,
+                            int8_t *d_tags, double *d_indicator, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
+    if (comp < 0 || comp >= cfg->ncomp || (kind != 0 && kind != 1)) return AF_ERR_ARG;
+    if (!(dx0 > 0.0) || !(dy0 > 0.0)) return AF_ERR_ARG;
+    if (forest->nleaf == 0) return AF_OK;
+    if (!d_state || !d_tags) return AF_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevForest F = make_dev(*forest, cfg->n);
+    if (cfg->prec == AF_F64)
+        tag_kernel<double><<<forest->nleaf, 256, 0, s>>>(F, view<double>(*cfg, const_cast<void *>(d_state)), comp, kind,
+                                                        dx0, dy0, refine_thr, coarsen_thr, d_tags, d_indicator);
+    else
+        tag_kernel<float><<<forest->nleaf, 256, 0, s>>>(F, view<float>(*cfg, const_cast<void *>(d_state)), comp, kind,
+                                                       dx0, dy0, refine_thr, coarsen_thr, d_tags, d_indicator);
+    return launched();
+}
+
+extern "C" int64_t af_mass_scratch_bytes(int32_t nleaf, int32_t ncomp) {
+    if (nleaf < 0 || ncomp < 1) return 0;
+    return (int64_t)mass_blocks(nleaf) * ncomp * (int64_t)sizeof(double);
+}
+
+extern "C" af_status af_mass(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0,
+                             double dy0, void *d_scratch, double *d_mass, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
+    if (!(dx0 > 0.0) || !(dy0 > 0.0) || !d_mass || !d_scratch) return AF_ERR_ARG;
+    if (forest->nleaf > 0 && !d_state) return AF_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_scratch) | reinterpret_cast<uintptr_t>(d_mass)) & 7u) return AF_ERR_LAYOUT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevForest F = make_dev(*forest, cfg->n);
+    const int nb = mass_blocks(forest->nleaf);
+    const int chunk = (forest->nleaf + nb - 1) / nb;
+    double *part = static_cast<double *>(d_scratch);
+    if (cfg->prec == AF_F64)
+        mass_partial<double><<<nb, kMassThreads, 0, s>>>(F, view<double>(*cfg, const_cast<void *>(d_state)), dx0, dy0,
+                                                        chunk, part);
+    else
+        mass_partial<float><<<nb, kMassThreads, 0, s>>>(F, view<float>(*cfg, const_cast<void *>(d_state)), dx0, dy0,
+                                                       chunk, part);
+    if (launched() != AF_OK) return AF_ERR_CUDA;
+    mass_final<<<1, kMassThreads, 0, s>>>(part, nb, cfg->ncomp, d_mass);
+    return launched();
+}

@@ -49,9 +49,12 @@ __device__ __forceinline__ int dir_index(int sx, int sy) {
 }
 
 // Stage the window of node lines [x0-1, x1+1] x [y0-1, y1+1] of every plane.
+// For a patch that advances its ghost layer (copy_all), the tile also writes
+// the staged entries of its share of the patch's lattice to the output, so
+// the output holds a complete patch (advanced entries are overwritten later).
 template <typename T, int NT>
 __device__ __forceinline__ void stage(const StepArgs<T> &A, int patch, const int *s_nbr, int x0, int y0,
-                                      int ww, int wh, T *Sin) {
+                                      int x1, int y1, int ww, int wh, bool copy_all, T *Sin) {
     const int n = A.n, W = n + 2 * kGhost + 1;
     const int64_t pw = (int64_t)A.ncomp * kPlanes * A.plane;
     const int ncp = A.ncomp * kPlanes;
@@ -74,6 +77,15 @@ __device__ __forceinline__ void stage(const StepArgs<T> &A, int patch, const int
         T *s = Sin + row * A.wn + col;
 #pragma unroll 4
         for (int cp = 0; cp < ncp; ++cp) s[cp * wsz] = __ldg(g + cp * A.plane);
+        if (copy_all) {
+            // share of the lattice [-2, n+2]^2 this tile copies
+            const int cxlo = x0 == -1 ? -2 : x0, cxhi = x1 == n + 1 ? n + 3 : x1;
+            const int cylo = y0 == -1 ? -2 : y0, cyhi = y1 == n + 1 ? n + 3 : y1;
+            if (li >= cxlo && li < cxhi && lj >= cylo && lj < cyhi) {
+                T *o = A.out + (int64_t)patch * pw + (int64_t)(lj + kGhost) * W + (li + kGhost);
+                for (int cp = 0; cp < ncp; ++cp) o[cp * A.plane] = s[cp * wsz];
+            }
+        }
     }
 }
 
@@ -168,7 +180,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ StepAr
     if (threadIdx.x < 8) s_nbr[threadIdx.x] = wk.nbr[threadIdx.x];
     __syncthreads();
     const int tw = x1 - x0, th = y1 - y0;
-    stage<T, NT>(A, patch, s_nbr, x0, y0, tw + 3, th + 3, Sin);
+    stage<T, NT>(A, patch, s_nbr, x0, y0, x1, y1, tw + 3, th + 3, (wk.flags & 1) != 0, Sin);
     __syncthreads();
 
     const int n = A.n, W_ = n + 2 * kGhost + 1;

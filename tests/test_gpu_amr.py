@@ -1,0 +1,247 @@
+"""Parity of the adaptive-mesh entry points (af_fill_ghosts, af_transfer,
+af_reflux, af_tag, af_mass) and of whole subcycled runs with the FP64 oracle,
+through the C ABI.  FP64 1e-12, FP32 1e-5 (normwise relative)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from oracle.amr import OracleForest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+G = S.G
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def af():
+    from paper_2205_07572_gb300 import af as _af, build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return _af
+
+
+def _diag_forest(lmin, lmax, extra=None):
+    def pred(l, ix, iy):
+        return ix == iy or (extra is not None and extra(l, ix, iy))
+    return S.balanced_forest(1, lmin, lmax, pred)
+
+
+def _ip(a):
+    import ctypes
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _oracle_fill(leaves, lmax, n, nc, st, dst, src, same_only=0):
+    lv = np.array([l for l, _, _ in leaves], np.int32)
+    ix = np.array([x for _, x, _ in leaves], np.int32)
+    iy = np.array([y for _, _, y in leaves], np.int32)
+    out = np.empty_like(st)
+    O.lib().orc_fill_amr(n, nc, len(leaves), _ip(lv), _ip(ix), _ip(iy), 1, lmax, dst, src, same_only,
+                         O._dp(st), O._dp(out))
+    return out
+
+
+def _device_forest(af, leaves, lmax):
+    from paper_2205_07572_gb300.amr import Forest
+    return Forest(1, lmax, leaves)
+
+
+def _sorted(leaves):
+    return sorted(leaves, key=lambda t: (t[0], t[2], t[1]))
+
+
+def _nerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("eq", [0, 1])
+def test_fill_matches_oracle(af, eq, prec):
+    n, lmax = 8, 4
+    nc = 1 if eq == 0 else 3
+    leaves = _sorted(_diag_forest(2, 4, lambda l, x, y: l == 3 and x == 5 and y == 2))
+    st = S.random_state(S.Layout(n, nc), len(leaves), seed=31).reshape(len(leaves), -1)
+    if prec:
+        st = st.astype(np.float32).astype(np.float64)
+    allm = (1 << (lmax + 1)) - 1
+    ref = _oracle_fill(leaves, lmax, n, nc, st, allm, allm)
+    F = _device_forest(af, leaves, lmax)
+    cfg = af.config(eq, prec, n, 1.0, 0.5, 1.0)
+    d = torch.from_numpy(st).to(torch.float64 if prec == 0 else torch.float32).cuda()
+    af.fill_ghosts(cfg, F.c, allm, allm, af.FILL_ALL_PATCHES, d)
+    torch.cuda.synchronize()
+    got = d.double().cpu().numpy()
+    assert _nerr(got, ref) < TOL[prec]
+    # same-level-only exchange of one level
+    ref2 = _oracle_fill(leaves, lmax, n, nc, st, 1 << 3, 1 << 3, 1)
+    d2 = torch.from_numpy(st).to(d.dtype).cuda()
+    af.fill_ghosts(cfg, F.c, 1 << 3, 1 << 3, af.FILL_ALL_PATCHES | af.FILL_SAME_LEVEL_ONLY, d2)
+    torch.cuda.synchronize()
+    assert _nerr(d2.double().cpu().numpy(), ref2) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_transfer_matches_oracle(af, prec):
+    from paper_2205_07572_gb300.amr import regrid_leaves
+    n, lmax, nc = 8, 4, 3
+    leaves = _sorted(_diag_forest(1, 3))
+    st = S.random_state(S.Layout(n, nc), len(leaves), seed=5).reshape(len(leaves), -1)
+    if prec:
+        st = st.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(2)
+    tags = rng.choice([-1, -1, 0, 1], size=len(leaves)).astype(np.int8)
+    F = _device_forest(af, leaves, lmax)
+    new = regrid_leaves(F, tags, 1)
+    assert new != leaves
+    lv = lambda L_, k: np.array([t[k] for t in L_], np.int32)
+    ref = np.zeros((len(new), st.shape[1]))
+    O.lib().orc_transfer(n, nc, 1, lmax, len(leaves), _ip(lv(leaves, 0)), _ip(lv(leaves, 1)), _ip(lv(leaves, 2)),
+                         O._dp(st), len(new), _ip(lv(new, 0)), _ip(lv(new, 1)), _ip(lv(new, 2)), O._dp(ref))
+    Fn = _device_forest(af, new, lmax)
+    cfg = af.config(1, prec, n, c=1.0)
+    tdt = torch.float64 if prec == 0 else torch.float32
+    d_old = torch.from_numpy(st).to(tdt).cuda()
+    d_new = torch.zeros((len(new), st.shape[1]), dtype=tdt, device="cuda")
+    af.transfer(cfg, F.c, d_old, Fn.c, d_new)
+    torch.cuda.synchronize()
+    got = d_new.double().cpu().numpy()
+    lay = S.Layout(n, nc)
+    g = lay.lattice(got.reshape(len(new), nc, 4, -1))[..., G:G + n, G:G + n]
+    r = lay.lattice(ref.reshape(len(new), nc, 4, -1))[..., G:G + n, G:G + n]
+    assert _nerr(g, r) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_reflux_matches_oracle(af, prec):
+    n, lmax, nc = 8, 3, 3
+    leaves = _sorted(_diag_forest(2, 3))
+    st = S.random_state(S.Layout(n, nc), len(leaves), seed=8).reshape(len(leaves), -1)
+    if prec:
+        st = st.astype(np.float32).astype(np.float64)
+    freg = np.random.default_rng(4).uniform(-1, 1, size=(len(leaves), 4 * nc * n))
+    lv = np.array([l for l, _, _ in leaves], np.int32)
+    ix = np.array([x for _, x, _ in leaves], np.int32)
+    iy = np.array([y for _, _, y in leaves], np.int32)
+    ref_st, ref_fr = st.copy(), freg.copy()
+    O.lib().orc_reflux_amr(n, nc, len(leaves), _ip(lv), _ip(ix), _ip(iy), 1, lmax, 0b1100, 0.125, 0.125,
+                           O._dp(ref_fr), O._dp(ref_st))
+    F = _device_forest(af, leaves, lmax)
+    cfg = af.config(1, prec, n, c=1.0)
+    d = torch.from_numpy(st).to(torch.float64 if prec == 0 else torch.float32).cuda()
+    dfr = torch.from_numpy(freg).cuda()
+    af.reflux(cfg, F.c, 0b1100, 0.125, 0.125, dfr, d)
+    torch.cuda.synchronize()
+    assert np.array_equal(dfr.cpu().numpy() == 0, ref_fr == 0)
+    assert _nerr(dfr.cpu().numpy(), ref_fr) < 1e-15
+    assert _nerr(d.double().cpu().numpy(), ref_st) < TOL[prec]
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_tag_and_mass_match_oracle(af, kind):
+    n, lmax, nc = 16, 3, 3
+    leaves = _sorted(_diag_forest(2, 3))
+    st = S.forest_state(n, nc, 1, lmax, leaves, S.pulse_plus_vortex(), nq=2).reshape(len(leaves), -1)
+    lv = np.array([l for l, _, _ in leaves], np.int32)
+    tags_ref = np.zeros(len(leaves), np.int8)
+    ind_ref = np.zeros(len(leaves))
+    import ctypes
+    thr = (0.05, 0.01) if kind == 0 else (2.0, 0.5)
+    O.lib().orc_tag(n, nc, len(leaves), _ip(lv), O._dp(st), 0, kind, 1 / 16, 1 / 16, thr[0], thr[1],
+                    tags_ref.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), O._dp(ind_ref))
+    m_ref = np.zeros(nc)
+    O.lib().orc_mass(n, nc, len(leaves), _ip(lv), O._dp(st), 1 / 16, 1 / 16, O._dp(m_ref))
+    F = _device_forest(af, leaves, lmax)
+    cfg = af.config(1, 0, n, c=1.0)
+    d = torch.from_numpy(st).cuda()
+    t = torch.zeros(len(leaves), dtype=torch.int8, device="cuda")
+    ind = torch.zeros(len(leaves), dtype=torch.float64, device="cuda")
+    af.tag(cfg, F.c, d, 0, kind, 1 / 16, 1 / 16, thr[0], thr[1], t, ind)
+    scratch = torch.zeros(af.mass_scratch_bytes(len(leaves), nc) // 8, dtype=torch.float64, device="cuda")
+    m = torch.zeros(nc, dtype=torch.float64, device="cuda")
+    af.mass(cfg, F.c, d, 1 / 16, 1 / 16, scratch, m)
+    torch.cuda.synchronize()
+    assert np.array_equal(t.cpu().numpy(), tags_ref)
+    assert _nerr(ind.cpu().numpy(), ind_ref) < 1e-13
+    assert np.abs(m.cpu().numpy() - m_ref).max() < 1e-13 * max(1.0, np.abs(m_ref).max())
+    assert (tags_ref == 1).any() and (tags_ref != 1).any()
+
+
+def _runs(af, eq, prec, n, lmin, lmax, funcs, cfl, leaves=None):
+    from paper_2205_07572_gb300.amr import AMRRun
+    nc = 1 if eq == 0 else 3
+    leaves = leaves or _sorted(_diag_forest(lmin, lmax))
+    st = S.forest_state(n, nc, 1, lmax, leaves, funcs, nq=3)
+    if prec:
+        st = st.astype(np.float32).astype(np.float64)
+    dx0 = 1.0 / n
+    dt0 = cfl * dx0 / (1.0 if eq == 0 else 1.0)
+    Fo = OracleForest(eq, n, 1, lmax, leaves, (0, 0), (1, 1), dt0, 1.0, 0.5, 1.0, state=st)
+    Fo.sync_fill((1 << (lmax + 1)) - 1)
+    run = AMRRun(af.config(eq, prec, n, 1.0, 0.5, 1.0), 1, lmax, leaves, st, (0, 0), (1, 1), dt0)
+    return Fo, run
+
+
+def _compare(Fo, run, n, nc, tol):
+    got = run.state_in_order(Fo.leaves)
+    lay = S.Layout(n, nc)
+    g = lay.lattice(got.reshape(len(Fo.leaves), nc, 4, -1))[..., G:G + n, G:G + n]
+    r = lay.lattice(Fo.state.reshape(len(Fo.leaves), nc, 4, -1))[..., G:G + n, G:G + n]
+    for c in range(nc):
+        assert _nerr(g[:, c], r[:, c]) < tol, (c, _nerr(g[:, c], r[:, c]))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("eq", [0, 1])
+def test_subcycled_amr_run_matches_oracle(af, eq, prec):
+    """Fixed diagonal forest, levels 2-3, several coarse steps with
+    subcycling, reflux and ghost exchange (Section 3.2)."""
+    n = 8
+    funcs = [S.sinsin_plus_gaussian] if eq == 0 else S.pulse_plus_vortex()
+    Fo, run = _runs(af, eq, prec, n, 2, 3, funcs, 0.6 if eq == 0 else 0.4)
+    m0 = run.mass()
+    for _ in range(3):
+        Fo.coarse_step()
+        run.coarse_step()
+    torch.cuda.synchronize()
+    _compare(Fo, run, n, 1 if eq == 0 else 3, TOL[prec] * (10 if prec else 1))
+    if prec == 0:
+        assert np.abs(run.mass() - m0).max() < 1e-13 * max(1.0, np.abs(m0).max())
+
+
+def test_three_level_amr_run_matches_oracle(af):
+    """Levels 2-4 (Fig. subcycle's three-level schedule), FP64 acoustics."""
+    n = 8
+    leaves = _sorted(S.balanced_forest(1, 2, 4, lambda l, x, y: x == y))
+    Fo, run = _runs(af, 1, 0, n, 2, 4, S.pulse_plus_vortex(), 0.4, leaves=leaves)
+    for _ in range(2):
+        Fo.coarse_step()
+        run.coarse_step()
+    torch.cuda.synchronize()
+    _compare(Fo, run, n, 3, 1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_dynamic_regrid_run_matches_oracle(af, prec):
+    """Coarse steps with a regrid after each (range indicator, Section 4.1's
+    criterion) on both sides: same forests, same data."""
+    n, lmin, lmax = 8, 2, 4
+    f = lambda x, y: np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2) / 0.01)
+    leaves = _sorted(S.balanced_forest(1, lmin, lmin, lambda *a: False))
+    Fo, run = _runs(af, 0, prec, n, lmin, lmax, [f], 0.6, leaves=leaves)
+    for it in range(3):
+        to, _ = Fo.tags(0, 0, 0.05, 0.01)
+        tg, _ = run.tags(0, 0, 0.05, 0.01)
+        order = {leaf: k for k, leaf in enumerate(run.forest.leaves)}
+        assert np.array_equal(tg[[order[l] for l in Fo.leaves]], to)
+        Fo.regrid(to, lmin)
+        run.regrid(tg, lmin)
+        assert Fo.leaves == run.forest.leaves
+        Fo.coarse_step()
+        run.coarse_step()
+    torch.cuda.synchronize()
+    assert len(set(l for l, _, _ in Fo.leaves)) >= 2
+    _compare(Fo, run, n, 1, TOL[prec] * (10 if prec else 1))
