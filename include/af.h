@@ -234,6 +234,29 @@ int64_t af_mass_scratch_bytes(int32_t nleaf, int32_t ncomp);
 af_status af_mass(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0, double dy0,
                   void *d_scratch, double *d_mass, void *stream);
 
+
+/* af_mass without any caller-provided scratch.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory -- for example a host code whose own pool allocator owns the
+ * whole device and lends the library only its state arrays, or a time loop
+ * that must not call cudaMalloc / cudaFree because those calls synchronise
+ * the device and stall every stream.  Same result as af_mass (same blocking,
+ * same summation order).
+ * The partial sums live in one fixed array inside the library, 1024 doubles
+ * (8 KB, room for 256 partial sums of up to 4 components), which every GPU
+ * that loads the library keeps until the process exits; AF_ERR_ARG if a
+ * call would need more (it never does for ncomp <= 3).  The first call on a
+ * device, with that device current, looks up the array's device address (a
+ * runtime query that enqueues no work); make that first call before any
+ * stream capture.  All calls on one device share that device's copy of the
+ * array, which keeps the last call's partial sums: calls that overlap on the
+ * GPU (for example on two streams with no ordering between them) race and
+ * give wrong totals; calls on different devices use different copies.
+ * Nothing needs clearing between calls: every partial sum is written before
+ * it is read. */
+af_status af_mass_noalloc(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0,
+                          double dy0, double *d_mass, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -216,3 +216,14 @@ def mass_scratch_bytes(nleaf: int, ncomp: int) -> int:
 def mass(cfg: Config, forest: ForestC, state, dx0: float, dy0: float, scratch, out, stream=None):
     _check(lib().af_mass(C.byref(cfg), C.byref(forest), ptr(state), dx0, dy0, ptr(scratch), ptr(out),
                          stream_handle(stream)), "af_mass")
+
+
+_EXTRA += [("af_mass_noalloc", C.c_int, [C.POINTER(Config), _FP, _VP, C.c_double, C.c_double, _VP, _VP])]
+if _lib is not None:
+    _register_more(_lib)
+
+
+def mass_noalloc(cfg: Config, forest: ForestC, state, dx0: float, dy0: float, out, stream=None):
+    """af_mass with the library's fixed scratch array (no allocation)."""
+    _check(lib().af_mass_noalloc(C.byref(cfg), C.byref(forest), ptr(state), dx0, dy0, ptr(out),
+                                 stream_handle(stream)), "af_mass_noalloc")

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "af_internal.h"
 
@@ -555,6 +556,60 @@ extern "C" af_status af_mass(const af_config *cfg, const af_forest *forest, cons
     const int nb = mass_blocks(forest->nleaf);
     const int chunk = (forest->nleaf + nb - 1) / nb;
     double *part = static_cast<double *>(d_scratch);
+    if (cfg->prec == AF_F64)
+        mass_partial<double><<<nb, kMassThreads, 0, s>>>(F, view<double>(*cfg, const_cast<void *>(d_state)), dx0, dy0,
+                                                        chunk, part);
+    else
+        mass_partial<float><<<nb, kMassThreads, 0, s>>>(F, view<float>(*cfg, const_cast<void *>(d_state)), dx0, dy0,
+                                                       chunk, part);
+    if (launched() != AF_OK) return AF_ERR_CUDA;
+    mass_final<<<1, kMassThreads, 0, s>>>(part, nb, cfg->ncomp, d_mass);
+    return launched();
+}
+
+// ---------------------------------------------------------------------------
+// af_mass_noalloc: af_mass for callers that cannot allocate device memory.
+// The per-block partial sums live in a fixed array compiled into the
+// library instead of a caller-provided scratch buffer.  Every device that
+// loads the library keeps this array (8 KB) until the process exits.
+static __device__ __align__(256) double g_mass_partials[256 * 4];  // kMassBlocks partial sums x up to 4 components
+
+namespace {
+std::mutex g_partials_mu;
+constexpr int kMaxDevices = 64;
+double *g_partials_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" af_status af_mass_noalloc(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0,
+                                     double dy0, double *d_mass, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
+    if (!(dx0 > 0.0) || !(dy0 > 0.0) || !d_mass) return AF_ERR_ARG;
+    if (forest->nleaf > 0 && !d_state) return AF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(d_mass) & 7u) return AF_ERR_LAYOUT;
+    const int nb = mass_blocks(forest->nleaf);
+    // capacity check: partial sums needed vs. the fixed array
+    if ((int64_t)nb * cfg->ncomp > (int64_t)(sizeof(g_mass_partials) / sizeof(double))) return AF_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AF_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return AF_ERR_ARG;
+    double *part = nullptr;
+    {
+        // In host code g_mass_partials names a host-side stand-in, not device
+        // memory: resolve the device address once per device, with that
+        // device current.
+        std::lock_guard<std::mutex> lk(g_partials_mu);
+        if (g_partials_addr[dev] == nullptr) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_mass_partials) != cudaSuccess || p == nullptr) return AF_ERR_CUDA;
+            g_partials_addr[dev] = static_cast<double *>(p);
+        }
+        part = g_partials_addr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevForest F = make_dev(*forest, cfg->n);
+    const int chunk = (forest->nleaf + nb - 1) / nb;
+    // every partial sum read by mass_final is written by mass_partial first,
+    // so nothing left in the array by an earlier call is used
     if (cfg->prec == AF_F64)
         mass_partial<double><<<nb, kMassThreads, 0, s>>>(F, view<double>(*cfg, const_cast<void *>(d_state)), dx0, dy0,
                                                         chunk, part);
