@@ -55,6 +55,22 @@ struct AcousticWeights {
     T wy[2][7][15];
 };
 
+// The same weights folded by the mirror symmetries of each node's stencil
+// (x -> -x and y -> -y about the node; they hold for dx != dy).  Degrees of
+// freedom are first combined into orbit sums: SS (symmetric in x and y),
+// AS (antisymmetric in x, symmetric in y), SA (symmetric in x, antisymmetric
+// in y).  The operator M + R d_R M acts on SS, -R M{d/dX} on AS and
+// -R M{d/dY} on SA; by symmetry every other combination vanishes.  Orbit
+// order and representatives: see sym_rep() in af_weights.cpp.
+//   corner node: SS 9, AS 6, SA 6;  left-edge mid: SS 6, AS 4, SA 3;
+//   bottom-edge mid: SS 6, AS 3, SA 4.   [2] = T combination, Q^{n+1}.
+template <typename T>
+struct AcousticSymWeights {
+    T cA[2][9], cDx[2][6], cDy[2][6];
+    T xA[2][6], xDx[2][4], xDy[2][3];
+    T yA[2][6], yDx[2][3], yDy[2][4];
+};
+
 // Advection weights (Eq. advection-update): for node type t (0 corner,
 // 1 left-edge mid, 2 bottom-edge mid) and time s (0: dt/2, 1: dt) the foot of
 // the characteristic lies in cell (line + off[t][s][0], line + off[t][s][1]);
@@ -69,6 +85,10 @@ struct AdvectionWeights {
 
 // Double-precision derivations on the host (af_weights.cpp).
 void acoustic_weights(double rho_x, double rho_y, AcousticWeights<double> &w);
+// Folded weights; returns false if the dense weights lack the symmetry
+// (max deviation above 1e-12 of the largest weight), which cannot happen for
+// the operators of Eq. ERFormula.
+bool acoustic_sym_weights(double rho_x, double rho_y, AcousticSymWeights<double> &w);
 void advection_weights(double nu_x, double nu_y, AdvectionWeights<double> &w);
 
 }  // namespace af

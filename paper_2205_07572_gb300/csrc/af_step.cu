@@ -52,13 +52,13 @@ __device__ __forceinline__ int dir_index(int sx, int sy) {
 // For a patch that advances its ghost layer (copy_all), the tile also writes
 // the staged entries of its share of the patch's lattice to the output, so
 // the output holds a complete patch (advanced entries are overwritten later).
-template <typename T, int NT>
+template <typename T, int NT, int WN>
 __device__ __forceinline__ void stage(const StepArgs<T> &A, int patch, const int *s_nbr, int x0, int y0,
                                       int x1, int y1, int ww, int wh, bool copy_all, T *Sin) {
     const int n = A.n, W = n + 2 * kGhost + 1;
     const int64_t pw = (int64_t)A.ncomp * kPlanes * A.plane;
     const int ncp = A.ncomp * kPlanes;
-    const int wsz = A.wn * A.wn;
+    constexpr int wsz = WN * WN;
     for (int pos = threadIdx.x; pos < ww * wh; pos += NT) {
         const int row = pos / ww, col = pos - row * ww;
         const int li = x0 - 1 + col, lj = y0 - 1 + row;
@@ -74,7 +74,7 @@ __device__ __forceinline__ void stage(const StepArgs<T> &A, int patch, const int
             }
         }
         const T *g = A.in + (int64_t)src * pw + (int64_t)(sj + kGhost) * W + (si + kGhost);
-        T *s = Sin + row * A.wn + col;
+        T *s = Sin + row * WN + col;
 #pragma unroll 4
         for (int cp = 0; cp < ncp; ++cp) s[cp * wsz] = __ldg(g + cp * A.plane);
         if (copy_all) {
@@ -100,49 +100,102 @@ __host__ __device__ constexpr int blk_b(int k) {
     return k < 4 ? (k >> 1) : (k < 13 ? (k - 4) / 3 : (k < 19 ? (k - 13) / 3 : (k - 19) / 2));
 }
 
-// Acoustic node evaluation of one node-cell item (window coords qi, rj of
-// node line (i, j)).  out: T and Q^{n+1} of corner, xmid, ymid for p, u, v.
+// Orbit sums of a quad (++, +-, -+, --): symmetric, x-antisymmetric,
+// y-antisymmetric parts.
 template <typename T>
-__device__ __forceinline__ void acoustic_item(const AcousticWeights<T> &W, const T *Sin, int wn, int qi, int rj,
+__device__ __forceinline__ void quad(T pp, T pm, T mp, T mm, T &ss, T &as, T &sa) {
+    const T a = pp + pm, b = mp + mm;
+    ss = a + b;
+    as = a - b;
+    sa = (pp - pm) + (mp - mm);
+}
+
+template <int N, typename T>
+__device__ __forceinline__ T dot(const T *w, const T *v) {
+    T s = w[0] * v[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k) s = fma(w[k], v[k], s);
+    return s;
+}
+
+// Acoustic node evaluation of one node-cell item (window coords qi, rj of
+// node line (i, j)) with the mirror-folded weights: the 25 block values of
+// each input component are combined into the orbit sums of the three nodes,
+// then p += A.SS_p + Dx.AS_u + Dy.SA_v, u += A.SS_u + Dx.AS_p,
+// v += A.SS_v + Dy.SA_p (the evolution operators of Eq. ERFormula).
+// out: T and Q^{n+1} of corner (tc, nc), left-edge mid (tx, nx) and
+// bottom-edge mid (ty, ny) for p, u, v.
+template <typename T, int WN>
+__device__ __forceinline__ void acoustic_item(const AcousticSymWeights<T> &W, const T *Sin, int qi, int rj,
                                               T tc[3], T nc[3], T tx[3], T nx[3], T ty[3], T ny[3]) {
-    const int wsz = wn * wn;
+    constexpr int WSZ = WN * WN;
 #pragma unroll
     for (int o = 0; o < 3; ++o) tc[o] = nc[o] = tx[o] = nx[o] = ty[o] = ny[o] = T(0);
-    const T *base = Sin + (rj - 1) * wn + (qi - 1);
+    const T *base = Sin + (rj - 1) * WN + (qi - 1);
 #pragma unroll
     for (int ci = 0; ci < 3; ++ci) {
         T b[25];
 #pragma unroll
-        for (int k = 0; k < 25; ++k)
-            b[k] = base[(ci * kPlanes + blk_plane(k)) * wsz + blk_b(k) * wn + blk_a(k)];
-        // (out, pair) receiving input component ci: p -> (p 0, u 4, v 6),
-        // u -> (p 1, u 3), v -> (p 2, v 5)
-        constexpr int kOut[3][3] = {{0, 1, 2}, {0, 1, -1}, {0, 2, -1}};
-        constexpr int kPair[3][3] = {{0, 4, 6}, {1, 3, -1}, {2, 5, -1}};
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            if (kOut[ci][r] < 0) continue;
-            const int o = kOut[ci][r], pr = kPair[ci][r];
-#pragma unroll
-            for (int k = 0; k < 25; ++k) {
-                tc[o] = fma(W.wc[0][pr][k], b[k], tc[o]);
-                nc[o] = fma(W.wc[1][pr][k], b[k], nc[o]);
-            }
-#pragma unroll
-            for (int k = 0; k < 15; ++k) {
-                tx[o] = fma(W.wx[0][pr][k], b[x_idx(k)], tx[o]);
-                nx[o] = fma(W.wx[1][pr][k], b[x_idx(k)], nx[o]);
-                ty[o] = fma(W.wy[0][pr][k], b[y_idx(k)], ty[o]);
-                ny[o] = fma(W.wy[1][pr][k], b[y_idx(k)], ny[o]);
-            }
+        for (int k = 0; k < 25; ++k) b[k] = base[(ci * kPlanes + blk_plane(k)) * WSZ + blk_b(k) * WN + blk_a(k)];
+        // ---- corner node
+        T css[9], cas[6], csa[6];
+        quad(b[3], b[1], b[2], b[0], css[0], cas[0], csa[0]);
+        quad(b[12], b[6], b[10], b[4], css[1], cas[1], csa[1]);
+        quad(b[18], b[15], b[16], b[13], css[2], cas[2], csa[2]);
+        quad(b[24], b[20], b[23], b[19], css[3], cas[3], csa[3]);
+        css[4] = b[9] + b[7];   cas[4] = b[9] - b[7];
+        css[5] = b[22] + b[21]; cas[5] = b[22] - b[21];
+        css[6] = b[11] + b[5];  csa[4] = b[11] - b[5];
+        css[7] = b[17] + b[14]; csa[5] = b[17] - b[14];
+        css[8] = b[8];
+        // ---- left-edge midpoint
+        T xss[6], xas[4], xsa[3];
+        quad(b[12], b[9], b[10], b[7], xss[0], xas[0], xsa[0]);
+        quad(b[24], b[22], b[23], b[21], xss[1], xas[1], xsa[1]);
+        xss[2] = b[3] + b[2];   xas[2] = b[3] - b[2];
+        xss[3] = b[18] + b[16]; xas[3] = b[18] - b[16];
+        xss[4] = b[11] + b[8];  xsa[2] = b[11] - b[8];
+        xss[5] = b[17];
+        // ---- bottom-edge midpoint
+        T yss[6], yas[3], ysa[4];
+        quad(b[12], b[6], b[11], b[5], yss[0], yas[0], ysa[0]);
+        quad(b[18], b[15], b[17], b[14], yss[1], yas[1], ysa[1]);
+        yss[2] = b[9] + b[8];   yas[2] = b[9] - b[8];
+        yss[3] = b[3] + b[1];   ysa[2] = b[3] - b[1];
+        yss[4] = b[24] + b[20]; ysa[3] = b[24] - b[20];
+        yss[5] = b[22];
+        if (ci == 0) {  // p: A on p; Dx.AS_p -> u; Dy.SA_p -> v
+            tc[0] += dot<9>(W.cA[0], css); nc[0] += dot<9>(W.cA[1], css);
+            tx[0] += dot<6>(W.xA[0], xss); nx[0] += dot<6>(W.xA[1], xss);
+            ty[0] += dot<6>(W.yA[0], yss); ny[0] += dot<6>(W.yA[1], yss);
+            tc[1] += dot<6>(W.cDx[0], cas); nc[1] += dot<6>(W.cDx[1], cas);
+            tx[1] += dot<4>(W.xDx[0], xas); nx[1] += dot<4>(W.xDx[1], xas);
+            ty[1] += dot<3>(W.yDx[0], yas); ny[1] += dot<3>(W.yDx[1], yas);
+            tc[2] += dot<6>(W.cDy[0], csa); nc[2] += dot<6>(W.cDy[1], csa);
+            tx[2] += dot<3>(W.xDy[0], xsa); nx[2] += dot<3>(W.xDy[1], xsa);
+            ty[2] += dot<4>(W.yDy[0], ysa); ny[2] += dot<4>(W.yDy[1], ysa);
+        } else if (ci == 1) {  // u: A on u; Dx.AS_u -> p
+            tc[1] += dot<9>(W.cA[0], css); nc[1] += dot<9>(W.cA[1], css);
+            tx[1] += dot<6>(W.xA[0], xss); nx[1] += dot<6>(W.xA[1], xss);
+            ty[1] += dot<6>(W.yA[0], yss); ny[1] += dot<6>(W.yA[1], yss);
+            tc[0] += dot<6>(W.cDx[0], cas); nc[0] += dot<6>(W.cDx[1], cas);
+            tx[0] += dot<4>(W.xDx[0], xas); nx[0] += dot<4>(W.xDx[1], xas);
+            ty[0] += dot<3>(W.yDx[0], yas); ny[0] += dot<3>(W.yDx[1], yas);
+        } else {  // v: A on v; Dy.SA_v -> p
+            tc[2] += dot<9>(W.cA[0], css); nc[2] += dot<9>(W.cA[1], css);
+            tx[2] += dot<6>(W.xA[0], xss); nx[2] += dot<6>(W.xA[1], xss);
+            ty[2] += dot<6>(W.yA[0], yss); ny[2] += dot<6>(W.yA[1], yss);
+            tc[0] += dot<6>(W.cDy[0], csa); nc[0] += dot<6>(W.cDy[1], csa);
+            tx[0] += dot<3>(W.xDy[0], xsa); nx[0] += dot<3>(W.xDy[1], xsa);
+            ty[0] += dot<4>(W.yDy[0], ysa); ny[0] += dot<4>(W.yDy[1], ysa);
         }
     }
 }
 
 // Advection: value of the reconstruction of window cell (cq, cr) with weights w.
-template <typename T>
-__device__ __forceinline__ T adv_eval(const T *w, const T *Sin, int wn, int cq, int cr) {
-    const int wsz = wn * wn;
+template <typename T, int wn>
+__device__ __forceinline__ T adv_eval(const T *w, const T *Sin, int cq, int cr) {
+    constexpr int wsz = wn * wn;
     const int o = cr * wn + cq;
     const T *A = Sin + kAvg * wsz, *C = Sin + kCorner * wsz, *X = Sin + kXmid * wsz, *Y = Sin + kYmid * wsz;
     T v = w[0] * A[o];
@@ -160,19 +213,20 @@ __device__ __forceinline__ T adv_eval(const T *w, const T *Sin, int wn, int cq, 
 template <typename T, int EQ, int NT>
 struct WeightsOf;
 template <typename T, int NT>
-struct WeightsOf<T, AF_ACOUSTICS, NT> { using type = AcousticWeights<T>; };
+struct WeightsOf<T, AF_ACOUSTICS, NT> { using type = AcousticSymWeights<T>; };
 template <typename T, int NT>
 struct WeightsOf<T, AF_ADVECTION, NT> { using type = AdvectionWeights<T>; };
 
-template <typename T, int EQ, int NT>
+template <typename T, int EQ, int NT, int TM>
 __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ StepArgs<T> A,
                                                   const __grid_constant__ typename WeightsOf<T, EQ, NT>::type W) {
+    constexpr int WN = TM + 3, TP = TM + 1;  // window pitch, T-array pitch
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_nbr[8];
     T *Sin = reinterpret_cast<T *>(smem_raw);
-    const int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
-    T *ST = Sin + ncomp * kPlanes * A.wn * A.wn;
-    const int tp = A.tp, tsz = tp * tp;
+    constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
+    T *ST = Sin + ncomp * kPlanes * WN * WN;
+    constexpr int tp = TP, tsz = TP * TP;
 
     const af_work &wk = A.work[blockIdx.x];
     const int patch = wk.patch, level = wk.level;
@@ -180,7 +234,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ StepAr
     if (threadIdx.x < 8) s_nbr[threadIdx.x] = wk.nbr[threadIdx.x];
     __syncthreads();
     const int tw = x1 - x0, th = y1 - y0;
-    stage<T, NT>(A, patch, s_nbr, x0, y0, x1, y1, tw + 3, th + 3, (wk.flags & 1) != 0, Sin);
+    stage<T, NT, WN>(A, patch, s_nbr, x0, y0, x1, y1, tw + 3, th + 3, (wk.flags & 1) != 0, Sin);
     __syncthreads();
 
     const int n = A.n, W_ = n + 2 * kGhost + 1;
@@ -190,7 +244,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ StepAr
     // ends on the outer edge of the advanced first ghost layer
     const int sxhi = (x1 == n + 1) ? x1 : x1 - 1;
     const int syhi = (y1 == n + 1) ? y1 : y1 - 1;
-    const int wn = A.wn, wsz = wn * wn;
+    constexpr int wn = WN, wsz = WN * WN;
 
     // ---- point values (Eq. advection-update / Eq. ERFormula)
     const int nitems = (tw + 1) * (th + 1);
@@ -203,7 +257,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ StepAr
         const int64_t lo = (int64_t)(j + kGhost) * W_ + (i + kGhost);
         if constexpr (EQ == AF_ACOUSTICS) {
             T tc[3], nc[3], tx[3], nx[3], ty[3], ny[3];
-            acoustic_item<T>(W, Sin, wn, qi, rj, tc, nc, tx, nx, ty, ny);
+            acoustic_item<T, WN>(W, Sin, qi, rj, tc, nc, tx, nx, ty, ny);
 #pragma unroll
             for (int o = 0; o < 3; ++o) {
                 ST[(o * 3 + 0) * tsz + jj * tp + ii] = tc[o];
@@ -217,20 +271,20 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ StepAr
         } else {
             const int own = rj * wn + qi;
             {
-                const T qh = adv_eval<T>(W.w[0][0], Sin, wn, qi + W.off[0][0][0], rj + W.off[0][0][1]);
-                const T q1 = adv_eval<T>(W.w[0][1], Sin, wn, qi + W.off[0][1][0], rj + W.off[0][1][1]);
+                const T qh = adv_eval<T, WN>(W.w[0][0], Sin, qi + W.off[0][0][0], rj + W.off[0][0][1]);
+                const T q1 = adv_eval<T, WN>(W.w[0][1], Sin, qi + W.off[0][1][0], rj + W.off[0][1][1]);
                 ST[0 * tsz + jj * tp + ii] = Sin[kCorner * wsz + own] + T(4) * qh + q1;
                 if (st_x && st_y) outp[kCorner * A.plane + lo] = q1;
             }
             if (hx) {
-                const T qh = adv_eval<T>(W.w[1][0], Sin, wn, qi + W.off[1][0][0], rj + W.off[1][0][1]);
-                const T q1 = adv_eval<T>(W.w[1][1], Sin, wn, qi + W.off[1][1][0], rj + W.off[1][1][1]);
+                const T qh = adv_eval<T, WN>(W.w[1][0], Sin, qi + W.off[1][0][0], rj + W.off[1][0][1]);
+                const T q1 = adv_eval<T, WN>(W.w[1][1], Sin, qi + W.off[1][1][0], rj + W.off[1][1][1]);
                 ST[1 * tsz + jj * tp + ii] = Sin[kXmid * wsz + own] + T(4) * qh + q1;
                 if (st_x) outp[kXmid * A.plane + lo] = q1;
             }
             if (hy) {
-                const T qh = adv_eval<T>(W.w[2][0], Sin, wn, qi + W.off[2][0][0], rj + W.off[2][0][1]);
-                const T q1 = adv_eval<T>(W.w[2][1], Sin, wn, qi + W.off[2][1][0], rj + W.off[2][1][1]);
+                const T qh = adv_eval<T, WN>(W.w[2][0], Sin, qi + W.off[2][0][0], rj + W.off[2][0][1]);
+                const T q1 = adv_eval<T, WN>(W.w[2][1], Sin, qi + W.off[2][1][0], rj + W.off[2][1][1]);
                 ST[2 * tsz + jj * tp + ii] = Sin[kYmid * wsz + own] + T(4) * qh + q1;
                 if (st_y) outp[kYmid * A.plane + lo] = q1;
             }
@@ -299,22 +353,25 @@ WeightKey g_akey{-1, 0, 0}, g_dkey{-1, 0, 0};
 AcousticWeights<double> g_aw;
 AdvectionWeights<double> g_dw;
 
+std::mutex g_smu;
+WeightKey g_skey{-1, 0, 0};
+AcousticSymWeights<double> g_sw;
+bool g_sw_ok = false;
+
 template <typename T>
-void get_acoustic(double rx, double ry, AcousticWeights<T> &out) {
-    std::lock_guard<std::mutex> lk(g_wmu);
+bool get_acoustic(double rx, double ry, AcousticSymWeights<T> &out) {
+    std::lock_guard<std::mutex> lk(g_smu);
     WeightKey k{AF_ACOUSTICS, rx, ry};
-    if (!(k == g_akey)) {
-        acoustic_weights(rx, ry, g_aw);
-        g_akey = k;
+    if (!(k == g_skey)) {
+        g_sw_ok = acoustic_sym_weights(rx, ry, g_sw);
+        g_skey = k;
     }
-    for (int c = 0; c < 2; ++c)
-        for (int p = 0; p < 7; ++p) {
-            for (int q = 0; q < 25; ++q) out.wc[c][p][q] = (T)g_aw.wc[c][p][q];
-            for (int q = 0; q < 15; ++q) {
-                out.wx[c][p][q] = (T)g_aw.wx[c][p][q];
-                out.wy[c][p][q] = (T)g_aw.wy[c][p][q];
-            }
-        }
+    const double *src = &g_sw.cA[0][0];
+    T *dst = &out.cA[0][0];
+    constexpr int nw = sizeof(AcousticSymWeights<double>) / sizeof(double);
+    static_assert(sizeof(AcousticSymWeights<T>) == nw * sizeof(T), "packed weight struct");
+    for (int i = 0; i < nw; ++i) dst[i] = (T)src[i];
+    return g_sw_ok;
 }
 
 template <typename T>
@@ -339,6 +396,23 @@ cudaError_t ensure_smem(Kern k, size_t bytes) {
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Tile geometry compiled into the kernel: 10, 18 or 32 cells per side.
+inline int tile_template_for(int n) {
+    const int t = tile_max_for(n);
+    return t <= 10 ? 10 : (t <= 18 ? 18 : 32);
+}
+
+template <typename T, int EQ, int TM>
+af_status launch_tm(const StepArgs<T> &A, const typename WeightsOf<T, EQ, kThreads>::type &W, int ncomp, int nwork,
+                    cudaStream_t stream) {
+    constexpr int WN = TM + 3, TP = TM + 1;
+    const size_t smem = sizeof(T) * ((size_t)ncomp * kPlanes * WN * WN + (size_t)ncomp * 3 * TP * TP);
+    auto kern = step_kernel<T, EQ, kThreads, TM>;
+    if (ensure_smem(kern, smem) != cudaSuccess) return AF_ERR_CUDA;
+    kern<<<nwork, kThreads, smem, stream>>>(A, W);
+    return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ERR_CUDA;
+}
+
 template <typename T, int EQ>
 af_status launch(const af_config &cfg, int nwork, const af_work *d_work, const void *d_in, void *d_out,
                  double dt0, double dx0, double dy0, double *d_freg, cudaStream_t stream) {
@@ -350,26 +424,24 @@ af_status launch(const af_config &cfg, int nwork, const af_work *d_work, const v
     A.plane = plane_stride(cfg.n);
     A.n = cfg.n;
     A.ncomp = cfg.ncomp;
-    const int tmax = tile_max_for(cfg.n);
-    A.wn = tmax + 3;
-    A.tp = tmax + 1;
+    const int tm = tile_template_for(cfg.n);
+    A.wn = tm + 3;
+    A.tp = tm + 1;
     A.dtdx = (T)(dt0 / dx0);
     A.dtdy = (T)(dt0 / dy0);
     A.dt0 = dt0;
-    const size_t smem = sizeof(T) * ((size_t)cfg.ncomp * kPlanes * A.wn * A.wn + (size_t)cfg.ncomp * 3 * A.tp * A.tp);
     typename WeightsOf<T, EQ, kThreads>::type W;
     if constexpr (EQ == AF_ACOUSTICS) {
         A.fx = A.fy = (T)(cfg.c / 36.0);
-        get_acoustic<T>(cfg.c * dt0 / dx0, cfg.c * dt0 / dy0, W);
+        if (!get_acoustic<T>(cfg.c * dt0 / dx0, cfg.c * dt0 / dy0, W)) return AF_ERR_UNIMPLEMENTED;
     } else {
         A.fx = (T)(cfg.a / 36.0);
         A.fy = (T)(cfg.b / 36.0);
         get_advection<T>(cfg.a * dt0 / dx0, cfg.b * dt0 / dy0, W);
     }
-    auto kern = step_kernel<T, EQ, kThreads>;
-    if (ensure_smem(kern, smem) != cudaSuccess) return AF_ERR_CUDA;
-    kern<<<nwork, kThreads, smem, stream>>>(A, W);
-    return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ERR_CUDA;
+    if (tm == 10) return launch_tm<T, EQ, 10>(A, W, cfg.ncomp, nwork, stream);
+    if (tm == 18) return launch_tm<T, EQ, 18>(A, W, cfg.ncomp, nwork, stream);
+    return launch_tm<T, EQ, 32>(A, W, cfg.ncomp, nwork, stream);
 }
 
 }  // namespace

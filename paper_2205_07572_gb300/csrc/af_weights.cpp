@@ -139,7 +139,10 @@ void node_operators(const Sector *sec, int nsec, double rx, double ry, double A[
 
 }  // namespace
 
-void acoustic_weights(double rho_x, double rho_y, AcousticWeights<double> &w) {
+// Dense operators of node type t (0 corner, 1 left-edge mid, 2 bottom-edge
+// mid) over the 25-entry block: op[c][0..2][k] = A, Dx, Dy for combination
+// c (0: T = Q^n + 4 Q^{n+1/2} + Q^{n+1}, 1: Q^{n+1}).
+void node_type_operators(int t, double rho_x, double rho_y, double op[2][3][25]) {
     // Sectors of the three node types (Eq. cfl-acoustics keeps each disc inside
     // the cells that share the node).
     const Sector corner[4] = {{0, 0, -1.0, -1.0, 0, 0}, {-1, 0, 1.0, -1.0, 1, 1},
@@ -149,17 +152,31 @@ void acoustic_weights(double rho_x, double rho_y, AcousticWeights<double> &w) {
     const Sector *secs[3] = {corner, xmid, ymid};
     const int nsec[3] = {4, 2, 2};
     const int own[3] = {8, 17, 22};  // block index of the node itself
+    double Ah[25], Dxh[25], Dyh[25], A1[25], Dx1[25], Dy1[25];
+    node_operators(secs[t], nsec[t], 0.5 * rho_x, 0.5 * rho_y, Ah, Dxh, Dyh);
+    node_operators(secs[t], nsec[t], rho_x, rho_y, A1, Dx1, Dy1);
+    for (int k = 0; k < 25; ++k) {
+        op[0][0][k] = 4.0 * Ah[k] + A1[k] + (k == own[t] ? 1.0 : 0.0);
+        op[0][1][k] = 4.0 * Dxh[k] + Dx1[k];
+        op[0][2][k] = 4.0 * Dyh[k] + Dy1[k];
+        op[1][0][k] = A1[k];
+        op[1][1][k] = Dx1[k];
+        op[1][2][k] = Dy1[k];
+    }
+}
+
+void acoustic_weights(double rho_x, double rho_y, AcousticWeights<double> &w) {
     for (int t = 0; t < 3; ++t) {
-        double Ah[25], Dxh[25], Dyh[25], A1[25], Dx1[25], Dy1[25];
-        node_operators(secs[t], nsec[t], 0.5 * rho_x, 0.5 * rho_y, Ah, Dxh, Dyh);
-        node_operators(secs[t], nsec[t], rho_x, rho_y, A1, Dx1, Dy1);
+        double op[2][3][25];
+        node_type_operators(t, rho_x, rho_y, op);
         double full[2][7][25];
         for (int k = 0; k < 25; ++k) {
-            const double ta = 4.0 * Ah[k] + A1[k] + (k == own[t] ? 1.0 : 0.0);
-            const double tx = 4.0 * Dxh[k] + Dx1[k];
-            const double ty = 4.0 * Dyh[k] + Dy1[k];
+            const double ta = op[0][0][k];
+            const double tx = op[0][1][k];
+            const double ty = op[0][2][k];
+            const double A1[1] = {op[1][0][k]}, Dx1[1] = {op[1][1][k]}, Dy1[1] = {op[1][2][k]};
             const double T[7] = {ta, tx, ty, ta, tx, ta, ty};
-            const double N[7] = {A1[k], Dx1[k], Dy1[k], A1[k], Dx1[k], A1[k], Dy1[k]};
+            const double N[7] = {A1[0], Dx1[0], Dy1[0], A1[0], Dx1[0], A1[0], Dy1[0]};
             for (int p = 0; p < 7; ++p) {
                 full[0][p][k] = T[p];
                 full[1][p][k] = N[p];
@@ -205,6 +222,86 @@ void advection_weights(double nu_x, double nu_y, AdvectionWeights<double> &w) {
             w.off[t][s][1] = ky;
             for (int d = 0; d < 9; ++d) w.w[t][s][d] = basis_value(d, xi, eta);
         }
+}
+
+}  // namespace af
+
+namespace af {
+namespace {
+
+// Orbits of the block entries under the two mirror symmetries of a node.
+// A quad lists (++, +-, -+, --) by the signs of (x, y) relative to the node;
+// an x-pair (p, m) lies on y = 0, a y-pair on x = 0.
+struct Orbit {
+    int kind;    // 0 quad, 1 x-pair, 2 y-pair, 3 single
+    int m[4];
+};
+
+// SS / AS / SA orbit lists of node type t, in the order the kernel uses.
+int orbits(int t, int which, Orbit *o) {
+    static const Orbit c_ss[9] = {{0, {3, 1, 2, 0}},   {0, {12, 6, 10, 4}}, {0, {18, 15, 16, 13}},
+                                  {0, {24, 20, 23, 19}}, {1, {9, 7}},        {1, {22, 21}},
+                                  {2, {11, 5}},          {2, {17, 14}},      {3, {8}}};
+    static const Orbit x_ss[6] = {{0, {12, 9, 10, 7}}, {0, {24, 22, 23, 21}}, {1, {3, 2}},
+                                  {1, {18, 16}},       {2, {11, 8}},          {3, {17}}};
+    static const Orbit y_ss[6] = {{0, {12, 6, 11, 5}}, {0, {18, 15, 17, 14}}, {1, {9, 8}},
+                                  {2, {3, 1}},         {2, {24, 20}},         {3, {22}}};
+    const Orbit *ss = t == 0 ? c_ss : (t == 1 ? x_ss : y_ss);
+    const int nss = t == 0 ? 9 : 6;
+    int n = 0;
+    for (int i = 0; i < nss; ++i) {
+        const int k = ss[i].kind;
+        if (which == 0 || (which == 1 && (k == 0 || k == 1)) || (which == 2 && (k == 0 || k == 2))) o[n++] = ss[i];
+    }
+    return n;
+}
+
+// Expected sign of member j of an orbit for operator `which` (0 A, 1 Dx, 2 Dy).
+double member_sign(const Orbit &o, int which, int j) {
+    if (which == 0) return 1.0;
+    if (o.kind == 0) {
+        const bool xneg = (j >= 2), yneg = (j == 1 || j == 3);
+        return which == 1 ? (xneg ? -1.0 : 1.0) : (yneg ? -1.0 : 1.0);
+    }
+    return j == 0 ? 1.0 : -1.0;  // the antisymmetric direction of a pair
+}
+
+}  // namespace
+
+bool acoustic_sym_weights(double rho_x, double rho_y, AcousticSymWeights<double> &w) {
+    bool ok = true;
+    for (int t = 0; t < 3; ++t) {
+        double op[2][3][25];
+        node_type_operators(t, rho_x, rho_y, op);
+        double big = 0.0;
+        for (int c = 0; c < 2; ++c)
+            for (int q = 0; q < 3; ++q)
+                for (int k = 0; k < 25; ++k) big = std::fmax(big, std::fabs(op[c][q][k]));
+        for (int c = 0; c < 2; ++c)
+            for (int which = 0; which < 3; ++which) {
+                Orbit o[9];
+                const int no = orbits(t, which, o);
+                double *dst = nullptr;
+                if (t == 0) dst = which == 0 ? w.cA[c] : (which == 1 ? w.cDx[c] : w.cDy[c]);
+                if (t == 1) dst = which == 0 ? w.xA[c] : (which == 1 ? w.xDx[c] : w.xDy[c]);
+                if (t == 2) dst = which == 0 ? w.yA[c] : (which == 1 ? w.yDx[c] : w.yDy[c]);
+                bool used[25] = {false};
+                for (int i = 0; i < no; ++i) {
+                    const int nm = o[i].kind == 0 ? 4 : (o[i].kind == 3 ? 1 : 2);
+                    const double rep = op[c][which][o[i].m[0]];
+                    dst[i] = rep;
+                    for (int j = 0; j < nm; ++j) {
+                        used[o[i].m[j]] = true;
+                        if (std::fabs(op[c][which][o[i].m[j]] - member_sign(o[i], which, j) * rep) > 1e-12 * big)
+                            ok = false;
+                    }
+                }
+                // every weight outside the listed orbits must vanish
+                for (int k = 0; k < 25; ++k)
+                    if (!used[k] && std::fabs(op[c][which][k]) > 1e-12 * big) ok = false;
+            }
+    }
+    return ok;
 }
 
 }  // namespace af
