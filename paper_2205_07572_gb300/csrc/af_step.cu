@@ -48,41 +48,71 @@ __device__ __forceinline__ int dir_index(int sx, int sy) {
     return 4 + (sx > 0 ? 1 : 0) + (sy > 0 ? 2 : 0);
 }
 
-// Stage the window of node lines [x0-1, x1+1] x [y0-1, y1+1] of every plane.
+__device__ __forceinline__ void cp_async(float *smem, const float *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async(double *smem, const double *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Lattice offset (within the state) of window entry (li, lj) of `patch`:
+// from the same-level neighbour in that direction if there is one, else
+// from the patch itself (its interior or its ghost ring).
+template <typename T>
+__device__ __forceinline__ int64_t window_source(const StepArgs<T> &A, int patch, const int *s_nbr, int li, int lj) {
+    const int n = A.n, W = n + 2 * kGhost + 1;
+    const int64_t pw = (int64_t)A.ncomp * kPlanes * A.plane;
+    const int sx = li < 0 ? -1 : (li >= n ? 1 : 0);
+    const int sy = lj < 0 ? -1 : (lj >= n ? 1 : 0);
+    int src = patch, si = li, sj = lj;
+    if (sx | sy) {
+        const int nb = s_nbr[dir_index(sx, sy)];
+        if (nb >= 0) {
+            src = nb;
+            si = li - sx * n;
+            sj = lj - sy * n;
+        }
+    }
+    return (int64_t)src * pw + (int64_t)(sj + kGhost) * W + (si + kGhost);
+}
+
+// Stage the window of node lines [x0-1, x1+1] x [y0-1, y1+1] of every plane
+// with asynchronous global->shared copies (all in flight at once), then wait.
 // For a patch that advances its ghost layer (copy_all), the tile also writes
 // the staged entries of its share of the patch's lattice to the output, so
 // the output holds a complete patch (advanced entries are overwritten later).
 template <typename T, int NT, int WN>
 __device__ __forceinline__ void stage(const StepArgs<T> &A, int patch, const int *s_nbr, int x0, int y0,
                                       int x1, int y1, int ww, int wh, bool copy_all, T *Sin) {
-    const int n = A.n, W = n + 2 * kGhost + 1;
-    const int64_t pw = (int64_t)A.ncomp * kPlanes * A.plane;
     const int ncp = A.ncomp * kPlanes;
     constexpr int wsz = WN * WN;
     for (int pos = threadIdx.x; pos < ww * wh; pos += NT) {
         const int row = pos / ww, col = pos - row * ww;
-        const int li = x0 - 1 + col, lj = y0 - 1 + row;
-        const int sx = li < 0 ? -1 : (li >= n ? 1 : 0);
-        const int sy = lj < 0 ? -1 : (lj >= n ? 1 : 0);
-        int src = patch, si = li, sj = lj;
-        if (sx | sy) {
-            const int nb = s_nbr[dir_index(sx, sy)];
-            if (nb >= 0) {
-                src = nb;
-                si = li - sx * n;
-                sj = lj - sy * n;
-            }
-        }
-        const T *g = A.in + (int64_t)src * pw + (int64_t)(sj + kGhost) * W + (si + kGhost);
+        const T *g = A.in + window_source(A, patch, s_nbr, x0 - 1 + col, y0 - 1 + row);
         T *s = Sin + row * WN + col;
 #pragma unroll 4
-        for (int cp = 0; cp < ncp; ++cp) s[cp * wsz] = __ldg(g + cp * A.plane);
-        if (copy_all) {
-            // share of the lattice [-2, n+2]^2 this tile copies
-            const int cxlo = x0 == -1 ? -2 : x0, cxhi = x1 == n + 1 ? n + 3 : x1;
-            const int cylo = y0 == -1 ? -2 : y0, cyhi = y1 == n + 1 ? n + 3 : y1;
+        for (int cp = 0; cp < ncp; ++cp) cp_async(s + cp * wsz, g + cp * A.plane);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (copy_all) {
+        const int n = A.n, W = n + 2 * kGhost + 1;
+        const int64_t pw = (int64_t)A.ncomp * kPlanes * A.plane;
+        // share of the lattice [-2, n+2]^2 this tile copies
+        const int cxlo = x0 == -1 ? -2 : x0, cxhi = x1 == n + 1 ? n + 3 : x1;
+        const int cylo = y0 == -1 ? -2 : y0, cyhi = y1 == n + 1 ? n + 3 : y1;
+        for (int pos = threadIdx.x; pos < ww * wh; pos += NT) {
+            const int row = pos / ww, col = pos - row * ww;
+            const int li = x0 - 1 + col, lj = y0 - 1 + row;
             if (li >= cxlo && li < cxhi && lj >= cylo && lj < cyhi) {
                 T *o = A.out + (int64_t)patch * pw + (int64_t)(lj + kGhost) * W + (li + kGhost);
+                const T *s = Sin + row * WN + col;
                 for (int cp = 0; cp < ncp; ++cp) o[cp * A.plane] = s[cp * wsz];
             }
         }
