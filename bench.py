@@ -136,6 +136,9 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
     dt = CFL * grid.dx
     cfg = af.config(af.ACOUSTICS, af.F32 if prec == "f32" else af.F64, N_CELLS, c=1.0)
     run = UniformRun(cfg, P_SIDE, P_SIDE, grid.dx, grid.dy, dt, state=st)
+    # autotune the tile shape on this workload (outside the timed region)
+    from paper_2205_07572_gb300 import tune
+    best, table = tune.tune(run, steps=3 if prec == "f64" else 10, warmup=1)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         run.step()
@@ -162,10 +165,14 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
     cells = grid.npatch * N_CELLS * N_CELLS
     # sanity: the state stays finite
     assert torch.isfinite(run.state).all().item()
-    return {"ms": ms, "cells": cells, "clocks": ck, "nwork": run.nwork, "run": run}
+    tilings = af.step_tilings()
+    return {"ms": ms, "cells": cells, "clocks": ck, "nwork": run.nwork, "run": run,
+            "tiling": {"index": best, "tile": tilings[best][:2], "threads": tilings[best][2],
+                       "persistent": bool(tilings[best][3]),
+                       "tuned_ms": {str(tilings[k]): round(v, 4) for k, v in table.items()}}}
 
 
-def run_e2e(prec: str, steps: int, warmup: int):
+def run_e2e(prec: str, steps: int, warmup: int, tiling=None):
     """Same step through the public API with the state kept in pinned HOST
     memory: every step copies it host->device, runs af_patch_step, and copies
     the result back (host<->device copies inside the timed region)."""
@@ -175,13 +182,13 @@ def run_e2e(prec: str, steps: int, warmup: int):
     dt = CFL * grid.dx
     cfg = af.config(af.ACOUSTICS, af.F32 if prec == "f32" else af.F64, N_CELLS, c=1.0)
     from paper_2205_07572_gb300.uniform import UniformRun
-    run = UniformRun(cfg, P_SIDE, P_SIDE, grid.dx, grid.dy, dt, state=None)
+    run = UniformRun(cfg, P_SIDE, P_SIDE, grid.dx, grid.dy, dt, state=None, tiling=tiling)
     host = torch.from_numpy(st.reshape(run.a.shape)).pin_memory()
     stream = torch.cuda.current_stream()
 
     def one():
         run.a.copy_(host, non_blocking=True)
-        af.patch_step(cfg, run.work, run.nwork, run.a, run.b, dt, grid.dx, grid.dy, None, stream)
+        af.patch_step(cfg, run.work, run.nwork, run.a, run.b, dt, grid.dx, grid.dy, None, stream, tiling=run.tiling)
         host.copy_(run.b, non_blocking=True)
 
     for _ in range(warmup):
@@ -317,7 +324,7 @@ def main():
         if rank == 0:
             print(json.dumps({"prec": args.prec, "ms_per_step": r["ms"],
                               "value": world * r["cells"] / (r["ms"] * 1e-3), "unit": "cell updates/s",
-                              "clocks": r["clocks"]}), flush=True)
+                              "clocks": r["clocks"], "tiling": r["tiling"]}), flush=True)
         return
     r32 = run_ours("f32", args.steps, warm, rank, world, dist)
     r64 = run_ours("f64", max(3, args.steps // 4), warm, rank, world, dist)
@@ -328,7 +335,7 @@ def main():
     line = None
     if rank == 0:
         extras = not args.no_extras
-        e2e = run_e2e("f32", max(3, args.steps // 4), 2) if extras else None
+        e2e = run_e2e("f32", max(3, args.steps // 4), 2, r32["tiling"]["index"]) if extras else None
         lit32 = literal_config2("f32", 50) if extras else None
         lit64 = literal_config2("f64", 10) if extras else None
         cpu = None if (args.no_cpu_baseline or not extras) else oracle_sample(20)
@@ -339,7 +346,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "patches": P_SIDE * P_SIDE, "cells_per_step": cells,
                        "l2": "inputs larger than L2 (1.1 GB FP32 state per copy)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "tiling_f32": r32["tiling"], "tiling_f64": r64["tiling"]},
             "fp64": {"value": v64, "unit": "cell updates/s", "ms_per_step": r64["ms"],
                      "achieved_gbs": cells * BYTES_PER_CELL["f64"] / (r64["ms"] * 1e-3) / 1e9,
                      "clocks": r64["clocks"]},

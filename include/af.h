@@ -102,12 +102,36 @@ int64_t af_patch_words(int32_t n, int32_t ncomp);
  * ghost ring (filled by af_fill_ghosts) and also advances its first ghost
  * layer, which subcycling needs at intermediate times (Section 3.2).
  *
- * Patches are split into tiles of at most 32 x 32 cells.  Writes at most
+ * Patches are split into tiles of the default tiling for cfg (see
+ * af_step_tilings).  Writes at most
  * `capacity` entries to h_work and the count to *nwork; returns AF_ERR_ARG if
  * capacity is too small (*nwork then holds the required count). */
 af_status af_build_step_work(const af_config *cfg, int32_t npatch, const int32_t *h_patch,
                              const int32_t *h_level, const int32_t *h_nbr, af_work *h_work,
                              int32_t capacity, int32_t *nwork);
+
+/* Compiled tile shapes of af_patch_step.  A tiling splits every patch (or
+ * its interior plus first ghost layer) into near-equal tiles of at most
+ * tile_x x tile_y cells, each advanced by one CTA of `threads` threads;
+ * persistent = CTAs loop over tiles with the next tile's copies in flight.
+ * Which is fastest depends on the patch size, equation and precision; the
+ * autotuner (paper_2205_07572_gb300/tune.py) times them. */
+typedef struct {
+    int32_t tile_x, tile_y;
+    int32_t threads;
+    int32_t persistent;
+} af_tiling;
+
+/* Writes up to `capacity` compiled tilings to `out`; returns how many exist. */
+int32_t af_step_tilings(af_tiling *out, int32_t capacity);
+
+/* Index of the tiling af_build_step_work / af_patch_step use for cfg. */
+int32_t af_step_default_tiling(const af_config *cfg);
+
+/* af_build_step_work with an explicit tiling (index into af_step_tilings). */
+af_status af_build_step_work_tiled(const af_config *cfg, int32_t tiling, int32_t npatch, const int32_t *h_patch,
+                                   const int32_t *h_level, const int32_t *h_nbr, af_work *h_work,
+                                   int32_t capacity, int32_t *nwork);
 
 /* One Active Flux time step (Section 2) for every work item:
  *   1. point values at t^{n+1/2}, t^{n+1} at corners and edge midpoints from
@@ -135,6 +159,12 @@ af_status af_build_step_work(const af_config *cfg, int32_t npatch, const int32_t
 af_status af_patch_step(const af_config *cfg, int32_t nwork, const af_work *d_work,
                         const void *d_in, void *d_out, double dt0, double dx0, double dy0,
                         double *d_flux_reg, void *stream);
+
+/* af_patch_step with an explicit tiling; d_work must have been built with the
+ * same tiling (tiles larger than the tiling's maximum are skipped). */
+af_status af_patch_step_tiled(const af_config *cfg, int32_t tiling, int32_t nwork, const af_work *d_work,
+                              const void *d_in, void *d_out, double dt0, double dx0, double dy0,
+                              double *d_flux_reg, void *stream);
 
 
 /* ======================================================================

@@ -61,6 +61,16 @@ def lib():
         L.af_patch_step.restype = C.c_int
         L.af_patch_step.argtypes = [C.POINTER(Config), C.c_int32, _VP, _VP, _VP, C.c_double, C.c_double,
                                     C.c_double, _VP, _VP]
+        L.af_build_step_work_tiled.restype = C.c_int
+        L.af_build_step_work_tiled.argtypes = [C.POINTER(Config), C.c_int32, C.c_int32, _IP, _IP, _IP,
+                                               C.POINTER(Work), C.c_int32, _IP]
+        L.af_patch_step_tiled.restype = C.c_int
+        L.af_patch_step_tiled.argtypes = [C.POINTER(Config), C.c_int32, C.c_int32, _VP, _VP, _VP, C.c_double,
+                                          C.c_double, C.c_double, _VP, _VP]
+        L.af_step_tilings.restype = C.c_int32
+        L.af_step_tilings.argtypes = [C.c_void_p, C.c_int32]
+        L.af_step_default_tiling.restype = C.c_int32
+        L.af_step_default_tiling.argtypes = [C.POINTER(Config)]
         _register_more(L)
         _lib = L
     return _lib
@@ -119,28 +129,52 @@ def patch_words(n: int, ncomp: int) -> int:
     return int(lib().af_patch_words(n, ncomp))
 
 
-def build_step_work(cfg: Config, patches, levels=None, nbr=None) -> np.ndarray:
+class Tiling(C.Structure):
+    _fields_ = [("tile_x", C.c_int32), ("tile_y", C.c_int32), ("threads", C.c_int32), ("persistent", C.c_int32)]
+
+
+def step_tilings():
+    """Compiled tilings of af_patch_step: list of (tile_x, tile_y, threads, persistent)."""
+    L = lib()
+    n = L.af_step_tilings(None, 0)
+    buf = (Tiling * n)()
+    L.af_step_tilings(buf, n)
+    return [(t.tile_x, t.tile_y, t.threads, t.persistent) for t in buf]
+
+
+def default_tiling(cfg: Config) -> int:
+    return int(lib().af_step_default_tiling(C.byref(cfg)))
+
+
+def build_step_work(cfg: Config, patches, levels=None, nbr=None, tiling=None) -> np.ndarray:
     """Host work list of af_patch_step as a uint8 array (64 bytes per entry)."""
     patches = np.ascontiguousarray(patches, dtype=np.int32)
     lv = None if levels is None else np.ascontiguousarray(levels, dtype=np.int32)
     nb = None if nbr is None else np.ascontiguousarray(nbr, dtype=np.int32).reshape(-1)
     npatch = len(patches)
     L = lib()
+    k = default_tiling(cfg) if tiling is None else int(tiling)
     cnt = C.c_int32(0)
     ip = lambda a: None if a is None else a.ctypes.data_as(_IP)
-    st = L.af_build_step_work(C.byref(cfg), npatch, ip(patches), ip(lv), ip(nb), None, 0, C.byref(cnt))
+    st = L.af_build_step_work_tiled(C.byref(cfg), k, npatch, ip(patches), ip(lv), ip(nb), None, 0, C.byref(cnt))
     if st != 0 and cnt.value == 0:
         _check(st, "af_build_step_work")
     buf = (Work * max(cnt.value, 1))()
-    st = L.af_build_step_work(C.byref(cfg), npatch, ip(patches), ip(lv), ip(nb), buf, cnt.value, C.byref(cnt))
+    st = L.af_build_step_work_tiled(C.byref(cfg), k, npatch, ip(patches), ip(lv), ip(nb), buf, cnt.value,
+                                    C.byref(cnt))
     _check(st, "af_build_step_work")
     return np.frombuffer(buf, dtype=np.uint8, count=64 * cnt.value).copy()
 
 
 def patch_step(cfg: Config, work, nwork: int, state_in, state_out, dt0: float, dx0: float, dy0: float,
-               flux_reg=None, stream=None) -> None:
-    st = lib().af_patch_step(C.byref(cfg), int(nwork), ptr(work), ptr(state_in), ptr(state_out),
-                             float(dt0), float(dx0), float(dy0), ptr(flux_reg), stream_handle(stream))
+               flux_reg=None, stream=None, tiling=None) -> None:
+    if tiling is None:
+        st = lib().af_patch_step(C.byref(cfg), int(nwork), ptr(work), ptr(state_in), ptr(state_out),
+                                 float(dt0), float(dx0), float(dy0), ptr(flux_reg), stream_handle(stream))
+    else:
+        st = lib().af_patch_step_tiled(C.byref(cfg), int(tiling), int(nwork), ptr(work), ptr(state_in),
+                                       ptr(state_out), float(dt0), float(dx0), float(dy0), ptr(flux_reg),
+                                       stream_handle(stream))
     _check(st, "af_patch_step")
 
 

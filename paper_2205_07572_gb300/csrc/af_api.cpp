@@ -23,47 +23,57 @@ extern "C" int64_t af_patch_words(int32_t n, int32_t ncomp) {
     return n < 1 || ncomp < 1 ? 0 : (int64_t)ncomp * af::kPlanes * af::plane_stride(n);
 }
 
-extern "C" af_status af_build_step_work(const af_config *cfg, int32_t npatch, const int32_t *h_patch,
-                                        const int32_t *h_level, const int32_t *h_nbr, af_work *h_work,
-                                        int32_t capacity, int32_t *nwork) {
+extern "C" af_status af_build_step_work_tiled(const af_config *cfg, int32_t tiling_index, int32_t npatch,
+                                              const int32_t *h_patch, const int32_t *h_level, const int32_t *h_nbr,
+                                              af_work *h_work, int32_t capacity, int32_t *nwork) {
     using namespace af;
     if (cfg == nullptr || nwork == nullptr || npatch < 0 || capacity < 0) return AF_ERR_ARG;
     if (cfg->n < 2 || cfg->n > 64) return AF_ERR_ARG;
+    if (tiling_index < 0 || tiling_index >= kNumTilings) return AF_ERR_ARG;
     if (npatch > 0 && h_patch == nullptr) return AF_ERR_ARG;
     const int n = cfg->n;
+    const Tiling tl = tiling(tiling_index);
+    auto extended = [&](int k) {
+        if (h_nbr == nullptr) return true;
+        for (int d = 0; d < 8; ++d)
+            if (h_nbr[8 * k + d] < 0) return true;
+        return false;
+    };
     int32_t count = 0;
     for (int k = 0; k < npatch; ++k) {
-        bool ext = (h_nbr == nullptr);
-        if (!ext)
-            for (int d = 0; d < 8; ++d) ext = ext || (h_nbr[8 * k + d] < 0);
-        const int lo = ext ? -1 : 0, hi = ext ? n + 1 : n;
-        const int w = hi - lo, nt = tiles_for(w);
-        count += nt * nt;
+        const int w = extended(k) ? n + 2 : n;
+        count += ((w + tl.tmx - 1) / tl.tmx) * ((w + tl.tmy - 1) / tl.tmy);
     }
     *nwork = count;
     if (count > capacity || (count > 0 && h_work == nullptr)) return AF_ERR_ARG;
     int32_t idx = 0;
     for (int k = 0; k < npatch; ++k) {
         if (h_patch[k] < 0) return AF_ERR_ARG;
-        bool ext = (h_nbr == nullptr);
-        if (!ext)
-            for (int d = 0; d < 8; ++d) ext = ext || (h_nbr[8 * k + d] < 0);
-        const int lo = ext ? -1 : 0, hi = ext ? n + 1 : n;
-        const int w = hi - lo, nt = tiles_for(w);
-        for (int ty = 0; ty < nt; ++ty)
-            for (int tx = 0; tx < nt; ++tx) {
+        const bool ext = extended(k);
+        const int lo = ext ? -1 : 0, w = ext ? n + 2 : n;
+        const int ntx = (w + tl.tmx - 1) / tl.tmx, nty = (w + tl.tmy - 1) / tl.tmy;
+        for (int ty = 0; ty < nty; ++ty)
+            for (int tx = 0; tx < ntx; ++tx) {
                 af_work &o = h_work[idx++];
                 std::memset(&o, 0, sizeof(o));
                 o.patch = h_patch[k];
                 o.level = h_level ? h_level[k] : 0;
                 for (int d = 0; d < 8; ++d) o.nbr[d] = h_nbr ? h_nbr[8 * k + d] : -1;
-                // near-equal split of [lo, hi) into nt pieces
-                o.x0 = (int16_t)(lo + (w * tx) / nt);
-                o.x1 = (int16_t)(lo + (w * (tx + 1)) / nt);
-                o.y0 = (int16_t)(lo + (w * ty) / nt);
-                o.y1 = (int16_t)(lo + (w * (ty + 1)) / nt);
+                // near-equal split of [lo, lo + w) into ntx x nty pieces
+                o.x0 = (int16_t)(lo + (w * tx) / ntx);
+                o.x1 = (int16_t)(lo + (w * (tx + 1)) / ntx);
+                o.y0 = (int16_t)(lo + (w * ty) / nty);
+                o.y1 = (int16_t)(lo + (w * (ty + 1)) / nty);
                 o.flags = ext ? 1 : 0;
             }
     }
     return AF_OK;
+}
+
+extern "C" af_status af_build_step_work(const af_config *cfg, int32_t npatch, const int32_t *h_patch,
+                                        const int32_t *h_level, const int32_t *h_nbr, af_work *h_work,
+                                        int32_t capacity, int32_t *nwork) {
+    if (cfg == nullptr) return AF_ERR_ARG;
+    return af_build_step_work_tiled(cfg, af::default_tiling(cfg->n), npatch, h_patch, h_level, h_nbr, h_work,
+                                    capacity, nwork);
 }

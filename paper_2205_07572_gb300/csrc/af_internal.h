@@ -95,6 +95,23 @@ void advection_weights(double nu_x, double nu_y, AdvectionWeights<double> &w);
 
 namespace af {
 
+// Tile shapes compiled into af_patch_step: at most tmx x tmy cells per tile,
+// `threads` per CTA; persistent = one CTA per available slot looping over
+// tiles with the next tile's copies in flight.
+struct Tiling {
+    int tmx, tmy, threads, persistent;
+};
+constexpr int kNumTilings = 9;
+AF_HD constexpr Tiling tiling(int k) {
+    constexpr Tiling t[kNumTilings] = {
+        {32, 32, 256, 0}, {32, 16, 192, 0}, {32, 16, 160, 0}, {32, 8, 128, 0}, {16, 16, 128, 0},
+        {32, 16, 256, 1}, {18, 18, 256, 0}, {18, 10, 192, 0}, {10, 10, 128, 0}};
+    return t[k];
+}
+// Default tiling for patches of n cells (overridden per configuration by
+// the autotuner through the *_tiled entry points).
+inline int default_tiling(int n) { return n <= 8 ? 8 : (n <= 16 ? 6 : 0); }
+
 // Split `w` cells into ceil(w / kTileMax) tiles of near-equal size.
 inline int tiles_for(int w) { return (w + kTileMax - 1) / kTileMax; }
 inline int tile_size_max(int w) {

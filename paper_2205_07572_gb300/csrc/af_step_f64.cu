@@ -1,0 +1,11 @@
+// Instantiates the af_patch_step launchers for double state arrays (the
+// kernels themselves live in af_step_kernels.cuh); one translation unit per
+// precision so the two compile in parallel.
+#include "af_step_kernels.cuh"
+
+namespace af {
+template af_status launch_step<double, AF_ACOUSTICS>(int, const StepArgs<double> &,
+                                                    const WeightsOf<double, AF_ACOUSTICS>::type &, int, cudaStream_t);
+template af_status launch_step<double, AF_ADVECTION>(int, const StepArgs<double> &,
+                                                    const WeightsOf<double, AF_ADVECTION>::type &, int, cudaStream_t);
+}  // namespace af

@@ -1,0 +1,494 @@
+// Device side of af_patch_step: one Active Flux time step (Section 2 of
+// arXiv 2205.07572) on GB300 (sm_103a).  Included by af_step_f32.cu and
+// af_step_f64.cu, which instantiate the launchers for one precision each.
+//
+// One CTA advances one tile (<= TMX x TMY cells) of one patch:
+//   stage  - the tile's degrees of freedom plus a one-cell halo are copied to
+//            shared memory with asynchronous copies; halo entries in a
+//            direction with a same-level neighbour are read straight from that
+//            neighbour's interior (the same-level ghost copy of Section 3.1
+//            fused into the load), other directions from the patch's own
+//            ghost ring;
+//   nodes  - one thread per node-cell evolves the corner, left-edge midpoint
+//            and bottom-edge midpoint of its cell to t^{n+1/2} and t^{n+1}
+//            (Eq. advection-update / Eq. ERFormula) as constant-weight
+//            stencils, keeps T = Q^n + 4 Q^{n+1/2} + Q^{n+1} in shared memory
+//            and writes Q^{n+1} to the output;
+//   update - one thread per cell forms the four face fluxes by the space-time
+//            Simpson rule (Eq. Simpson-2d: f is linear, so the 3 x 3 sum is
+//            f((T_lo + 4 T_mid + T_hi) / 36)) and applies Eq. 2dfv.
+// No tensor cores: the stencil is not a dense contraction.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "af_internal.h"
+
+namespace af {
+
+template <typename T>
+struct StepArgs {
+    const af_work *work;
+    const T *in;
+    T *out;
+    double *freg;
+    int64_t plane;   // plane stride (elements)
+    int n, ncomp;
+    T dtdx, dtdy;    // dt/dx and dt/dy (the same on every level)
+    T fx, fy;        // flux scale: advection a/36, b/36; acoustics c/36
+    double dt0;      // level-0 time step (flux registers)
+};
+
+template <typename T, int EQ>
+struct WeightsOf;
+template <typename T>
+struct WeightsOf<T, AF_ACOUSTICS> { using type = AcousticSymWeights<T>; };
+template <typename T>
+struct WeightsOf<T, AF_ADVECTION> { using type = AdvectionWeights<T>; };
+
+// Launch one af_patch_step with compiled tiling k (host; af_step_f32/f64.cu).
+template <typename T, int EQ>
+af_status launch_step(int k, const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W, int nwork,
+                      cudaStream_t stream);
+
+namespace dev {
+
+__device__ __forceinline__ int dir_index(int sx, int sy) {
+    if (sy == 0) return sx < 0 ? 0 : 1;
+    if (sx == 0) return sy < 0 ? 2 : 3;
+    return 4 + (sx > 0 ? 1 : 0) + (sy > 0 ? 2 : 0);
+}
+
+__device__ __forceinline__ void cp_async(float *smem, const float *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async(double *smem, const double *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Issue (without waiting) the copies of the window of node lines
+// [x0-1, x1+1] x [y0-1, y1+1] of every plane of work item wk into Sin
+// (row pitch WX, plane size WSZ).
+template <typename T, int NT, int WX, int WSZ>
+__device__ __forceinline__ void stage_issue(const StepArgs<T> &A, const af_work &wk, T *Sin) {
+    const int patch = wk.patch, x0 = wk.x0, y0 = wk.y0;
+    const int ww = wk.x1 - x0 + 3, wh = wk.y1 - y0 + 3;
+    int nb[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) nb[d] = wk.nbr[d];
+    const int n = A.n, W = n + 2 * kGhost + 1;
+    const int64_t pw = (int64_t)A.ncomp * kPlanes * A.plane;
+    const int ncp = A.ncomp * kPlanes;
+    for (int pos = threadIdx.x; pos < ww * wh; pos += NT) {
+        const int row = pos / ww, col = pos - row * ww;
+        const int li = x0 - 1 + col, lj = y0 - 1 + row;
+        const int sx = li < 0 ? -1 : (li >= n ? 1 : 0);
+        const int sy = lj < 0 ? -1 : (lj >= n ? 1 : 0);
+        int src = patch, si = li, sj = lj;
+        if (sx | sy) {
+            const int d = dir_index(sx, sy);
+            int q = nb[0];
+#pragma unroll
+            for (int e = 1; e < 8; ++e) q = (d == e) ? nb[e] : q;
+            if (q >= 0) {
+                src = q;
+                si = li - sx * n;
+                sj = lj - sy * n;
+            }
+        }
+        const T *g = A.in + (int64_t)src * pw + (int64_t)(sj + kGhost) * W + (si + kGhost);
+        T *sp = Sin + row * WX + col;
+#pragma unroll 4
+        for (int cp = 0; cp < ncp; ++cp) cp_async(sp + cp * WSZ, g + cp * A.plane);
+    }
+}
+
+// For a patch that advances its ghost layer, write the staged entries of the
+// tile's share of the patch lattice to the output, so the output holds a
+// complete patch (advanced entries are overwritten afterwards).
+template <typename T, int NT, int WX, int WSZ>
+__device__ __forceinline__ void stage_copy_out(const StepArgs<T> &A, const af_work &wk, const T *Sin) {
+    const int patch = wk.patch, x0 = wk.x0, y0 = wk.y0, x1 = wk.x1, y1 = wk.y1;
+    const int ww = x1 - x0 + 3, wh = y1 - y0 + 3;
+    const int n = A.n, W = n + 2 * kGhost + 1;
+    const int64_t pw = (int64_t)A.ncomp * kPlanes * A.plane;
+    const int ncp = A.ncomp * kPlanes;
+    const int cxlo = x0 == -1 ? -2 : x0, cxhi = x1 == n + 1 ? n + 3 : x1;
+    const int cylo = y0 == -1 ? -2 : y0, cyhi = y1 == n + 1 ? n + 3 : y1;
+    for (int pos = threadIdx.x; pos < ww * wh; pos += NT) {
+        const int row = pos / ww, col = pos - row * ww;
+        const int li = x0 - 1 + col, lj = y0 - 1 + row;
+        if (li >= cxlo && li < cxhi && lj >= cylo && lj < cyhi) {
+            T *o = A.out + (int64_t)patch * pw + (int64_t)(lj + kGhost) * W + (li + kGhost);
+            const T *sp = Sin + row * WX + col;
+            for (int cp = 0; cp < ncp; ++cp) o[cp * A.plane] = sp[cp * WSZ];
+        }
+    }
+}
+
+// Position of block entry k (see af_internal.h) relative to (i-1, j-1).
+__host__ __device__ constexpr int blk_plane(int k) {
+    return k < 4 ? kAvg : (k < 13 ? kCorner : (k < 19 ? kXmid : kYmid));
+}
+__host__ __device__ constexpr int blk_a(int k) {
+    return k < 4 ? (k & 1) : (k < 13 ? (k - 4) % 3 : (k < 19 ? (k - 13) % 3 : (k - 19) % 2));
+}
+__host__ __device__ constexpr int blk_b(int k) {
+    return k < 4 ? (k >> 1) : (k < 13 ? (k - 4) / 3 : (k < 19 ? (k - 13) / 3 : (k - 19) / 2));
+}
+
+// Orbit sums of a quad (++, +-, -+, --): symmetric, x-antisymmetric,
+// y-antisymmetric parts.
+template <typename T>
+__device__ __forceinline__ void quad(T pp, T pm, T mp, T mm, T &ss, T &as, T &sa) {
+    const T a = pp + pm, b = mp + mm;
+    ss = a + b;
+    as = a - b;
+    sa = (pp - pm) + (mp - mm);
+}
+
+template <int N, typename T>
+__device__ __forceinline__ T dot(const T *w, const T *v) {
+    T s = w[0] * v[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k) s = fma(w[k], v[k], s);
+    return s;
+}
+
+// Acoustic node evaluation of one node-cell item (window coords qi, rj of
+// node line (i, j)) with the mirror-folded weights: the 25 block values of
+// each input component are combined into the orbit sums of the three nodes,
+// then p += A.SS_p + Dx.AS_u + Dy.SA_v, u += A.SS_u + Dx.AS_p,
+// v += A.SS_v + Dy.SA_p (the evolution operators of Eq. ERFormula).
+// out: T and Q^{n+1} of corner (tc, nc), left-edge mid (tx, nx) and
+// bottom-edge mid (ty, ny) for p, u, v.
+template <typename T, int WX, int WSZ>
+__device__ __forceinline__ void acoustic_item(const AcousticSymWeights<T> &W, const T *Sin, int qi, int rj,
+                                              T tc[3], T nc[3], T tx[3], T nx[3], T ty[3], T ny[3]) {
+#pragma unroll
+    for (int o = 0; o < 3; ++o) tc[o] = nc[o] = tx[o] = nx[o] = ty[o] = ny[o] = T(0);
+    const T *base = Sin + (rj - 1) * WX + (qi - 1);
+#pragma unroll
+    for (int ci = 0; ci < 3; ++ci) {
+        T b[25];
+#pragma unroll
+        for (int k = 0; k < 25; ++k) b[k] = base[(ci * kPlanes + blk_plane(k)) * WSZ + blk_b(k) * WX + blk_a(k)];
+        // ---- corner node
+        T css[9], cas[6], csa[6];
+        quad(b[3], b[1], b[2], b[0], css[0], cas[0], csa[0]);
+        quad(b[12], b[6], b[10], b[4], css[1], cas[1], csa[1]);
+        quad(b[18], b[15], b[16], b[13], css[2], cas[2], csa[2]);
+        quad(b[24], b[20], b[23], b[19], css[3], cas[3], csa[3]);
+        css[4] = b[9] + b[7];   cas[4] = b[9] - b[7];
+        css[5] = b[22] + b[21]; cas[5] = b[22] - b[21];
+        css[6] = b[11] + b[5];  csa[4] = b[11] - b[5];
+        css[7] = b[17] + b[14]; csa[5] = b[17] - b[14];
+        css[8] = b[8];
+        // ---- left-edge midpoint
+        T xss[6], xas[4], xsa[3];
+        quad(b[12], b[9], b[10], b[7], xss[0], xas[0], xsa[0]);
+        quad(b[24], b[22], b[23], b[21], xss[1], xas[1], xsa[1]);
+        xss[2] = b[3] + b[2];   xas[2] = b[3] - b[2];
+        xss[3] = b[18] + b[16]; xas[3] = b[18] - b[16];
+        xss[4] = b[11] + b[8];  xsa[2] = b[11] - b[8];
+        xss[5] = b[17];
+        // ---- bottom-edge midpoint
+        T yss[6], yas[3], ysa[4];
+        quad(b[12], b[6], b[11], b[5], yss[0], yas[0], ysa[0]);
+        quad(b[18], b[15], b[17], b[14], yss[1], yas[1], ysa[1]);
+        yss[2] = b[9] + b[8];   yas[2] = b[9] - b[8];
+        yss[3] = b[3] + b[1];   ysa[2] = b[3] - b[1];
+        yss[4] = b[24] + b[20]; ysa[3] = b[24] - b[20];
+        yss[5] = b[22];
+        if (ci == 0) {  // p: A on p; Dx.AS_p -> u; Dy.SA_p -> v
+            tc[0] += dot<9>(W.cA[0], css); nc[0] += dot<9>(W.cA[1], css);
+            tx[0] += dot<6>(W.xA[0], xss); nx[0] += dot<6>(W.xA[1], xss);
+            ty[0] += dot<6>(W.yA[0], yss); ny[0] += dot<6>(W.yA[1], yss);
+            tc[1] += dot<6>(W.cDx[0], cas); nc[1] += dot<6>(W.cDx[1], cas);
+            tx[1] += dot<4>(W.xDx[0], xas); nx[1] += dot<4>(W.xDx[1], xas);
+            ty[1] += dot<3>(W.yDx[0], yas); ny[1] += dot<3>(W.yDx[1], yas);
+            tc[2] += dot<6>(W.cDy[0], csa); nc[2] += dot<6>(W.cDy[1], csa);
+            tx[2] += dot<3>(W.xDy[0], xsa); nx[2] += dot<3>(W.xDy[1], xsa);
+            ty[2] += dot<4>(W.yDy[0], ysa); ny[2] += dot<4>(W.yDy[1], ysa);
+        } else if (ci == 1) {  // u: A on u; Dx.AS_u -> p
+            tc[1] += dot<9>(W.cA[0], css); nc[1] += dot<9>(W.cA[1], css);
+            tx[1] += dot<6>(W.xA[0], xss); nx[1] += dot<6>(W.xA[1], xss);
+            ty[1] += dot<6>(W.yA[0], yss); ny[1] += dot<6>(W.yA[1], yss);
+            tc[0] += dot<6>(W.cDx[0], cas); nc[0] += dot<6>(W.cDx[1], cas);
+            tx[0] += dot<4>(W.xDx[0], xas); nx[0] += dot<4>(W.xDx[1], xas);
+            ty[0] += dot<3>(W.yDx[0], yas); ny[0] += dot<3>(W.yDx[1], yas);
+        } else {  // v: A on v; Dy.SA_v -> p
+            tc[2] += dot<9>(W.cA[0], css); nc[2] += dot<9>(W.cA[1], css);
+            tx[2] += dot<6>(W.xA[0], xss); nx[2] += dot<6>(W.xA[1], xss);
+            ty[2] += dot<6>(W.yA[0], yss); ny[2] += dot<6>(W.yA[1], yss);
+            tc[0] += dot<6>(W.cDy[0], csa); nc[0] += dot<6>(W.cDy[1], csa);
+            tx[0] += dot<3>(W.xDy[0], xsa); nx[0] += dot<3>(W.xDy[1], xsa);
+            ty[0] += dot<4>(W.yDy[0], ysa); ny[0] += dot<4>(W.yDy[1], ysa);
+        }
+    }
+}
+
+// Advection: value of the reconstruction of window cell (cq, cr) with weights w.
+template <typename T, int WX, int WSZ>
+__device__ __forceinline__ T adv_eval(const T *w, const T *Sin, int cq, int cr) {
+    const int o = cr * WX + cq;
+    const T *A = Sin + kAvg * WSZ, *C = Sin + kCorner * WSZ, *X = Sin + kXmid * WSZ, *Y = Sin + kYmid * WSZ;
+    T v = w[0] * A[o];
+    v = fma(w[1], C[o], v);
+    v = fma(w[2], C[o + 1], v);
+    v = fma(w[3], C[o + WX], v);
+    v = fma(w[4], C[o + WX + 1], v);
+    v = fma(w[5], X[o], v);
+    v = fma(w[6], X[o + 1], v);
+    v = fma(w[7], Y[o], v);
+    v = fma(w[8], Y[o + WX], v);
+    return v;
+}
+
+// Point values (Eq. advection-update / Eq. ERFormula), then fluxes (Eq.
+// Simpson-2d) and the update (Eq. 2dfv) of one staged tile.  Sin: window
+// (pitch WX, plane size WSZ); ST: T arrays (pitch TX, size TSZ).
+template <typename T, int EQ, int NT, int WX, int WSZ, int TX, int TSZ>
+__device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W,
+                                             const T *Sin, T *ST, int patch, int level, int x0, int x1, int y0,
+                                             int y1) {
+    constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
+    const int tw = x1 - x0, th = y1 - y0;
+    const int n = A.n, W_ = n + 2 * kGhost + 1;
+    const int64_t pw = (int64_t)ncomp * kPlanes * A.plane;
+    T *outp = A.out + (int64_t)patch * pw;
+    // node lines stored by this tile: [x0, x1) plus x1 itself when the tile
+    // ends on the outer edge of the advanced first ghost layer
+    const int sxhi = (x1 == n + 1) ? x1 : x1 - 1;
+    const int syhi = (y1 == n + 1) ? y1 : y1 - 1;
+
+    // ---- point values
+    const int nitems = (tw + 1) * (th + 1);
+    for (int it = threadIdx.x; it < nitems; it += NT) {
+        const int jj = it / (tw + 1), ii = it - jj * (tw + 1);
+        const int i = x0 + ii, j = y0 + jj;
+        const int qi = ii + 1, rj = jj + 1;
+        const bool hx = j < y1, hy = i < x1;            // edge midpoints that exist
+        const bool st_x = i <= sxhi, st_y = j <= syhi;  // stored lines
+        const int64_t lo = (int64_t)(j + kGhost) * W_ + (i + kGhost);
+        const int so = jj * TX + ii;
+        if constexpr (EQ == AF_ACOUSTICS) {
+            T tc[3], nc[3], tx[3], nx[3], ty[3], ny[3];
+            acoustic_item<T, WX, WSZ>(W, Sin, qi, rj, tc, nc, tx, nx, ty, ny);
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                ST[(o * 3 + 0) * TSZ + so] = tc[o];
+                ST[(o * 3 + 1) * TSZ + so] = tx[o];
+                ST[(o * 3 + 2) * TSZ + so] = ty[o];
+                T *po = outp + (int64_t)o * kPlanes * A.plane + lo;
+                if (st_x && st_y) po[kCorner * A.plane] = nc[o];
+                if (st_x && hx) po[kXmid * A.plane] = nx[o];
+                if (hy && st_y) po[kYmid * A.plane] = ny[o];
+            }
+        } else {
+            const int own = rj * WX + qi;
+            {
+                const T qh = adv_eval<T, WX, WSZ>(W.w[0][0], Sin, qi + W.off[0][0][0], rj + W.off[0][0][1]);
+                const T q1 = adv_eval<T, WX, WSZ>(W.w[0][1], Sin, qi + W.off[0][1][0], rj + W.off[0][1][1]);
+                ST[0 * TSZ + so] = Sin[kCorner * WSZ + own] + T(4) * qh + q1;
+                if (st_x && st_y) outp[kCorner * A.plane + lo] = q1;
+            }
+            if (hx) {
+                const T qh = adv_eval<T, WX, WSZ>(W.w[1][0], Sin, qi + W.off[1][0][0], rj + W.off[1][0][1]);
+                const T q1 = adv_eval<T, WX, WSZ>(W.w[1][1], Sin, qi + W.off[1][1][0], rj + W.off[1][1][1]);
+                ST[1 * TSZ + so] = Sin[kXmid * WSZ + own] + T(4) * qh + q1;
+                if (st_x) outp[kXmid * A.plane + lo] = q1;
+            }
+            if (hy) {
+                const T qh = adv_eval<T, WX, WSZ>(W.w[2][0], Sin, qi + W.off[2][0][0], rj + W.off[2][0][1]);
+                const T q1 = adv_eval<T, WX, WSZ>(W.w[2][1], Sin, qi + W.off[2][1][0], rj + W.off[2][1][1]);
+                ST[2 * TSZ + so] = Sin[kYmid * WSZ + own] + T(4) * qh + q1;
+                if (st_y) outp[kYmid * A.plane + lo] = q1;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- fluxes and update
+    const double dtl = ldexp(A.dt0, -level);
+    for (int it = threadIdx.x; it < tw * th; it += NT) {
+        const int jj = it / tw, ii = it - jj * tw;
+        const int i = x0 + ii, j = y0 + jj;
+        const int s00 = jj * TX + ii;
+        T Fl[3], Fr[3], Gb[3], Gt[3];
+#pragma unroll
+        for (int c = 0; c < ncomp; ++c) {
+            const T *Tc = ST + (c * 3 + 0) * TSZ, *Tx = ST + (c * 3 + 1) * TSZ, *Ty = ST + (c * 3 + 2) * TSZ;
+            // time-Simpson sums at the three points of each face
+            Fl[c] = Tc[s00] + T(4) * Tx[s00] + Tc[s00 + TX];
+            Fr[c] = Tc[s00 + 1] + T(4) * Tx[s00 + 1] + Tc[s00 + TX + 1];
+            Gb[c] = Tc[s00] + T(4) * Ty[s00] + Tc[s00 + 1];
+            Gt[c] = Tc[s00 + TX] + T(4) * Ty[s00 + TX] + Tc[s00 + TX + 1];
+        }
+        T fl[3], fr[3], gb[3], gt[3];
+        if constexpr (EQ == AF_ACOUSTICS) {
+            // f = c (u, p, 0), g = c (v, 0, p)
+            fl[0] = A.fx * Fl[1]; fl[1] = A.fx * Fl[0]; fl[2] = T(0);
+            fr[0] = A.fx * Fr[1]; fr[1] = A.fx * Fr[0]; fr[2] = T(0);
+            gb[0] = A.fy * Gb[2]; gb[1] = T(0); gb[2] = A.fy * Gb[0];
+            gt[0] = A.fy * Gt[2]; gt[1] = T(0); gt[2] = A.fy * Gt[0];
+        } else {
+            fl[0] = A.fx * Fl[0]; fr[0] = A.fx * Fr[0];
+            gb[0] = A.fy * Gb[0]; gt[0] = A.fy * Gt[0];
+        }
+        const int64_t lo = (int64_t)(j + kGhost) * W_ + (i + kGhost);
+        const int sa = (jj + 1) * WX + (ii + 1);
+#pragma unroll
+        for (int c = 0; c < ncomp; ++c) {
+            const T q = Sin[(c * kPlanes + kAvg) * WSZ + sa];
+            outp[(int64_t)(c * kPlanes + kAvg) * A.plane + lo] = q - A.dtdx * (fr[c] - fl[c]) - A.dtdy * (gt[c] - gb[c]);
+        }
+        if (A.freg != nullptr) {
+            double *fr_p = A.freg + (int64_t)patch * 4 * ncomp * n;
+            const bool iny = (j >= 0 && j < n), inx = (i >= 0 && i < n);
+#pragma unroll
+            for (int c = 0; c < ncomp; ++c) {
+                if (iny && i == 0) fr_p[(0 * ncomp + c) * n + j] += dtl * (double)fl[c];
+                if (iny && i == n - 1) fr_p[(1 * ncomp + c) * n + j] += dtl * (double)fr[c];
+                if (inx && j == 0) fr_p[(2 * ncomp + c) * n + i] += dtl * (double)gb[c];
+                if (inx && j == n - 1) fr_p[(3 * ncomp + c) * n + i] += dtl * (double)gt[c];
+            }
+        }
+    }
+}
+
+// Shared-memory geometry of a TMX x TMY tile.
+template <int TMX, int TMY>
+struct Geo {
+    static constexpr int WX = TMX + 3, WY = TMY + 3, WSZ = WX * WY;  // window
+    static constexpr int TX = TMX + 1, TY = TMY + 1, TSZ = TX * TY;  // T arrays
+};
+
+// One tile per CTA.
+template <typename T, int EQ, int NT, int TMX, int TMY>
+__global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ StepArgs<T> A,
+                                                  const __grid_constant__ typename WeightsOf<T, EQ>::type W) {
+    using Gm = Geo<TMX, TMY>;
+    constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Sin = reinterpret_cast<T *>(smem_raw);
+    T *ST = Sin + ncomp * kPlanes * Gm::WSZ;
+    const af_work &wk = A.work[blockIdx.x];
+    if (wk.x1 - wk.x0 > TMX || wk.y1 - wk.y0 > TMY) return;  // built for another tiling
+    stage_issue<T, NT, Gm::WX, Gm::WSZ>(A, wk, Sin);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (wk.flags & 1) {
+        stage_copy_out<T, NT, Gm::WX, Gm::WSZ>(A, wk, Sin);
+        __syncthreads();  // copies land before the computed values overwrite them
+    }
+    tile_compute<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ>(A, W, Sin, ST, wk.patch, wk.level, wk.x0, wk.x1,
+                                                             wk.y0, wk.y1);
+}
+
+// Persistent variant: one CTA loops over work items, double-buffering the
+// staged windows: while tile t is computed, the copies of the next tile are
+// already in flight.
+template <typename T, int EQ, int NT, int TMX, int TMY>
+__global__ void __launch_bounds__(NT) step_kernel_pipe(const __grid_constant__ StepArgs<T> A,
+                                                       const __grid_constant__ typename WeightsOf<T, EQ>::type W,
+                                                       int nwork) {
+    using Gm = Geo<TMX, TMY>;
+    constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
+    constexpr int wbuf = ncomp * kPlanes * Gm::WSZ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *S0 = reinterpret_cast<T *>(smem_raw);
+    T *ST = S0 + 2 * wbuf;
+    int t = blockIdx.x;
+    if (t >= nwork) return;
+    auto fits = [](const af_work &w) { return w.x1 - w.x0 <= TMX && w.y1 - w.y0 <= TMY; };
+    if (fits(A.work[t])) stage_issue<T, NT, Gm::WX, Gm::WSZ>(A, A.work[t], S0);
+    cp_async_commit();
+    int buf = 0;
+    for (; t < nwork; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        if (tn < nwork && fits(A.work[tn])) stage_issue<T, NT, Gm::WX, Gm::WSZ>(A, A.work[tn], S0 + (buf ^ 1) * wbuf);
+        cp_async_commit();
+        cp_async_wait_one();
+        __syncthreads();
+        const af_work &wk = A.work[t];
+        if (fits(wk)) {
+            const T *Sin = S0 + buf * wbuf;
+            if (wk.flags & 1) {
+                stage_copy_out<T, NT, Gm::WX, Gm::WSZ>(A, wk, Sin);
+                __syncthreads();
+            }
+            tile_compute<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ>(A, W, Sin, ST, wk.patch, wk.level, wk.x0,
+                                                                     wk.x1, wk.y0, wk.y1);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+}
+
+}  // namespace dev
+
+template <typename Kern>
+inline cudaError_t ensure_smem(Kern k, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int EQ, int NT, int TMX, int TMY, int PIPE>
+af_status launch_tiling(const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W, int nwork,
+                        cudaStream_t stream) {
+    using Gm = dev::Geo<TMX, TMY>;
+    constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
+    const size_t win = sizeof(T) * (size_t)ncomp * kPlanes * Gm::WSZ;
+    const size_t tarr = sizeof(T) * (size_t)ncomp * 3 * Gm::TSZ;
+    if constexpr (PIPE) {
+        const size_t smem = 2 * win + tarr;
+        if (smem > 227 * 1024) return AF_ERR_UNIMPLEMENTED;
+        auto kern = dev::step_kernel_pipe<T, EQ, NT, TMX, TMY>;
+        if (ensure_smem(kern, smem) != cudaSuccess) return AF_ERR_CUDA;
+        int dev_id = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev_id) != cudaSuccess) return AF_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess) return AF_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) return AF_ERR_CUDA;
+        const int slots = sms * (per_sm > 0 ? per_sm : 1);
+        kern<<<nwork < slots ? nwork : slots, NT, smem, stream>>>(A, W, nwork);
+    } else {
+        const size_t smem = win + tarr;
+        if (smem > 227 * 1024) return AF_ERR_UNIMPLEMENTED;
+        auto kern = dev::step_kernel<T, EQ, NT, TMX, TMY>;
+        if (ensure_smem(kern, smem) != cudaSuccess) return AF_ERR_CUDA;
+        kern<<<nwork, NT, smem, stream>>>(A, W);
+    }
+    return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ERR_CUDA;
+}
+
+#define AF_TILING_CASE(K)                                                                             \
+    case K:                                                                                           \
+        return launch_tiling<T, EQ, tiling(K).threads, tiling(K).tmx, tiling(K).tmy, tiling(K).persistent>( \
+            A, W, nwork, stream);
+
+template <typename T, int EQ>
+af_status launch_step(int k, const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W, int nwork,
+                      cudaStream_t stream) {
+    static_assert(kNumTilings == 9, "one case per compiled tiling");
+    switch (k) {
+        AF_TILING_CASE(0)
+        AF_TILING_CASE(1)
+        AF_TILING_CASE(2)
+        AF_TILING_CASE(3)
+        AF_TILING_CASE(4)
+        AF_TILING_CASE(5)
+        AF_TILING_CASE(6)
+        AF_TILING_CASE(7)
+        AF_TILING_CASE(8)
+    }
+    return AF_ERR_ARG;
+}
+
+}  // namespace af

@@ -1,0 +1,47 @@
+"""Autotuner of af_patch_step's tile shape and threads per tile.
+
+For a given run (anything with .set_tiling(k) and .step()), every compiled
+tiling that the library accepts is timed with CUDA events on the current
+stream over a few steps after warm-up, and the fastest is kept.  Results
+are memoised per (equation, precision, patch size, patches, neighbour mode)
+for the life of the process.
+"""
+from __future__ import annotations
+
+from . import af
+
+_memo: dict = {}
+
+
+def time_tiling(run, k: int, steps: int = 5, warmup: int = 2) -> float:
+    """Milliseconds per step of `run` with tiling k (inf if not supported)."""
+    import torch
+    try:
+        run.set_tiling(k)
+        for _ in range(warmup):
+            run.step()
+    except af.AFError:
+        return float("inf")
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        run.step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def tune(run, key=None, steps: int = 5, warmup: int = 2, candidates=None):
+    """Pick the fastest tiling for `run`; returns (best index, {index: ms})."""
+    if key is not None and key in _memo:
+        run.set_tiling(_memo[key][0])
+        return _memo[key]
+    cands = range(len(af.step_tilings())) if candidates is None else candidates
+    times = {k: time_tiling(run, k, steps, warmup) for k in cands}
+    best = min(times, key=times.get)
+    run.set_tiling(best)
+    if key is not None:
+        _memo[key] = (best, times)
+    return best, times

@@ -27,7 +27,7 @@ class UniformRun:
     """px x py patches of n x n cells, periodic, advanced by af_patch_step."""
 
     def __init__(self, cfg: af.Config, px: int, py: int, dx: float, dy: float, dt: float, device="cuda",
-                 state=None, flux_reg: bool = False):
+                 state=None, flux_reg: bool = False, tiling=None):
         import torch
         self.cfg, self.px, self.py = cfg, px, py
         self.dx, self.dy, self.dt = dx, dy, dt
@@ -38,15 +38,23 @@ class UniformRun:
         if state is not None:
             self.a.copy_(torch.as_tensor(np.asarray(state).reshape(self.npatch, self.words)).to(dtype))
         self.b = self.a.clone()
-        w = af.build_step_work(cfg, np.arange(self.npatch), nbr=periodic_neighbours(px, py))
-        self.nwork = len(w) // 64
-        self.work = torch.from_numpy(w).to(device)
+        self.nbr = periodic_neighbours(px, py)
+        self.device = device
+        self.set_tiling(tiling)
         self.freg = (torch.zeros((self.npatch, 4, cfg.ncomp, cfg.n), dtype=torch.float64, device=device)
                      if flux_reg else None)
 
+    def set_tiling(self, tiling=None):
+        """Rebuild the work list for a compiled tiling (None: the default)."""
+        import torch
+        self.tiling = af.default_tiling(self.cfg) if tiling is None else int(tiling)
+        w = af.build_step_work(self.cfg, np.arange(self.npatch), nbr=self.nbr, tiling=self.tiling)
+        self.nwork = len(w) // 64
+        self.work = torch.from_numpy(w).to(self.device)
+
     def step(self, stream=None):
         af.patch_step(self.cfg, self.work, self.nwork, self.a, self.b, self.dt, self.dx, self.dy,
-                      self.freg, stream)
+                      self.freg, stream, tiling=self.tiling)
         self.a, self.b = self.b, self.a
 
     @property

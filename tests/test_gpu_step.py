@@ -207,3 +207,47 @@ def test_lukacova_gpu_error_equals_oracle(af):
     for k in range(3):
         eg, eo = grid.l1_error(got, k, ex[k]), grid.l1_error(ref, k, ex[k])
         assert abs(eg - eo) < 1e-8 * eo, (k, eg, eo)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("eq,n", [(1, 32), (1, 16), (0, 32), (0, 8)])
+def test_every_tiling_matches_oracle(af, prec, eq, n):
+    """Every compiled tile shape (the autotuner's search space) gives the
+    oracle's step, for patches that advance their ghost layer (own ghosts)
+    and for interior-only patches with neighbour halos (periodic grid)."""
+    from paper_2205_07572_gb300.uniform import UniformRun
+    nc = 1 if eq == 0 else 3
+    tdt = torch.float64 if prec == 0 else torch.float32
+    a, b, c = 0.9, -0.4, 1.0
+    # own ghosts
+    lay = S.Layout(n, nc)
+    st = S.random_state(lay, 2, seed=60 + n).astype(np.float32 if prec else np.float64).astype(np.float64)
+    dx, dy = 1.0 / n, 1.3 / n
+    dt = _dt(eq, 0.45, dx, dy, a, b, c)
+    cf = O.cfg(eq, n, dx, dy, dt, a, b, c)
+    ref = np.stack([O.step_patch(cf, st[p]) for p in range(2)])
+    # periodic grid
+    grid = S.UniformGrid(S.Layout(n, nc), 2, 2)
+    own = S.random_owned(grid, seed=61 + n)
+    if prec:
+        own = own.astype(np.float32).astype(np.float64)
+    pst = S.pack_owned(grid, own)
+    pdt = _dt(eq, 0.45, grid.dx, grid.dy, a, b, c)
+    pref = S.unpack_owned(grid, O.run_uniform(O.cfg(eq, n, grid.dx, grid.dy, pdt, a, b, c), 2, 2, 2, pst))
+    cfg = af.config(eq, prec, n, a, b, c)
+    for k in range(len(af.step_tilings())):
+        work = af.build_step_work(cfg, np.arange(2), tiling=k)
+        din = torch.from_numpy(st.reshape(2, -1)).to(tdt).cuda()
+        dout = din.clone()
+        af.patch_step(cfg, torch.from_numpy(work).cuda(), len(work) // 64, din, dout, dt, dx, dy, tiling=k)
+        torch.cuda.synchronize()
+        got = dout.double().cpu().numpy().reshape(ref.shape)
+        assert _normwise(got, ref, nc) < TOL[prec], ("own ghosts", k)
+        run = UniformRun(cfg, 2, 2, grid.dx, grid.dy, pdt, state=np.nan_to_num(pst), tiling=k)
+        run.step()
+        run.step()
+        torch.cuda.synchronize()
+        g = S.unpack_owned(grid, run.state.double().cpu().numpy().reshape(pst.shape))
+        for comp in range(nc):
+            err = np.abs(g[comp] - pref[comp]).max() / np.abs(pref[comp]).max()
+            assert err < TOL[prec] * (10 if prec else 1), ("periodic", k, comp, err)
