@@ -84,8 +84,12 @@ __device__ __forceinline__ void stage_issue(const StepArgs<T> &A, const af_work 
     const int n = A.n, W = n + 2 * kGhost + 1;
     const int64_t pw = (int64_t)A.ncomp * kPlanes * A.plane;
     const int ncp = A.ncomp * kPlanes;
-    for (int pos = threadIdx.x; pos < ww * wh; pos += NT) {
-        const int row = pos / ww, col = pos - row * ww;
+    const int plane = (int)A.plane;
+    // positions enumerated with the compile-time window pitch WX (cheap
+    // division); columns beyond the tile's window width are skipped
+    for (int pos = threadIdx.x; pos < WX * wh; pos += NT) {
+        const int row = pos / WX, col = pos - row * WX;
+        if (col >= ww) continue;
         const int li = x0 - 1 + col, lj = y0 - 1 + row;
         const int sx = li < 0 ? -1 : (li >= n ? 1 : 0);
         const int sy = lj < 0 ? -1 : (lj >= n ? 1 : 0);
@@ -101,10 +105,14 @@ __device__ __forceinline__ void stage_issue(const StepArgs<T> &A, const af_work 
                 sj = lj - sy * n;
             }
         }
-        const T *g = A.in + (int64_t)src * pw + (int64_t)(sj + kGhost) * W + (si + kGhost);
+        const T *g = A.in + (int64_t)src * pw + ((sj + kGhost) * W + (si + kGhost));
         T *sp = Sin + row * WX + col;
 #pragma unroll 4
-        for (int cp = 0; cp < ncp; ++cp) cp_async(sp + cp * WSZ, g + cp * A.plane);
+        for (int cp = 0; cp < ncp; ++cp) {
+            cp_async(sp, g);
+            sp += WSZ;
+            g += plane;
+        }
     }
 }
 
@@ -152,12 +160,11 @@ __device__ __forceinline__ void quad(T pp, T pm, T mp, T mm, T &ss, T &as, T &sa
     sa = (pp - pm) + (mp - mm);
 }
 
+// acc += w . v as one chain of fused multiply-adds
 template <int N, typename T>
-__device__ __forceinline__ T dot(const T *w, const T *v) {
-    T s = w[0] * v[0];
+__device__ __forceinline__ void dot(T &acc, const T *w, const T *v) {
 #pragma unroll
-    for (int k = 1; k < N; ++k) s = fma(w[k], v[k], s);
-    return s;
+    for (int k = 0; k < N; ++k) acc = fma(w[k], v[k], acc);
 }
 
 // Acoustic node evaluation of one node-cell item (window coords qi, rj of
@@ -206,29 +213,29 @@ __device__ __forceinline__ void acoustic_item(const AcousticSymWeights<T> &W, co
         yss[4] = b[24] + b[20]; ysa[3] = b[24] - b[20];
         yss[5] = b[22];
         if (ci == 0) {  // p: A on p; Dx.AS_p -> u; Dy.SA_p -> v
-            tc[0] += dot<9>(W.cA[0], css); nc[0] += dot<9>(W.cA[1], css);
-            tx[0] += dot<6>(W.xA[0], xss); nx[0] += dot<6>(W.xA[1], xss);
-            ty[0] += dot<6>(W.yA[0], yss); ny[0] += dot<6>(W.yA[1], yss);
-            tc[1] += dot<6>(W.cDx[0], cas); nc[1] += dot<6>(W.cDx[1], cas);
-            tx[1] += dot<4>(W.xDx[0], xas); nx[1] += dot<4>(W.xDx[1], xas);
-            ty[1] += dot<3>(W.yDx[0], yas); ny[1] += dot<3>(W.yDx[1], yas);
-            tc[2] += dot<6>(W.cDy[0], csa); nc[2] += dot<6>(W.cDy[1], csa);
-            tx[2] += dot<3>(W.xDy[0], xsa); nx[2] += dot<3>(W.xDy[1], xsa);
-            ty[2] += dot<4>(W.yDy[0], ysa); ny[2] += dot<4>(W.yDy[1], ysa);
+            dot<9>(tc[0], W.cA[0], css); dot<9>(nc[0], W.cA[1], css);
+            dot<6>(tx[0], W.xA[0], xss); dot<6>(nx[0], W.xA[1], xss);
+            dot<6>(ty[0], W.yA[0], yss); dot<6>(ny[0], W.yA[1], yss);
+            dot<6>(tc[1], W.cDx[0], cas); dot<6>(nc[1], W.cDx[1], cas);
+            dot<4>(tx[1], W.xDx[0], xas); dot<4>(nx[1], W.xDx[1], xas);
+            dot<3>(ty[1], W.yDx[0], yas); dot<3>(ny[1], W.yDx[1], yas);
+            dot<6>(tc[2], W.cDy[0], csa); dot<6>(nc[2], W.cDy[1], csa);
+            dot<3>(tx[2], W.xDy[0], xsa); dot<3>(nx[2], W.xDy[1], xsa);
+            dot<4>(ty[2], W.yDy[0], ysa); dot<4>(ny[2], W.yDy[1], ysa);
         } else if (ci == 1) {  // u: A on u; Dx.AS_u -> p
-            tc[1] += dot<9>(W.cA[0], css); nc[1] += dot<9>(W.cA[1], css);
-            tx[1] += dot<6>(W.xA[0], xss); nx[1] += dot<6>(W.xA[1], xss);
-            ty[1] += dot<6>(W.yA[0], yss); ny[1] += dot<6>(W.yA[1], yss);
-            tc[0] += dot<6>(W.cDx[0], cas); nc[0] += dot<6>(W.cDx[1], cas);
-            tx[0] += dot<4>(W.xDx[0], xas); nx[0] += dot<4>(W.xDx[1], xas);
-            ty[0] += dot<3>(W.yDx[0], yas); ny[0] += dot<3>(W.yDx[1], yas);
+            dot<9>(tc[1], W.cA[0], css); dot<9>(nc[1], W.cA[1], css);
+            dot<6>(tx[1], W.xA[0], xss); dot<6>(nx[1], W.xA[1], xss);
+            dot<6>(ty[1], W.yA[0], yss); dot<6>(ny[1], W.yA[1], yss);
+            dot<6>(tc[0], W.cDx[0], cas); dot<6>(nc[0], W.cDx[1], cas);
+            dot<4>(tx[0], W.xDx[0], xas); dot<4>(nx[0], W.xDx[1], xas);
+            dot<3>(ty[0], W.yDx[0], yas); dot<3>(ny[0], W.yDx[1], yas);
         } else {  // v: A on v; Dy.SA_v -> p
-            tc[2] += dot<9>(W.cA[0], css); nc[2] += dot<9>(W.cA[1], css);
-            tx[2] += dot<6>(W.xA[0], xss); nx[2] += dot<6>(W.xA[1], xss);
-            ty[2] += dot<6>(W.yA[0], yss); ny[2] += dot<6>(W.yA[1], yss);
-            tc[0] += dot<6>(W.cDy[0], csa); nc[0] += dot<6>(W.cDy[1], csa);
-            tx[0] += dot<3>(W.xDy[0], xsa); nx[0] += dot<3>(W.xDy[1], xsa);
-            ty[0] += dot<4>(W.yDy[0], ysa); ny[0] += dot<4>(W.yDy[1], ysa);
+            dot<9>(tc[2], W.cA[0], css); dot<9>(nc[2], W.cA[1], css);
+            dot<6>(tx[2], W.xA[0], xss); dot<6>(nx[2], W.xA[1], xss);
+            dot<6>(ty[2], W.yA[0], yss); dot<6>(ny[2], W.yA[1], yss);
+            dot<6>(tc[0], W.cDy[0], csa); dot<6>(nc[0], W.cDy[1], csa);
+            dot<3>(tx[0], W.xDy[0], xsa); dot<3>(nx[0], W.xDy[1], xsa);
+            dot<4>(ty[0], W.yDy[0], ysa); dot<4>(ny[0], W.yDy[1], ysa);
         }
     }
 }
@@ -267,15 +274,17 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
     const int sxhi = (x1 == n + 1) ? x1 : x1 - 1;
     const int syhi = (y1 == n + 1) ? y1 : y1 - 1;
 
-    // ---- point values
-    const int nitems = (tw + 1) * (th + 1);
+    const int plane = (int)A.plane;
+    // ---- point values (node-cells enumerated with the compile-time pitch TX)
+    const int nitems = TX * (th + 1);
     for (int it = threadIdx.x; it < nitems; it += NT) {
-        const int jj = it / (tw + 1), ii = it - jj * (tw + 1);
+        const int jj = it / TX, ii = it - jj * TX;
+        if (ii > tw) continue;
         const int i = x0 + ii, j = y0 + jj;
         const int qi = ii + 1, rj = jj + 1;
         const bool hx = j < y1, hy = i < x1;            // edge midpoints that exist
         const bool st_x = i <= sxhi, st_y = j <= syhi;  // stored lines
-        const int64_t lo = (int64_t)(j + kGhost) * W_ + (i + kGhost);
+        T *const ob = outp + ((j + kGhost) * W_ + (i + kGhost));  // this node-cell in plane 0 of comp 0
         const int so = jj * TX + ii;
         if constexpr (EQ == AF_ACOUSTICS) {
             T tc[3], nc[3], tx[3], nx[3], ty[3], ny[3];
@@ -285,10 +294,10 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
                 ST[(o * 3 + 0) * TSZ + so] = tc[o];
                 ST[(o * 3 + 1) * TSZ + so] = tx[o];
                 ST[(o * 3 + 2) * TSZ + so] = ty[o];
-                T *po = outp + (int64_t)o * kPlanes * A.plane + lo;
-                if (st_x && st_y) po[kCorner * A.plane] = nc[o];
-                if (st_x && hx) po[kXmid * A.plane] = nx[o];
-                if (hy && st_y) po[kYmid * A.plane] = ny[o];
+                T *po = ob + o * kPlanes * plane;
+                if (st_x && st_y) po[kCorner * plane] = nc[o];
+                if (st_x && hx) po[kXmid * plane] = nx[o];
+                if (hy && st_y) po[kYmid * plane] = ny[o];
             }
         } else {
             const int own = rj * WX + qi;
@@ -296,19 +305,19 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
                 const T qh = adv_eval<T, WX, WSZ>(W.w[0][0], Sin, qi + W.off[0][0][0], rj + W.off[0][0][1]);
                 const T q1 = adv_eval<T, WX, WSZ>(W.w[0][1], Sin, qi + W.off[0][1][0], rj + W.off[0][1][1]);
                 ST[0 * TSZ + so] = Sin[kCorner * WSZ + own] + T(4) * qh + q1;
-                if (st_x && st_y) outp[kCorner * A.plane + lo] = q1;
+                if (st_x && st_y) ob[kCorner * plane] = q1;
             }
             if (hx) {
                 const T qh = adv_eval<T, WX, WSZ>(W.w[1][0], Sin, qi + W.off[1][0][0], rj + W.off[1][0][1]);
                 const T q1 = adv_eval<T, WX, WSZ>(W.w[1][1], Sin, qi + W.off[1][1][0], rj + W.off[1][1][1]);
                 ST[1 * TSZ + so] = Sin[kXmid * WSZ + own] + T(4) * qh + q1;
-                if (st_x) outp[kXmid * A.plane + lo] = q1;
+                if (st_x) ob[kXmid * plane] = q1;
             }
             if (hy) {
                 const T qh = adv_eval<T, WX, WSZ>(W.w[2][0], Sin, qi + W.off[2][0][0], rj + W.off[2][0][1]);
                 const T q1 = adv_eval<T, WX, WSZ>(W.w[2][1], Sin, qi + W.off[2][1][0], rj + W.off[2][1][1]);
                 ST[2 * TSZ + so] = Sin[kYmid * WSZ + own] + T(4) * qh + q1;
-                if (st_y) outp[kYmid * A.plane + lo] = q1;
+                if (st_y) ob[kYmid * plane] = q1;
             }
         }
     }
@@ -316,8 +325,10 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
 
     // ---- fluxes and update
     const double dtl = ldexp(A.dt0, -level);
-    for (int it = threadIdx.x; it < tw * th; it += NT) {
-        const int jj = it / tw, ii = it - jj * tw;
+    constexpr int CX = TX - 1;  // cells per tile row at most
+    for (int it = threadIdx.x; it < CX * th; it += NT) {
+        const int jj = it / CX, ii = it - jj * CX;
+        if (ii >= tw) continue;
         const int i = x0 + ii, j = y0 + jj;
         const int s00 = jj * TX + ii;
         T Fl[3], Fr[3], Gb[3], Gt[3];
@@ -341,12 +352,12 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
             fl[0] = A.fx * Fl[0]; fr[0] = A.fx * Fr[0];
             gb[0] = A.fy * Gb[0]; gt[0] = A.fy * Gt[0];
         }
-        const int64_t lo = (int64_t)(j + kGhost) * W_ + (i + kGhost);
+        T *const ob = outp + ((j + kGhost) * W_ + (i + kGhost));
         const int sa = (jj + 1) * WX + (ii + 1);
 #pragma unroll
         for (int c = 0; c < ncomp; ++c) {
             const T q = Sin[(c * kPlanes + kAvg) * WSZ + sa];
-            outp[(int64_t)(c * kPlanes + kAvg) * A.plane + lo] = q - A.dtdx * (fr[c] - fl[c]) - A.dtdy * (gt[c] - gb[c]);
+            ob[c * kPlanes * plane] = q - A.dtdx * (fr[c] - fl[c]) - A.dtdy * (gt[c] - gb[c]);
         }
         if (A.freg != nullptr) {
             double *fr_p = A.freg + (int64_t)patch * 4 * ncomp * n;
