@@ -260,7 +260,7 @@ __device__ __forceinline__ T adv_eval(const T *w, const T *Sin, int cq, int cr) 
 // Point values (Eq. advection-update / Eq. ERFormula), then fluxes (Eq.
 // Simpson-2d) and the update (Eq. 2dfv) of one staged tile.  Sin: window
 // (pitch WX, plane size WSZ); ST: T arrays (pitch TX, size TSZ).
-template <typename T, int EQ, int NT, int WX, int WSZ, int TX, int TSZ>
+template <typename T, int EQ, int NT, int WX, int WSZ, int TX, int TSZ, int TMX = TX - 1>
 __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W,
                                              const T *Sin, T *ST, int patch, int level, int x0, int x1, int y0,
                                              int y1) {
@@ -275,11 +275,30 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
     const int syhi = (y1 == n + 1) ? y1 : y1 - 1;
 
     const int plane = (int)A.plane;
-    // ---- point values (node-cells enumerated with the compile-time pitch TX)
-    const int nitems = TX * (th + 1);
+    // ---- point values.  Node-cells (ii, jj), ii in [0, tw], jj in [0, th].
+    // A full-width tile (tw == TMX) enumerates columns [0, TMX) with the
+    // compile-time pitch TMX -- one warp covers consecutive words of one row,
+    // so the block loads are free of bank conflicts -- and its last node
+    // column (ii = TMX) as a short list after them; narrower tiles use the
+    // pitch tw + 1.
+    const bool full = (tw == TMX);
+    const int pitch = full ? TMX : tw + 1;
+    const int nmain = pitch * (th + 1);
+    const int nitems = nmain + (full ? th + 1 : 0);
     for (int it = threadIdx.x; it < nitems; it += NT) {
-        const int jj = it / TX, ii = it - jj * TX;
-        if (ii > tw) continue;
+        int jj, ii;
+        if (it < nmain) {
+            if (full) {
+                jj = it / TMX;
+                ii = it - jj * TMX;
+            } else {
+                jj = it / pitch;
+                ii = it - jj * pitch;
+            }
+        } else {
+            jj = it - nmain;
+            ii = TMX;
+        }
         const int i = x0 + ii, j = y0 + jj;
         const int qi = ii + 1, rj = jj + 1;
         const bool hx = j < y1, hy = i < x1;            // edge midpoints that exist
@@ -325,10 +344,15 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
 
     // ---- fluxes and update
     const double dtl = ldexp(A.dt0, -level);
-    constexpr int CX = TX - 1;  // cells per tile row at most
-    for (int it = threadIdx.x; it < CX * th; it += NT) {
-        const int jj = it / CX, ii = it - jj * CX;
-        if (ii >= tw) continue;
+    for (int it = threadIdx.x; it < tw * th; it += NT) {
+        int jj, ii;
+        if (full) {
+            jj = it / TMX;
+            ii = it - jj * TMX;
+        } else {
+            jj = it / tw;
+            ii = it - jj * tw;
+        }
         const int i = x0 + ii, j = y0 + jj;
         const int s00 = jj * TX + ii;
         T Fl[3], Fr[3], Gb[3], Gt[3];
