@@ -236,6 +236,168 @@ def literal_config2(prec: str, steps: int):
             "steps_T0.5": 640, "run_ms_T0.5": 640 * ms}
 
 
+# ------------------------------------------------------- adaptive workloads
+# Quadtree AMR with 16 x 16-cell patches and subcycling.  One AMR bench step
+# is one coarse step: every level advanced to the next time of the coarsest
+# level (level l takes 2^(l - lmin) steps), with the conservative fix and the
+# ghost exchange at every synchronised time.
+AMR_CASES = {
+    "advection_levels2-6": dict(
+        eq=0, B=1, lmin=2, lmax=6, lo=(0.0, 0.0), hi=(1.0, 1.0), a=1.0, b=1.0,
+        desc=("advection a=(1,1), periodic unit square, wave packet exp(-r^2/0.01) cos(60 pi x), levels 2-6, "
+              "16x16-cell patches, gradient tagging (refine >= 4, coarsen < 1), CFL 0.4"),
+        tag=(0, 1, 4.0, 1.0)),
+    "acoustics_levels3-7": dict(
+        eq=1, B=3, lmin=3, lmax=7, lo=(-1.5, -1.5), hi=(1.5, 1.5), a=0.0, b=0.0,
+        desc=("acoustics c=1, periodic [-1.5,1.5]^2 (3x3 brick), ring wave exp(-(r-0.25)^2/0.001) cos(80 pi r), "
+              "u=v=0, levels 3-7, 16x16-cell patches, gradient tagging on p (refine >= 4, coarsen < 1), CFL 0.4"),
+        tag=(0, 1, 4.0, 1.0)),
+}
+AMR_N = 16
+
+
+def _amr_funcs(eq):
+    import synth as S
+    if eq == 0:
+        return [S.wave_packet]
+    zero = lambda x, y: 0.0 * x
+    return [S.ring_wave, zero, zero]
+
+
+def amr_initial(case: str, device="cuda"):
+    """Initial forest by the method's own adaptation: start from the uniform
+    coarsest level, then tag (af_tag) and regrid (af_forest_regrid) the exact
+    initial data once per level."""
+    import synth as S
+    from paper_2205_07572_gb300 import af
+    from paper_2205_07572_gb300.amr import AMRRun, Forest, regrid_leaves
+    c = AMR_CASES[case]
+    B, lmin, lmax = c["B"], c["lmin"], c["lmax"]
+    side = B << lmin
+    leaves = [(lmin, x, y) for y in range(side) for x in range(side)]
+    cfg = af.config(c["eq"], af.F64, AMR_N, c["a"], c["b"], 1.0)
+    funcs = _amr_funcs(c["eq"])
+    for _ in range(lmax - lmin):
+        lv = np.array(leaves, dtype=np.int64).reshape(-1, 3)
+        st = S.forest_state_fast(AMR_N, cfg.ncomp, B, lv[:, 0], lv[:, 1], lv[:, 2], funcs, c["lo"], c["hi"])
+        run = AMRRun(cfg, B, lmax, leaves, st, c["lo"], c["hi"], 1e-9, device=device)
+        comp, kind, rt, ct = c["tag"]
+        tags, _ = run.tags(comp, kind, rt, ct)
+        new = regrid_leaves(run.forest, np.maximum(tags, 0), lmin)
+        if new == run.forest.leaves:
+            break
+        leaves = new
+    lv = np.array(leaves, dtype=np.int64).reshape(-1, 3)
+    st = S.forest_state_fast(AMR_N, cfg.ncomp, B, lv[:, 0], lv[:, 1], lv[:, 2], funcs, c["lo"], c["hi"])
+    return leaves, st
+
+
+def amr_time(case: str, leaves, st, prec: str, mode: str, graphs: bool, coarse_steps: int, warmup: int,
+             regrid: bool = False):
+    """Cell updates per second of coarse steps of an adaptive run (the
+    forest fixed, or regridded before every coarse step)."""
+    import torch
+    from paper_2205_07572_gb300 import af
+    from paper_2205_07572_gb300.amr import AMRRun
+    c = AMR_CASES[case]
+    cfg = af.config(c["eq"], af.F32 if prec == "f32" else af.F64, AMR_N, c["a"], c["b"], 1.0)
+    dx0 = (c["hi"][0] - c["lo"][0]) / (c["B"] * AMR_N)
+    speed = max(abs(c["a"]), abs(c["b"])) if c["eq"] == 0 else 1.0
+    dt0 = CFL * dx0 / speed
+    run = AMRRun(cfg, c["B"], c["lmax"], leaves, st, c["lo"], c["hi"], dt0, mode=mode, graphs=graphs)
+    comp, kind, rt, ct = c["tag"]
+
+    def one():
+        if regrid:
+            tags, _ = run.tags(comp, kind, rt, ct)
+            run.regrid(tags, c["lmin"])
+        cu = run.cell_updates_per_coarse_step()
+        nl = run.launches_per_coarse_step()
+        run.coarse_step()
+        return cu, nl
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cu = nl = 0
+    ev0.record(stream)
+    for _ in range(coarse_steps):
+        a, b = one()
+        cu += a
+        nl += b
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    levels = np.bincount(run.forest.level, minlength=c["lmax"] + 1).tolist()
+    return {"value": cu / (ms * 1e-3), "unit": "cell updates/s", "ms_per_coarse_step": ms / coarse_steps,
+            "coarse_steps": coarse_steps, "cell_updates": cu, "gpu_launches": nl, "leaves": run.forest.nleaf,
+            "leaves_per_level": levels}, run
+
+
+def amr_l1_exact(case: str, run, t: float):
+    """Sum over leaves and interior cells of |Q - Q_exact| dx_l dy_l (advection:
+    the initial data translated by (a, b) t)."""
+    import synth as S
+    c = AMR_CASES[case]
+    f = S.translated(S.wave_packet, c["a"], c["b"], t, c["lo"], c["hi"])
+    F = run.forest
+    ex = S.forest_state_fast(AMR_N, 1, c["B"], F.level, F.ix, F.iy, [f], c["lo"], c["hi"], nq=4)
+    lay = S.Layout(AMR_N, 1)
+    got = run.current().double().cpu().numpy().reshape(F.nleaf, 1, 4, -1)
+    g = lay.lattice(got)[:, 0, 0, S.G:S.G + AMR_N, S.G:S.G + AMR_N]
+    e = lay.lattice(ex)[:, 0, 0, S.G:S.G + AMR_N, S.G:S.G + AMR_N]
+    area = ((c["hi"][0] - c["lo"][0]) / ((c["B"] << F.level) * AMR_N)) ** 2
+    return float((np.abs(g - e).sum(axis=(1, 2)) * area).sum())
+
+
+def amr_l1_between(case: str, ra, rb):
+    """L1 distance of the first component's averages of two runs on the same forest."""
+    import synth as S
+    c = AMR_CASES[case]
+    F = ra.forest
+    assert F.leaves == rb.forest.leaves
+    lay = S.Layout(AMR_N, ra.cfg.ncomp)
+    ga = lay.lattice(ra.current().double().cpu().numpy().reshape(F.nleaf, ra.cfg.ncomp, 4, -1))
+    gb = lay.lattice(rb.current().double().cpu().numpy().reshape(F.nleaf, rb.cfg.ncomp, 4, -1))
+    sl = (slice(None), 0, 0, slice(S.G, S.G + AMR_N), slice(S.G, S.G + AMR_N))
+    area = ((c["hi"][0] - c["lo"][0]) / ((c["B"] << F.level) * AMR_N)) ** 2
+    return float((np.abs(ga[sl] - gb[sl]).sum(axis=(1, 2)) * area).sum())
+
+
+def amr_bench(case: str, coarse_steps: int, warmup: int, per_patch: bool = True):
+    """Batched FP32 (graph-replayed) vs batched FP64 vs per-level and
+    per-patch FP64 launches on one adaptive workload."""
+    t0 = time.perf_counter()
+    leaves, st = amr_initial(case)
+    out = {"workload": AMR_CASES[case]["desc"], "setup_s": None}
+    out["setup_s"] = round(time.perf_counter() - t0, 1)
+    c = AMR_CASES[case]
+    dx0 = (c["hi"][0] - c["lo"][0]) / (c["B"] * AMR_N)
+    speed = max(abs(c["a"]), abs(c["b"])) if c["eq"] == 0 else 1.0
+    t_end = (coarse_steps + max(4, warmup)) * CFL * dx0 / speed
+    # graphs: the first coarse step from each level parity runs eagerly, the
+    # second is captured, so four warm-up steps leave only replays timed
+    r32, run32 = amr_time(case, leaves, st, "f32", "batched", True, coarse_steps, max(4, warmup))
+    r64, run64 = amr_time(case, leaves, st, "f64", "batched", False, coarse_steps, max(4, warmup))
+    out["batched_graphs_f32"] = r32
+    out["batched_f64"] = r64
+    out["l1_f32_vs_f64"] = amr_l1_between(case, run32, run64)
+    if c["eq"] == 0:
+        out["l1_vs_exact"] = {"f32": amr_l1_exact(case, run32, t_end), "f64": amr_l1_exact(case, run64, t_end),
+                              "t": t_end}
+    del run32, run64
+    out["per_level_f64"], _ = amr_time(case, leaves, st, "f64", "per_level", False, max(1, coarse_steps // 2), 1)
+    if per_patch:
+        out["per_patch_f64"], _ = amr_time(case, leaves, st, "f64", "per_patch", False, 1, 1)
+    out["regrid_every_coarse_step_f32"], _ = amr_time(case, leaves, st, "f32", "batched", False,
+                                                      max(2, coarse_steps // 2), 1, regrid=True)
+    base = out.get("per_patch_f64", out["per_level_f64"])["value"]
+    out["speedup_batched_f32_vs_per_patch_f64"] = r32["value"] / base
+    return out
+
+
 # ----------------------------------------------------------- CPU oracle arm
 def oracle_sample(steps: int, budget_s: float = 15.0):
     """Time the FP64 oracle on a bounded sample of the workload: an 8 x 8 block
@@ -274,7 +436,9 @@ def main():
     ap.add_argument("--prec", default="both", choices=["both", "f32", "f64"],
                     help="which stencil precision(s) to time (profiling runs use one)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the end-to-end, literal-size and CPU-baseline measurements")
+                    help="skip the end-to-end, literal-size, adaptive-mesh and CPU-baseline measurements")
+    ap.add_argument("--amr-only", action="store_true",
+                    help="time only the adaptive-mesh workloads (one JSON object per workload)")
     args = ap.parse_args()
     warm = max(3, args.warmup)
 
@@ -319,6 +483,11 @@ def main():
     if dist is not None:
         dist.barrier()
 
+    if args.amr_only:
+        if rank == 0:
+            for case in AMR_CASES:
+                print(json.dumps({"amr": case, **amr_bench(case, 8, 4)}), flush=True)
+        return
     if args.prec != "both":
         r = run_ours(args.prec, args.steps, warm, rank, world, dist)
         if rank == 0:
@@ -339,6 +508,7 @@ def main():
         lit32 = literal_config2("f32", 50) if extras else None
         lit64 = literal_config2("f64", 10) if extras else None
         cpu = None if (args.no_cpu_baseline or not extras) else oracle_sample(20)
+        amr = {case: amr_bench(case, 8, 4) for case in AMR_CASES} if extras else None
         v64 = world * cells / (r64["ms"] * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": "cell updates/s", "n_gpus": world,
@@ -357,6 +527,7 @@ def main():
                          "peak_source": f"{src} HBM copy bandwidth",
                          "algorithmic_bytes_per_launch": cells * BYTES_PER_CELL["f32"]},
             "literal_512x512": {"f32": lit32, "f64": lit64, "note": "L2-resident (34 MB FP64 state)"},
+            "amr": amr,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

@@ -166,6 +166,35 @@ af_status af_patch_step_tiled(const af_config *cfg, int32_t tiling, int32_t nwor
                               const void *d_in, void *d_out, double dt0, double dx0, double dy0,
                               double *d_flux_reg, void *stream);
 
+/* Two state arrays with a per-level choice of the current one, so that a
+ * subcycled adaptive run (Section 3.2: level l takes 2^(l-m) steps for every
+ * step of the coarsest level m) can advance any set of levels without
+ * copying: a step reads the current array of each level and writes the
+ * other, and the caller then flips the parity bits of the levels it
+ * advanced.  Both arrays have the same shape (npatch_total patches, layout
+ * above) and are owned by the caller; parity bit l set means the current
+ * values of the level-l leaves are in buf[1], clear means buf[0].  Entries
+ * of the other array are stale and are never read.  The paper keeps one
+ * array per patch; this is the GPU's way to batch all levels that advance at
+ * one time into one launch. */
+typedef struct {
+    void *buf[2];
+    uint32_t parity;
+    uint32_t pad_;
+} af_state_pair;
+
+/* af_patch_step_tiled on a state pair: every work item of level l reads
+ * buf[(parity >> l) & 1] and writes the other array.  Work items of several
+ * levels may share one call: they use dt0 / 2^l and dx0 / 2^l, so the CFL
+ * numbers and stencil weights are those of level 0, and the flux registers
+ * receive dt_l * F.  Levels advanced together must not read one another
+ * (true of the levels that advance at one time of a subcycled schedule:
+ * their patches read only same-level neighbours and their own ghost rings).
+ * AF_ERR_ARG if buf[0] == buf[1]; other errors as af_patch_step. */
+af_status af_patch_step_pair(const af_config *cfg, int32_t tiling, int32_t nwork, const af_work *d_work,
+                             const af_state_pair *state, double dt0, double dx0, double dy0,
+                             double *d_flux_reg, void *stream);
+
 
 /* ======================================================================
  * Adaptive mesh refinement (Section 3): a forest of quadtrees over a B x B
@@ -200,6 +229,31 @@ int64_t af_forest_map_offset(int32_t B, int32_t level);
 af_status af_forest_build_map(int32_t nleaf, int32_t B, int32_t lmax, const int32_t *h_level,
                               const int32_t *h_ix, const int32_t *h_iy, int32_t *h_map);
 
+/* Same-level neighbours of every leaf (host): h_nbr[8p + d] is the leaf
+ * index of the level-l region next to leaf p in direction d (W, E, S, N,
+ * SW, SE, NW, NE; periodic), or -1 if that region is not a leaf.  h_map is
+ * the output of af_forest_build_map.  This is the h_nbr argument of
+ * af_build_step_work. */
+af_status af_forest_neighbours(int32_t nleaf, int32_t B, int32_t lmax, const int32_t *h_level,
+                               const int32_t *h_ix, const int32_t *h_iy, const int32_t *h_map, int32_t *h_nbr);
+
+/* Regrid (Section 3: refinement and coarsening "at each time step" from a
+ * per-patch criterion; the forest stays 2:1 balanced), on the host, from the
+ * per-leaf tags of af_tag:
+ *   1. every leaf tagged 1 below lmax is split into its four children;
+ *   2. families of four leaves tagged -1 above lmin, taken in ascending
+ *      order of their parent's (level, ix, iy), are merged into the parent
+ *      unless a face or corner neighbour region of the parent then holds a
+ *      leaf two or more levels finer;
+ *   3. leaves with such a neighbour are split until none is left.
+ * The new leaves are written sorted by (level, iy, ix), at most `capacity`
+ * of them; *out_n receives their count (AF_ERR_ARG if capacity is too
+ * small).  Host memory O(B^2 4^lmax) bytes.  AF_ERR_ARG on out-of-range or
+ * duplicate leaves. */
+af_status af_forest_regrid(int32_t nleaf, int32_t B, int32_t lmin, int32_t lmax, const int32_t *h_level,
+                           const int32_t *h_ix, const int32_t *h_iy, const int8_t *h_tags, int32_t capacity,
+                           int32_t *out_level, int32_t *out_ix, int32_t *out_iy, int32_t *out_n);
+
 /* Flags of af_fill_ghosts. */
 #define AF_FILL_SAME_LEVEL_ONLY 1 /* copy from same-level leaves only */
 #define AF_FILL_ALL_PATCHES 2     /* also fill leaves whose 8 neighbours are all same-level */
@@ -221,6 +275,44 @@ af_status af_forest_build_map(int32_t nleaf, int32_t B, int32_t lmax, const int3
  * reads their halo from the neighbours directly). */
 af_status af_fill_ghosts(const af_config *cfg, const af_forest *forest, uint32_t dst_levels,
                          uint32_t src_levels, int32_t flags, void *d_state, void *stream);
+
+/* Ghost plan: af_fill_ghosts with the owner of every exchanged entry found
+ * once per forest.  The exchange itself (Section 3.1 cases 1-3, at the
+ * synchronised times of Section 3.2) is then two passes over a flat list:
+ * pass A replaces entries whose owner is same-level (copy) or finer (mean of
+ * the four finer averages, or the coinciding finer vertex); pass B replaces
+ * entries whose owner is coarser by the owner's reconstruction (point value,
+ * or Simpson's rule over the finer cell).  Pass B reads the coarse cell's
+ * boundary point values from the coarse leaf's own lattice, which pass A has
+ * refreshed, so the result equals af_fill_ghosts bit for bit.
+ *
+ * The plan is a device array of AF_GHOST_ENTRY_BYTES-byte entries owned by
+ * the caller, valid for one forest (rebuild after every regrid):
+ *   1. af_ghost_plan_count writes the number of pass-A and pass-B entries to
+ *      d_counts[0], d_counts[1] (device, int64, 8-byte aligned);
+ *   2. the caller allocates (n_a + n_b) entries (16-byte aligned) and calls
+ *      af_ghost_plan_build with the counts and 3 int64 of device scratch
+ *      (16-byte aligned; zeroed by the call); after the build, scratch[2]
+ *      is non-zero if the counts were too small (the plan is then unusable).
+ * flags: AF_FILL_ALL_PATCHES includes leaves whose eight neighbours are all
+ * same-level (as af_fill_ghosts).  Entries are in no particular order; each
+ * destination entry appears once, so the order does not change the result.
+ *
+ * af_fill_ghosts_planned runs the exchange for the leaves of `levels` from
+ * owners of `levels` (af_fill_ghosts with dst_levels = src_levels = levels).
+ * `levels` must be upward closed -- with its coarsest level it holds every
+ * finer level up to the forest's lmax (true of every synchronised set of a
+ * subcycled schedule, and of all levels) -- else AF_ERR_ARG, because pass B
+ * relies on pass A having refreshed the coarse leaves.  flags may add
+ * AF_FILL_SAME_LEVEL_ONLY (pass A's copies from same-level owners only). */
+#define AF_GHOST_ENTRY_BYTES 16
+af_status af_ghost_plan_count(const af_config *cfg, const af_forest *forest, int32_t flags, int64_t *d_counts,
+                              void *stream);
+af_status af_ghost_plan_build(const af_config *cfg, const af_forest *forest, int32_t flags, void *d_plan,
+                              int64_t n_a, int64_t n_b, int64_t *d_scratch, void *stream);
+af_status af_fill_ghosts_planned(const af_config *cfg, const af_forest *forest, uint32_t levels, int32_t flags,
+                                 const void *d_plan, int64_t n_a, int64_t n_b, const af_state_pair *state,
+                                 void *stream);
 
 /* Regrid transfer (Section 3.1 cases 1 and 2): every leaf of new_forest that
  * is a leaf of old_forest is copied whole from d_old; every other new leaf
@@ -263,6 +355,23 @@ int64_t af_mass_scratch_bytes(int32_t nleaf, int32_t ncomp);
  * to d_mass[ncomp]. */
 af_status af_mass(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0, double dy0,
                   void *d_scratch, double *d_mass, void *stream);
+
+/* The operations above on a state pair (see af_state_pair): every leaf is
+ * read from and written to the current array of its level; the other array
+ * is not touched.  af_transfer_pair reads the old forest's state from a pair
+ * and writes the new forest's state to the single array d_new.  Results are
+ * those of the single-array calls applied to the current arrays. */
+af_status af_fill_ghosts_pair(const af_config *cfg, const af_forest *forest, uint32_t dst_levels,
+                              uint32_t src_levels, int32_t flags, const af_state_pair *state, void *stream);
+af_status af_transfer_pair(const af_config *cfg, const af_forest *old_forest, const af_state_pair *old_state,
+                           const af_forest *new_forest, void *d_new, void *stream);
+af_status af_reflux_pair(const af_config *cfg, const af_forest *forest, uint32_t sync_levels, double dx0,
+                         double dy0, double *d_flux_reg, const af_state_pair *state, void *stream);
+af_status af_tag_pair(const af_config *cfg, const af_forest *forest, const af_state_pair *state, int32_t comp,
+                      int32_t kind, double dx0, double dy0, double refine_thr, double coarsen_thr, int8_t *d_tags,
+                      double *d_indicator, void *stream);
+af_status af_mass_pair(const af_config *cfg, const af_forest *forest, const af_state_pair *state, double dx0,
+                       double dy0, void *d_scratch, double *d_mass, void *stream);
 
 
 /* af_mass without any caller-provided scratch.  The paper has no

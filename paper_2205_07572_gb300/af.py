@@ -261,3 +261,102 @@ def mass_noalloc(cfg: Config, forest: ForestC, state, dx0: float, dy0: float, ou
     """af_mass with the library's fixed scratch array (no allocation)."""
     _check(lib().af_mass_noalloc(C.byref(cfg), C.byref(forest), ptr(state), dx0, dy0, ptr(out),
                                  stream_handle(stream)), "af_mass_noalloc")
+
+
+# --------------------------------------------------------------- state pairs
+class StatePair(C.Structure):
+    """af_state_pair: level l's current values are in buf[(parity >> l) & 1]."""
+    _fields_ = [("buf", C.c_void_p * 2), ("parity", C.c_uint32), ("pad_", C.c_uint32)]
+
+
+_SP = C.POINTER(StatePair)
+_EXTRA += [
+    ("af_patch_step_pair", C.c_int, [C.POINTER(Config), C.c_int32, C.c_int32, _VP, _SP, C.c_double, C.c_double,
+                                     C.c_double, _VP, _VP]),
+    ("af_fill_ghosts_pair", C.c_int, [C.POINTER(Config), _FP, C.c_uint32, C.c_uint32, C.c_int32, _SP, _VP]),
+    ("af_transfer_pair", C.c_int, [C.POINTER(Config), _FP, _SP, _FP, _VP, _VP]),
+    ("af_reflux_pair", C.c_int, [C.POINTER(Config), _FP, C.c_uint32, C.c_double, C.c_double, _VP, _SP, _VP]),
+    ("af_tag_pair", C.c_int, [C.POINTER(Config), _FP, _SP, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                              C.c_double, C.c_double, _VP, _VP, _VP]),
+    ("af_mass_pair", C.c_int, [C.POINTER(Config), _FP, _SP, C.c_double, C.c_double, _VP, _VP, _VP]),
+]
+if _lib is not None:
+    _register_more(_lib)
+
+
+def state_pair(buf0, buf1, parity: int) -> StatePair:
+    p = StatePair()
+    p.buf[0] = ptr(buf0)
+    p.buf[1] = ptr(buf1)
+    p.parity = int(parity) & 0xFFFFFFFF
+    return p
+
+
+def patch_step_pair(cfg: Config, tiling: int, work, nwork: int, pair: StatePair, dt0: float, dx0: float, dy0: float,
+                    flux_reg=None, stream=None) -> None:
+    _check(lib().af_patch_step_pair(C.byref(cfg), int(tiling), int(nwork), ptr(work), C.byref(pair), float(dt0),
+                                    float(dx0), float(dy0), ptr(flux_reg), stream_handle(stream)),
+           "af_patch_step_pair")
+
+
+def fill_ghosts_pair(cfg: Config, forest: ForestC, dst_levels: int, src_levels: int, flags: int, pair: StatePair,
+                     stream=None):
+    _check(lib().af_fill_ghosts_pair(C.byref(cfg), C.byref(forest), dst_levels, src_levels, flags, C.byref(pair),
+                                     stream_handle(stream)), "af_fill_ghosts_pair")
+
+
+def transfer_pair(cfg: Config, old: ForestC, old_pair: StatePair, new: ForestC, d_new, stream=None):
+    _check(lib().af_transfer_pair(C.byref(cfg), C.byref(old), C.byref(old_pair), C.byref(new), ptr(d_new),
+                                  stream_handle(stream)), "af_transfer_pair")
+
+
+def reflux_pair(cfg: Config, forest: ForestC, sync_levels: int, dx0: float, dy0: float, flux_reg, pair: StatePair,
+                stream=None):
+    _check(lib().af_reflux_pair(C.byref(cfg), C.byref(forest), sync_levels, dx0, dy0, ptr(flux_reg),
+                                C.byref(pair), stream_handle(stream)), "af_reflux_pair")
+
+
+def tag_pair(cfg: Config, forest: ForestC, pair: StatePair, comp: int, kind: int, dx0: float, dy0: float,
+             refine_thr: float, coarsen_thr: float, tags, indicator=None, stream=None):
+    _check(lib().af_tag_pair(C.byref(cfg), C.byref(forest), C.byref(pair), comp, kind, dx0, dy0, refine_thr,
+                             coarsen_thr, ptr(tags), ptr(indicator), stream_handle(stream)), "af_tag_pair")
+
+
+def mass_pair(cfg: Config, forest: ForestC, pair: StatePair, dx0: float, dy0: float, scratch, out, stream=None):
+    _check(lib().af_mass_pair(C.byref(cfg), C.byref(forest), C.byref(pair), dx0, dy0, ptr(scratch), ptr(out),
+                              stream_handle(stream)), "af_mass_pair")
+
+
+# --------------------------------------------------------------- ghost plan
+GHOST_ENTRY_BYTES = 16
+_EXTRA += [
+    ("af_ghost_plan_count", C.c_int, [C.POINTER(Config), _FP, C.c_int32, _VP, _VP]),
+    ("af_ghost_plan_build", C.c_int, [C.POINTER(Config), _FP, C.c_int32, _VP, C.c_int64, C.c_int64, _VP, _VP]),
+    ("af_fill_ghosts_planned", C.c_int, [C.POINTER(Config), _FP, C.c_uint32, C.c_int32, _VP, C.c_int64, C.c_int64,
+                                         _SP, _VP]),
+]
+if _lib is not None:
+    _register_more(_lib)
+
+
+def ghost_plan(cfg: Config, forest: ForestC, flags: int = 0, device="cuda", stream=None):
+    """Build the ghost plan of a forest: returns (plan tensor, n_a, n_b).
+    Reads the two counts back to the host (one stream synchronisation)."""
+    import torch
+    counts = torch.zeros(2, dtype=torch.int64, device=device)
+    _check(lib().af_ghost_plan_count(C.byref(cfg), C.byref(forest), flags, ptr(counts), stream_handle(stream)),
+           "af_ghost_plan_count")
+    n_a, n_b = (int(v) for v in counts.cpu().tolist())
+    plan = torch.empty(max(1, (n_a + n_b) * GHOST_ENTRY_BYTES // 8), dtype=torch.int64, device=device)
+    scratch = torch.empty(4, dtype=torch.int64, device=device)
+    _check(lib().af_ghost_plan_build(C.byref(cfg), C.byref(forest), flags, ptr(plan), n_a, n_b, ptr(scratch),
+                                     stream_handle(stream)), "af_ghost_plan_build")
+    if int(scratch[2].item()) != 0:
+        raise AFError(1, "af_ghost_plan_build: counts too small")
+    return plan, n_a, n_b
+
+
+def fill_ghosts_planned(cfg: Config, forest: ForestC, levels: int, flags: int, plan, n_a: int, n_b: int,
+                        pair: StatePair, stream=None):
+    _check(lib().af_fill_ghosts_planned(C.byref(cfg), C.byref(forest), levels, flags, ptr(plan), n_a, n_b,
+                                        C.byref(pair), stream_handle(stream)), "af_fill_ghosts_planned")

@@ -1,20 +1,40 @@
 """Host driver of the adaptive Active Flux method (Section 3) on the GPU.
 
 The forest (a periodic B x B brick of quadtrees), its device description, the
-per-level work lists of af_patch_step and the subcycling schedule live here;
-every arithmetic step -- the patch step, the ghost exchange, the conservative
-fix, the regrid transfer, the indicator and the mass totals -- is a call into
-libaf.so.
+work lists of af_patch_step and the subcycling schedule live here; every
+arithmetic step -- the patch step, the ghost exchange, the conservative fix,
+the regrid transfer, the indicator and the mass totals -- is a call into
+libaf.so, and so are the forest's neighbour tables and the regrid decision
+(af_forest_neighbours, af_forest_regrid).
 
 Leaves are kept sorted by level (then row-major), so the patches of one level
-are a contiguous slice of the state array.  A level is advanced from the
-state buffer into a scratch buffer and the slice is copied back.
+are a contiguous slice of the state array, and the levels that advance at one
+time of the subcycled schedule (all levels finer than some level) are a
+contiguous suffix of it.
+
+Three ways to run the same schedule:
+  "batched"   the state is a pair of arrays with a current one per level
+              (af_state_pair): at each time of the schedule ONE af_patch_step
+              launch advances every level due, with no copies; a whole
+              coarse step can be captured once in a CUDA graph and replayed;
+  "per_level" one launch per level into a scratch array, then the level's
+              slice is copied back;
+  "per_patch" one launch per patch (the patch-by-patch loop of a CPU solver),
+              then the level's slice is copied back.
 """
 from __future__ import annotations
+
+import ctypes as C
 
 import numpy as np
 
 from . import af
+
+_IP = C.POINTER(C.c_int32)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_IP)
 
 
 def _leaf_order(leaves):
@@ -22,20 +42,24 @@ def _leaf_order(leaves):
 
 
 class Forest:
-    """Leaves (level, ix, iy) of a periodic forest with their region maps."""
+    """Leaves (level, ix, iy) of a periodic forest with their region maps and
+    same-level neighbour table."""
 
     def __init__(self, B: int, lmax: int, leaves, device="cuda"):
         import torch
         self.B, self.lmax = B, lmax
-        self.leaves = _leaf_order(leaves)
-        self.level = np.array([l for l, _, _ in self.leaves], dtype=np.int32)
-        self.ix = np.array([x for _, x, _ in self.leaves], dtype=np.int32)
-        self.iy = np.array([y for _, _, y in self.leaves], dtype=np.int32)
+        self.leaves = _leaf_order([tuple(int(v) for v in t) for t in leaves])
+        n = len(self.leaves)
+        arr = np.array(self.leaves, dtype=np.int32).reshape(n, 3)
+        self.level = np.ascontiguousarray(arr[:, 0])
+        self.ix = np.ascontiguousarray(arr[:, 1])
+        self.iy = np.ascontiguousarray(arr[:, 2])
         self.map = af.forest_build_map(B, lmax, self.level, self.ix, self.iy)
         self.offsets = [af.forest_map_offset(B, l) for l in range(lmax + 2)]
+        self.nbr = forest_neighbours(B, lmax, self.level, self.ix, self.iy, self.map)
         t = lambda a: torch.from_numpy(a).to(device)
         self.d_level, self.d_ix, self.d_iy, self.d_map = t(self.level), t(self.ix), t(self.iy), t(self.map)
-        self.c = af.forest_struct(len(self.leaves), B, lmax, self.d_level, self.d_ix, self.d_iy, self.d_map)
+        self.c = af.forest_struct(n, B, lmax, self.d_level, self.d_ix, self.d_iy, self.d_map)
 
     @property
     def nleaf(self) -> int:
@@ -51,106 +75,87 @@ class Forest:
         return int(self.map[self.offsets[l] + (y % side) * side + (x % side)])
 
     def level_slice(self, l: int) -> slice:
-        idx = np.nonzero(self.level == l)[0]
-        return slice(int(idx[0]), int(idx[-1]) + 1) if len(idx) else slice(0, 0)
+        lo = int(np.searchsorted(self.level, l, side="left"))
+        hi = int(np.searchsorted(self.level, l, side="right"))
+        return slice(lo, hi)
 
     def neighbours(self, idx) -> np.ndarray:
         """Same-level neighbour of each leaf in idx (W, E, S, N, SW, SE, NW, NE) or -1."""
-        dirs = [(-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (1, -1), (-1, 1), (1, 1)]
-        out = np.full((len(idx), 8), -1, dtype=np.int32)
-        for r, p in enumerate(idx):
-            l, x, y = self.leaves[p]
-            for d, (sx, sy) in enumerate(dirs):
-                out[r, d] = self.region(l, x + sx, y + sy)
-        return out
+        return self.nbr[np.asarray(list(idx), dtype=np.int64)]
+
+    def cells(self, n: int) -> np.ndarray:
+        """Interior cells per level (index = level)."""
+        return np.bincount(self.level, minlength=self.lmax + 1) * n * n
+
+
+_EXTRA = [
+    ("af_forest_neighbours", C.c_int, [C.c_int32, C.c_int32, C.c_int32, _IP, _IP, _IP, _IP, _IP]),
+    ("af_forest_regrid", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _IP, _IP, _IP, C.c_void_p,
+                                   C.c_int32, _IP, _IP, _IP, _IP]),
+]
+
+
+def _lib():
+    L = af.lib()
+    for name, res, args in _EXTRA:
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    return L
+
+
+def forest_neighbours(B, lmax, level, ix, iy, fmap) -> np.ndarray:
+    n = len(level)
+    out = np.full((n, 8), -1, dtype=np.int32)
+    af._check(_lib().af_forest_neighbours(n, B, lmax, _ip(level), _ip(ix), _ip(iy), _ip(fmap), _ip(out)),
+              "af_forest_neighbours")
+    return out
 
 
 def regrid_leaves(forest: Forest, tags, lmin: int):
-    """New leaf set: leaves tagged 1 below lmax are split, complete families of
-    four leaves tagged -1 above lmin are merged unless the merged leaf would
-    sit next to a leaf two levels finer, then leaves are split until no leaf
-    has a face or corner neighbour region holding a leaf two or more levels
-    finer (2:1 balance).  The same rules as the oracle's, implemented on
-    per-level occupancy grids."""
-    B, lmax = forest.B, forest.lmax
-    # occ[l]: level-l region grid, 1 where a leaf of level exactly l sits
-    occ = [np.zeros((B << l, B << l), dtype=np.int8) for l in range(lmax + 1)]
-    tag = {}
-    for (l, x, y), t in zip(forest.leaves, tags):
-        occ[l][y, x] = 1
-        tag[(l, x, y)] = int(t)
+    """New leaf set from per-leaf tags (af_forest_regrid): leaves tagged 1
+    below lmax are split, complete families of four leaves tagged -1 above
+    lmin are merged unless the merged leaf would sit next to a leaf two levels
+    finer, then leaves are split until the forest is 2:1 balanced."""
+    tags = np.ascontiguousarray(tags, dtype=np.int8)
+    L = _lib()
+    cnt = C.c_int32(0)
+    args = (forest.nleaf, forest.B, lmin, forest.lmax, _ip(forest.level), _ip(forest.ix), _ip(forest.iy),
+            tags.ctypes.data)
+    st = L.af_forest_regrid(*args, 0, None, None, None, C.byref(cnt))
+    if st != 0 and cnt.value == 0:
+        af._check(st, "af_forest_regrid")
+    m = cnt.value
+    lv, x, y = (np.empty(max(m, 1), dtype=np.int32) for _ in range(3))
+    af._check(L.af_forest_regrid(*args, m, _ip(lv), _ip(x), _ip(y), C.byref(cnt)), "af_forest_regrid")
+    return list(zip(lv[:m].tolist(), x[:m].tolist(), y[:m].tolist()))
 
-    def split(l, x, y):
-        occ[l][y, x] = 0
-        occ[l + 1][2 * y:2 * y + 2, 2 * x:2 * x + 2] = 1
 
-    for (l, x, y), t in list(tag.items()):
-        if t == 1 and l < lmax:
-            split(l, x, y)
-
-    def finer_than(l, x, y, d):
-        """True if the level-l region (x, y) contains a leaf of level >= l + d."""
-        for m in range(l + d, lmax + 1):
-            s = 1 << (m - l)
-            if occ[m][y * s:(y + 1) * s, x * s:(x + 1) * s].any():
-                return True
-        return False
-
-    def unbalanced(l, x, y):
-        side = B << l
-        for sy in (-1, 0, 1):
-            for sx in (-1, 0, 1):
-                if (sx or sy) and finer_than(l, (x + sx) % side, (y + sy) % side, 2):
-                    return True
-        return False
-
-    families = {}
-    for (l, x, y), t in tag.items():
-        if t == -1 and l > lmin:
-            families.setdefault((l - 1, x // 2, y // 2), []).append((l, x, y))
-    for (pl, px, py) in sorted(families):
-        kids = families[(pl, px, py)]
-        if len(kids) != 4 or not all(occ[l][y, x] for (l, x, y) in kids):
-            continue
-        for (l, x, y) in kids:
-            occ[l][y, x] = 0
-        occ[pl][py, px] = 1
-        if unbalanced(pl, px, py):
-            occ[pl][py, px] = 0
-            for (l, x, y) in kids:
-                occ[l][y, x] = 1
-    changed = True
-    while changed:
-        changed = False
-        for l in range(lmax + 1):
-            ys, xs = np.nonzero(occ[l])
-            for y, x in sorted(zip(ys.tolist(), xs.tolist())):
-                if occ[l][y, x] and unbalanced(l, x, y):
-                    split(l, x, y)
-                    changed = True
-    out = []
-    for l in range(lmax + 1):
-        ys, xs = np.nonzero(occ[l])
-        out += [(l, int(x), int(y)) for y, x in zip(ys, xs)]
-    return _leaf_order(out)
+MODES = ("batched", "per_level", "per_patch")
 
 
 class AMRRun:
     """Adaptive run: subcycled steps (Section 3.2), reflux, ghost exchange, regrid."""
 
-    def __init__(self, cfg: af.Config, B: int, lmax: int, leaves, state, lo, hi, dt0: float, device="cuda"):
+    def __init__(self, cfg: af.Config, B: int, lmax: int, leaves, state, lo, hi, dt0: float, device="cuda",
+                 mode: str = "batched", graphs: bool = False, tiling=None, planned_fill: bool = True):
         import torch
+        if mode not in MODES:
+            raise ValueError(f"mode must be one of {MODES}")
         self.cfg, self.B, self.lmax, self.device = cfg, B, lmax, device
+        self.mode, self.use_graphs = mode, bool(graphs) and mode == "batched"
+        self.planned_fill = planned_fill
         self.lo, self.hi = lo, hi
         self.dx0 = (hi[0] - lo[0]) / (B * cfg.n)
         self.dy0 = (hi[1] - lo[1]) / (B * cfg.n)
         self.dt0 = dt0
+        self.tiling = af.default_tiling(cfg) if tiling is None else int(tiling)
         self.dtype = torch.float64 if cfg.prec == af.F64 else torch.float32
         self.words = af.patch_words(cfg.n, cfg.ncomp)
         self.forest = Forest(B, lmax, leaves, device)
-        order = {leaf: k for k, leaf in enumerate(leaves)}
+        order = {leaf: k for k, leaf in enumerate(_leaf_order(leaves))}
         st = np.asarray(state).reshape(len(leaves), -1)[[order[leaf] for leaf in self.forest.leaves]]
         self.a = torch.as_tensor(st).to(device=device, dtype=self.dtype).contiguous()
+        self.parity = 0
         self._setup()
         self.fill(self.all_levels, self.all_levels)
 
@@ -159,55 +164,161 @@ class AMRRun:
     def all_levels(self) -> int:
         return (1 << (self.lmax + 1)) - 1
 
+    @property
+    def pair(self) -> af.StatePair:
+        return af.state_pair(self.a, self.b, self.parity)
+
     def _setup(self):
         import torch
         F = self.forest
-        self.b = self.a.clone()
+        self.b = torch.zeros_like(self.a) if self.mode == "batched" else self.a.clone()
         self.freg = torch.zeros((F.nleaf, 4, self.cfg.ncomp, self.cfg.n), dtype=torch.float64, device=self.device)
-        self.work = {}
-        for l in F.levels:
-            sl = F.level_slice(l)
-            idx = np.arange(sl.start, sl.stop)
-            w = af.build_step_work(self.cfg, idx, np.full(len(idx), l, np.int32), F.neighbours(idx))
-            self.work[l] = (torch.from_numpy(w).to(self.device), len(w) // 64, sl)
+        w = af.build_step_work(self.cfg, np.arange(F.nleaf), F.level, F.nbr, tiling=self.tiling)
+        nwork = len(w) // 64
+        wl = w.view(np.int32).reshape(nwork, 16)[:, 1] if nwork else np.zeros(0, np.int32)
+        self.work_all = torch.from_numpy(w).to(self.device)
+        # first work item of every level (items are in leaf order)
+        self.work_start = [int(np.searchsorted(wl, l, side="left")) for l in range(self.lmax + 2)]
+        self.nwork = nwork
+        if self.mode == "per_patch":
+            wp = w.view(np.int32).reshape(nwork, 16)[:, 0] if nwork else np.zeros(0, np.int32)
+            self.patch_work = [(int(s), int(e)) for s, e in
+                               zip(np.searchsorted(wp, np.arange(F.nleaf), side="left"),
+                                   np.searchsorted(wp, np.arange(F.nleaf), side="right"))]
         self.scratch = torch.zeros(max(1, af.mass_scratch_bytes(F.nleaf, self.cfg.ncomp) // 8),
                                    dtype=torch.float64, device=self.device)
         self.mass_out = torch.zeros(self.cfg.ncomp, dtype=torch.float64, device=self.device)
+        self.graphs = {}
+        if self.planned_fill and str(self.device) != "cpu":
+            self.plan = af.ghost_plan(self.cfg, F.c, 0, self.device)
+        else:
+            self.plan = None
 
-    def fill(self, dst: int, src: int, flags: int = 0):
-        af.fill_ghosts(self.cfg, self.forest.c, dst, src, flags, self.a)
+    def fill(self, dst: int, src: int, flags: int = 0, stream=None):
+        if self.plan is not None and dst == src and not (flags & af.FILL_ALL_PATCHES):
+            plan, n_a, n_b = self.plan
+            # levels finer than any present are empty: adding them makes the
+            # set upward closed without changing what is exchanged
+            levels = dst | (self.all_levels & ~((1 << dst.bit_length()) - 1))
+            af.fill_ghosts_planned(self.cfg, self.forest.c, levels, flags, plan, n_a, n_b, self.pair, stream)
+        elif self.mode == "batched":
+            af.fill_ghosts_pair(self.cfg, self.forest.c, dst, src, flags, self.pair, stream)
+        else:
+            af.fill_ghosts(self.cfg, self.forest.c, dst, src, flags, self.a, stream)
+
+    def _work_ptr(self, start: int) -> int:
+        return self.work_all.data_ptr() + 64 * start
 
     # -------------------------------------------------------------- steps
-    def advance(self, l: int):
-        """One step of dt_l on every leaf of level l."""
-        work, nwork, sl = self.work[l]
-        af.patch_step(self.cfg, work, nwork, self.a, self.b, self.dt0, self.dx0, self.dy0, self.freg)
+    def advance_from(self, lstar: int, stream=None):
+        """One step of dt_l on every leaf of every level l >= lstar (the
+        levels due at one time of the subcycled schedule)."""
+        s, e = self.work_start[lstar], self.nwork
+        if self.mode == "batched":
+            if e > s:
+                af.patch_step_pair(self.cfg, self.tiling, self._work_ptr(s), e - s, self.pair, self.dt0, self.dx0,
+                                   self.dy0, self.freg, stream)
+            self.parity ^= self.all_levels & ~((1 << lstar) - 1)
+            return
+        for l in range(self.lmax, lstar - 1, -1):
+            self.advance(l, stream)
+
+    def advance(self, l: int, stream=None):
+        """One step of dt_l on every leaf of level l (per_level / per_patch)."""
+        assert self.mode != "batched"
+        s, e = self.work_start[l], self.work_start[l + 1]
+        if e == s:
+            return
+        sl = self.forest.level_slice(l)
+        if self.mode == "per_level":
+            af.patch_step(self.cfg, self._work_ptr(s), e - s, self.a, self.b, self.dt0, self.dx0, self.dy0,
+                          self.freg, stream, tiling=self.tiling)
+        else:
+            for p in range(sl.start, sl.stop):
+                ps, pe = self.patch_work[p]
+                af.patch_step(self.cfg, self._work_ptr(ps), pe - ps, self.a, self.b, self.dt0, self.dx0, self.dy0,
+                              self.freg, stream, tiling=self.tiling)
         self.a[sl].copy_(self.b[sl])
 
-    def coarse_step(self):
-        """Advance all levels by the step of the coarsest level present,
-        finest level first; at every time where two or more levels are
+    def _schedule(self, stream=None):
+        """Finest level first; at every time where two or more levels are
         synchronised: conservative fix, then ghost exchange among them."""
         levels = self.forest.levels
         lmin, lmx = levels[0], levels[-1]
         for s in range(1 << (lmx - lmin)):
-            for l in range(lmx, lmin - 1, -1):
-                if l in self.work and s % (1 << (lmx - l)) == 0:
-                    self.advance(l)
+            due = [l for l in levels if s % (1 << (lmx - l)) == 0]
+            self.advance_from(min(due), stream)
             sync = 0
             for l in range(lmin, lmx + 1):
                 if (s + 1) % (1 << (lmx - l)) == 0:
                     sync |= 1 << l
             if bin(sync).count("1") > 1:
-                af.reflux(self.cfg, self.forest.c, sync, self.dx0, self.dy0, self.freg, self.a)
-                self.fill(sync, sync)
+                if self.mode == "batched":
+                    af.reflux_pair(self.cfg, self.forest.c, sync, self.dx0, self.dy0, self.freg, self.pair, stream)
+                else:
+                    af.reflux(self.cfg, self.forest.c, sync, self.dx0, self.dy0, self.freg, self.a, stream)
+                self.fill(sync, sync, stream=stream)
+
+    def coarse_step(self):
+        """Advance all levels by the step of the coarsest level present."""
+        if not self.use_graphs:
+            self._schedule()
+            return
+        import torch
+        key = self.parity
+        g = self.graphs.get(key)
+        if g is None:
+            # first coarse step from this parity runs eagerly (warm-up: kernel
+            # attributes and weight tables are set up outside the capture);
+            # the next one from the same parity is captured
+            if key not in self.graphs:
+                self.graphs[key] = None
+                self._schedule()
+                return
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            p0 = self.parity
+            with torch.cuda.graph(g, stream=side):
+                self._schedule()
+            torch.cuda.current_stream().wait_stream(side)
+            self.graphs[key] = (g, self.parity)
+            self.parity = p0  # capture did not run anything
+        g, p1 = self.graphs[key]
+        g.replay()
+        self.parity = p1
+
+    def cell_updates_per_coarse_step(self) -> int:
+        levels = self.forest.levels
+        lmin = levels[0]
+        cells = self.forest.cells(self.cfg.n)
+        return int(sum(int(cells[l]) << (l - lmin) for l in levels))
+
+    def launches_per_coarse_step(self) -> int:
+        """Kernels of this library launched by one coarse step."""
+        levels = self.forest.levels
+        lmin, lmx = levels[0], levels[-1]
+        n = 0
+        for s in range(1 << (lmx - lmin)):
+            due = [l for l in levels if s % (1 << (lmx - l)) == 0]
+            if self.mode == "batched":
+                n += 1
+            elif self.mode == "per_level":
+                n += len(due)
+            else:
+                n += sum(self.forest.level_slice(l).stop - self.forest.level_slice(l).start for l in due)
+            sync = sum(1 for l in range(lmin, lmx + 1) if (s + 1) % (1 << (lmx - l)) == 0)
+            if sync > 1:
+                n += 1 + 3
+        return n
 
     # ---------------------------------------------------- tags and regrid
     def tags(self, comp: int, kind: int, refine_thr: float, coarsen_thr: float):
         import torch
         t = torch.zeros(self.forest.nleaf, dtype=torch.int8, device=self.device)
         ind = torch.zeros(self.forest.nleaf, dtype=torch.float64, device=self.device)
-        af.tag(self.cfg, self.forest.c, self.a, comp, kind, self.dx0, self.dy0, refine_thr, coarsen_thr, t, ind)
+        af.tag_pair(self.cfg, self.forest.c, self.pair, comp, kind, self.dx0, self.dy0, refine_thr, coarsen_thr,
+                    t, ind)
         return t.cpu().numpy(), ind.cpu().numpy()
 
     def regrid(self, tags, lmin: int) -> bool:
@@ -215,21 +326,35 @@ class AMRRun:
         new = regrid_leaves(self.forest, tags, lmin)
         if new == self.forest.leaves:
             return False
-        old_forest, old_state = self.forest, self.a
+        old_forest, old_pair = self.forest, self.pair
+        old_bufs = (self.a, self.b)
         self.forest = Forest(self.B, self.lmax, new, self.device)
         self.a = torch.empty((self.forest.nleaf, self.words), dtype=self.dtype, device=self.device)
-        af.transfer(self.cfg, old_forest.c, old_state, self.forest.c, self.a)
-        self._keep = old_forest  # device arrays of the old forest stay alive until the copy ran
+        af.transfer_pair(self.cfg, old_forest.c, old_pair, self.forest.c, self.a)
+        self._keep = (old_forest, old_bufs)  # the old arrays stay alive until the copy ran
+        self.parity = 0
         self._setup()
         self.fill(self.all_levels, self.all_levels)
         return True
 
     def mass(self):
-        af.mass(self.cfg, self.forest.c, self.a, self.dx0, self.dy0, self.scratch, self.mass_out)
+        af.mass_pair(self.cfg, self.forest.c, self.pair, self.dx0, self.dy0, self.scratch, self.mass_out)
         return self.mass_out.cpu().numpy()
+
+    def current(self):
+        """Device tensor with every leaf's current values (a copy when levels
+        are split between the two arrays)."""
+        if self.parity == 0:
+            return self.a
+        out = self.a.clone()
+        for l in self.forest.levels:
+            if (self.parity >> l) & 1:
+                sl = self.forest.level_slice(l)
+                out[sl] = self.b[sl]
+        return out
 
     def state_in_order(self, leaves):
         """Host copy of the state with leaves in the given order."""
         idx = {leaf: k for k, leaf in enumerate(self.forest.leaves)}
-        host = self.a.double().cpu().numpy()
+        host = self.current().double().cpu().numpy()
         return host[[idx[leaf] for leaf in leaves]]

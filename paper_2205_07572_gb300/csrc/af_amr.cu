@@ -97,14 +97,24 @@ __device__ __forceinline__ long long reld(const DevForest &F, long long x, long 
     return d > F.D / 2 ? d - F.D : d;
 }
 
+// State of all leaves: one array, or two with a per-level choice of the
+// current one (af_state_pair).
 template <typename T>
 struct StateView {
-    T *base;
-    int64_t plane;  // plane stride
-    int ncomp, W;   // components, lattice width
+    T *base0, *base1;
+    const int32_t *level;  // leaf levels (read only when parity != 0)
+    uint32_t parity;       // bit l: level l is current in base1
+    int64_t plane;         // plane stride
+    int ncomp, W;          // components, lattice width
+    __device__ __forceinline__ T *patch(int q) const {
+        T *b = (parity != 0u && ((parity >> __ldg(level + q)) & 1u)) ? base1 : base0;
+        return b + (int64_t)q * ncomp * kPlanes * plane;
+    }
+    __device__ __forceinline__ T *patch_at_level(int q, int l) const {
+        return (((parity >> l) & 1u) ? base1 : base0) + (int64_t)q * ncomp * kPlanes * plane;
+    }
     __device__ __forceinline__ T *at(int q, int c, int k, int i, int j) const {
-        return base + ((int64_t)q * ncomp * kPlanes + c * kPlanes + k) * plane + (int64_t)(j + kGhost) * W +
-               (i + kGhost);
+        return patch(q) + (int64_t)(c * kPlanes + k) * plane + (int64_t)(j + kGhost) * W + (i + kGhost);
     }
 };
 
@@ -123,9 +133,20 @@ __device__ __forceinline__ void lattice_of(const DevForest &F, int q, int k, lon
     j = j < lo ? lo : (j > hi ? hi : j);
 }
 
-// Value of the reconstruction (Eq. poly) of leaf q, component c, at (x, y):
-// tensor Lagrange interpolant on {-1,0,1}^2 whose centre value follows from
-// the average, (9/4) Q - (1/16) sum(corners) - (1/4) sum(edge midpoints).
+// The reconstruction (Eq. poly) of one cell at (xi, eta) in [-1, 1]^2 from
+// its corners c.., edge midpoints x./y. and average: the tensor Lagrange
+// interpolant on {-1,0,1}^2 whose centre value follows from the average,
+// (9/4) Q - (1/16) sum(corners) - (1/4) sum(edge midpoints).
+__device__ __forceinline__ double recon_eval(double c00, double c10, double c01, double c11, double xl, double xr,
+                                             double yb, double yt, double avg, double xi, double eta) {
+    const double cen = 2.25 * avg - 0.0625 * (c00 + c10 + c01 + c11) - 0.25 * (xl + xr + yb + yt);
+    const double lx0 = 0.5 * xi * (xi - 1.0), lx1 = 1.0 - xi * xi, lx2 = 0.5 * xi * (xi + 1.0);
+    const double ly0 = 0.5 * eta * (eta - 1.0), ly1 = 1.0 - eta * eta, ly2 = 0.5 * eta * (eta + 1.0);
+    return ly0 * (lx0 * c00 + lx1 * yb + lx2 * c10) + ly1 * (lx0 * xl + lx1 * cen + lx2 * xr) +
+           ly2 * (lx0 * c01 + lx1 * yt + lx2 * c11);
+}
+
+// Value of the reconstruction of leaf q, component c, at (x, y).
 template <typename T>
 __device__ double recon_at(const DevForest &F, const StateView<T> &S, int q, int c, long long x, long long y) {
     const long long hw = hwid(F, __ldg(F.level + q));
@@ -157,11 +178,7 @@ __device__ double recon_at(const DevForest &F, const StateView<T> &S, int q, int
     const double xl = node(kXmid, i, j), xr = node(kXmid, i + 1, j);
     const double yb = node(kYmid, i, j), yt = node(kYmid, i, j + 1);
     const double avg = *S.at(q, c, kAvg, i, j);
-    const double cen = 2.25 * avg - 0.0625 * (c00 + c10 + c01 + c11) - 0.25 * (xl + xr + yb + yt);
-    const double lx0 = 0.5 * xi * (xi - 1.0), lx1 = 1.0 - xi * xi, lx2 = 0.5 * xi * (xi + 1.0);
-    const double ly0 = 0.5 * eta * (eta - 1.0), ly1 = 1.0 - eta * eta, ly2 = 0.5 * eta * (eta + 1.0);
-    return ly0 * (lx0 * c00 + lx1 * yb + lx2 * c10) + ly1 * (lx0 * xl + lx1 * cen + lx2 * xr) +
-           ly2 * (lx0 * c01 + lx1 * yt + lx2 * c11);
+    return recon_eval(c00, c10, c01, c11, xl, xr, yb, yt, avg, xi, eta);
 }
 
 // Value for an entry of plane k of a destination at level lp from owner q
@@ -252,19 +269,189 @@ __global__ void fill_kernel(DevForest F, StateView<T> S, uint32_t dst, uint32_t 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Ghost plan: the owner of every ghost entry resolved once per forest, so an
+// exchange is two flat passes over a list instead of per-entry searches.
+// Pass A (kinds copy / mean of four finer averages) writes only entries the
+// destination does not own and reads only owned ones, so its entries are
+// independent; among them are the boundary-line point values of every leaf
+// with a coarser-or-finer neighbour.  Pass B (coarse -> fine) then reads the
+// coarse leaf's whole cell -- boundary-line nodes included -- from that
+// leaf's own lattice, which pass A has just made current.
+struct GhostEntry {
+    int32_t dst, src;
+    uint16_t dst_off;  // plane * plane_stride + lattice index (component 0)
+    uint8_t kind, levels;  // levels: dst level | src level << 4
+    uint32_t aux;      // kinds 0, 1: source offset; kinds 2, 3: u | v << 16 (quarter cells of the source)
+};
+static_assert(sizeof(GhostEntry) == AF_GHOST_ENTRY_BYTES, "ghost plan entry layout");
+enum : uint8_t { kGCopy = 0, kGMean4 = 1, kGPoint = 2, kGSimpson = 3 };
+
+// Classify ghost entry (k, i, j) of leaf p; false if it is not exchanged.
+__device__ bool ghost_entry(const DevForest &F, int64_t plane, int p, int lp, int k, int i, int j, GhostEntry &g) {
+    const int n = F.n, W = n + 2 * kGhost + 1;
+    if (i > 0 && i < n && j > 0 && j < n) return false;
+    if (i == n + kGhost && (k == kAvg || k == kYmid)) return false;
+    if (j == n + kGhost && (k == kAvg || k == kXmid)) return false;
+    long long x, y;
+    entry_xy(F, p, k, i, j, x, y);
+    const int q = entry_owner(F, k, x, y);
+    if (q < 0 || q == p) return false;
+    const int lq = __ldg(F.level + q);
+    g.dst = p;
+    g.src = q;
+    g.dst_off = (uint16_t)(k * plane + (int64_t)(j + kGhost) * W + (i + kGhost));
+    g.levels = (uint8_t)(lp | (lq << 4));
+    int si, sj;
+    if (lq == lp) {
+        lattice_of(F, q, k, x, y, si, sj);
+        g.kind = kGCopy;
+        g.aux = (uint32_t)(k * plane + (int64_t)(sj + kGhost) * W + (si + kGhost));
+    } else if (lq > lp) {
+        if (k == kAvg) {
+            const long long h = hwid(F, lq) / 2;  // the four finer cells: (si, sj) .. (si + 1, sj + 1)
+            lattice_of(F, q, kAvg, x - h, y - h, si, sj);
+            g.kind = kGMean4;
+            g.aux = (uint32_t)(kAvg * plane + (int64_t)(sj + kGhost) * W + (si + kGhost));
+        } else {
+            lattice_of(F, q, kCorner, x, y, si, sj);
+            g.kind = kGCopy;
+            g.aux = (uint32_t)(kCorner * plane + (int64_t)(sj + kGhost) * W + (si + kGhost));
+        }
+    } else {
+        const long long quarter = hwid(F, lq) / 4;
+        long long u = reld(F, x, leaf_x0(F, q)) / quarter, v = reld(F, y, leaf_y0(F, q)) / quarter;
+        u = u < 0 ? 0 : (u > 4 * n ? 4 * n : u);
+        v = v < 0 ? 0 : (v > 4 * n ? 4 * n : v);
+        g.kind = k == kAvg ? kGSimpson : kGPoint;
+        g.aux = (uint32_t)u | ((uint32_t)v << 16);
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool plan_leaf(const DevForest &F, int p, int flags) {
+    return (flags & AF_FILL_ALL_PATCHES) || has_other_level_neighbour(F, p);
+}
+
+// counts[0]: pass-A entries, counts[1]: pass-B entries.
+__global__ void plan_count_kernel(DevForest F, int64_t plane, int flags, unsigned long long *counts) {
+    const int p = blockIdx.x;
+    __shared__ int s_use;
+    __shared__ unsigned int s_cnt[2];
+    if (threadIdx.x == 0) {
+        s_use = plan_leaf(F, p, flags);
+        s_cnt[0] = s_cnt[1] = 0;
+    }
+    __syncthreads();
+    if (!s_use) return;
+    const int lp = __ldg(F.level + p), W = F.n + 2 * kGhost + 1;
+    for (int e = threadIdx.x; e < kPlanes * W * W; e += blockDim.x) {
+        const int k = e / (W * W), r = e - k * W * W;
+        GhostEntry g;
+        if (ghost_entry(F, plane, p, lp, k, r % W - kGhost, r / W - kGhost, g)) atomicAdd(&s_cnt[g.kind >= kGPoint], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 && s_cnt[threadIdx.x]) atomicAdd(counts + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+// Pass-A entries fill [0, na), pass-B entries [na, na + nb); cursor[2] starts at 0.
+__global__ void plan_build_kernel(DevForest F, int64_t plane, int flags, GhostEntry *plan, long long na, long long nb,
+                                  unsigned long long *cursor, int *overflow) {
+    const int p = blockIdx.x;
+    __shared__ int s_use;
+    if (threadIdx.x == 0) s_use = plan_leaf(F, p, flags);
+    __syncthreads();
+    if (!s_use) return;
+    const int lp = __ldg(F.level + p), W = F.n + 2 * kGhost + 1;
+    for (int e = threadIdx.x; e < kPlanes * W * W; e += blockDim.x) {
+        const int k = e / (W * W), r = e - k * W * W;
+        GhostEntry g;
+        if (!ghost_entry(F, plane, p, lp, k, r % W - kGhost, r / W - kGhost, g)) continue;
+        const int b = g.kind >= kGPoint;
+        const unsigned long long slot = atomicAdd(cursor + b, 1ull);
+        if ((long long)slot >= (b ? nb : na)) {
+            atomicExch(overflow, 1);
+            continue;
+        }
+        plan[(b ? na : 0) + (long long)slot] = g;
+    }
+}
+
+template <typename T>
+__global__ void plan_exec_a(StateView<T> S, const GhostEntry *__restrict__ plan, long long na, uint32_t levels,
+                            int same_only) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < na; t += (long long)gridDim.x * blockDim.x) {
+        const GhostEntry g = plan[t];
+        const int ld = g.levels & 15, ls = g.levels >> 4;
+        if (!((levels >> ld) & 1u) || !((levels >> ls) & 1u) || (same_only && ld != ls)) continue;
+        const T *src = S.patch_at_level(g.src, ls) + g.aux;
+        T *dst = S.patch_at_level(g.dst, ld) + g.dst_off;
+        const int64_t cs = (int64_t)kPlanes * S.plane;
+        for (int c = 0; c < S.ncomp; ++c) {
+            if (g.kind == kGCopy) {
+                dst[c * cs] = src[c * cs];
+            } else {
+                const T *a = src + c * cs;
+                const double sum = (double)a[0] + (double)a[1] + (double)a[S.W] + (double)a[S.W + 1];
+                dst[c * cs] = (T)(0.25 * sum);
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void plan_exec_b(StateView<T> S, int n, const GhostEntry *__restrict__ plan, long long nb, uint32_t levels) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nb; t += (long long)gridDim.x * blockDim.x) {
+        const GhostEntry g = plan[t];
+        const int ld = g.levels & 15, ls = g.levels >> 4;
+        if (!((levels >> ld) & 1u) || !((levels >> ls) & 1u)) continue;
+        const T *q = S.patch_at_level(g.src, ls);
+        T *dst = S.patch_at_level(g.dst, ld) + g.dst_off;
+        const int u0 = (int)(g.aux & 0xffffu), v0 = (int)(g.aux >> 16);
+        const int64_t cs = (int64_t)kPlanes * S.plane;
+        const int W = S.W;
+        // value at quarter-cell position (u, v) of the source leaf, with the
+        // cell chosen as the direct exchange chooses it
+        auto at = [&](const T *b, int u, int v) -> double {
+            int ci = u / 4, cj = v / 4;
+            ci = ci > n - 1 ? n - 1 : ci;
+            cj = cj > n - 1 ? n - 1 : cj;
+            const double xi = 0.5 * (double)(u - 4 * ci) - 1.0, eta = 0.5 * (double)(v - 4 * cj) - 1.0;
+            const T *cr = b + kCorner * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
+            const T *xm = b + kXmid * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
+            const T *ym = b + kYmid * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
+            const T *av = b + kAvg * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
+            return recon_eval(cr[0], cr[1], cr[W], cr[W + 1], xm[0], xm[1], ym[0], ym[W], av[0], xi, eta);
+        };
+        for (int c = 0; c < S.ncomp; ++c) {
+            const T *b = q + c * cs;
+            double v;
+            if (g.kind == kGPoint) {
+                v = at(b, u0, v0);
+            } else {
+                const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+                v = 0.0;
+                for (int bb = 0; bb < 3; ++bb)
+                    for (int a = 0; a < 3; ++a) v += w[a] * w[bb] * at(b, u0 + a - 1, v0 + bb - 1);
+            }
+            dst[c * cs] = (T)v;
+        }
+    }
+}
+
 template <typename T>
 __global__ void transfer_kernel(DevForest Fo, StateView<T> So, DevForest Fn, StateView<T> Sn) {
     const int p = blockIdx.x;
     const int l = __ldg(Fn.level + p), px = __ldg(Fn.ix + p), py = __ldg(Fn.iy + p);
     const int64_t words = (int64_t)Sn.ncomp * kPlanes * Sn.plane;
-    T *dst = Sn.base + (int64_t)p * words;
+    T *dst = Sn.patch(p);
     int same = -1;
     if (l <= Fo.lmax) {
         const long long side = (long long)Fo.B << l;
         same = __ldg(Fo.map + map_offset(Fo.B, l) + (long long)py * side + px);
     }
     if (same >= 0) {
-        const T *srcp = So.base + (int64_t)same * words;
+        const T *srcp = So.patch(same);
         for (int64_t e = threadIdx.x; e < words; e += blockDim.x) dst[e] = srcp[e];
         return;
     }
@@ -423,13 +610,33 @@ bool check_forest(const af_forest *f) {
 }
 
 template <typename T>
-StateView<T> view(const af_config &cfg, void *base) {
+StateView<T> view(const af_config &cfg, const af_forest &f, const af_state_pair &st) {
     StateView<T> s;
-    s.base = static_cast<T *>(base);
+    s.base0 = static_cast<T *>(st.buf[0]);
+    s.base1 = static_cast<T *>(st.buf[1]);
+    s.level = f.d_level;
+    s.parity = st.parity;
     s.plane = plane_stride(cfg.n);
     s.ncomp = cfg.ncomp;
     s.W = cfg.n + 2 * kGhost + 1;
     return s;
+}
+
+af_state_pair single(const void *d_state) {
+    af_state_pair p;
+    p.buf[0] = p.buf[1] = const_cast<void *>(d_state);
+    p.parity = 0u;
+    p.pad_ = 0u;
+    return p;
+}
+
+// A pair is usable if its current arrays exist and are aligned; a pair whose
+// parity is zero may leave buf[1] NULL.
+af_status check_pair(const af_state_pair *st) {
+    if (!st || !st->buf[0] || (st->parity != 0u && !st->buf[1])) return AF_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(st->buf[0]) | reinterpret_cast<uintptr_t>(st->buf[1])) & 31u)
+        return AF_ERR_LAYOUT;
+    return AF_OK;
 }
 
 inline af_status launched() { return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ERR_CUDA; }
@@ -464,80 +671,179 @@ extern "C" af_status af_forest_build_map(int32_t nleaf, int32_t B, int32_t lmax,
     return AF_OK;
 }
 
-extern "C" af_status af_fill_ghosts(const af_config *cfg, const af_forest *forest, uint32_t dst_levels,
-                                    uint32_t src_levels, int32_t flags, void *d_state, void *stream) {
+extern "C" af_status af_fill_ghosts_pair(const af_config *cfg, const af_forest *forest, uint32_t dst_levels,
+                                         uint32_t src_levels, int32_t flags, const af_state_pair *state,
+                                         void *stream) {
     if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
     if (forest->nleaf == 0) return AF_OK;
-    if (!d_state) return AF_ERR_ARG;
-    if (reinterpret_cast<uintptr_t>(d_state) & 31u) return AF_ERR_LAYOUT;
+    if (const af_status e = check_pair(state)) return e;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const DevForest F = make_dev(*forest, cfg->n);
     for (int pass = 0; pass < 3; ++pass) {
         if ((flags & AF_FILL_SAME_LEVEL_ONLY) && pass != 1) continue;
         if (cfg->prec == AF_F64)
-            fill_kernel<double><<<forest->nleaf, 256, 0, s>>>(F, view<double>(*cfg, d_state), dst_levels, src_levels,
-                                                              flags, pass);
+            fill_kernel<double><<<forest->nleaf, 256, 0, s>>>(F, view<double>(*cfg, *forest, *state), dst_levels,
+                                                              src_levels, flags, pass);
         else
-            fill_kernel<float><<<forest->nleaf, 256, 0, s>>>(F, view<float>(*cfg, d_state), dst_levels, src_levels,
-                                                             flags, pass);
+            fill_kernel<float><<<forest->nleaf, 256, 0, s>>>(F, view<float>(*cfg, *forest, *state), dst_levels,
+                                                             src_levels, flags, pass);
         if (launched() != AF_OK) return AF_ERR_CUDA;
     }
     return AF_OK;
 }
 
-extern "C" af_status af_transfer(const af_config *cfg, const af_forest *old_forest, const void *d_old,
-                                 const af_forest *new_forest, void *d_new, void *stream) {
-    if (!check_cfg(cfg) || !check_forest(old_forest) || !check_forest(new_forest)) return AF_ERR_ARG;
-    if (old_forest->B != new_forest->B || old_forest->lmax != new_forest->lmax) return AF_ERR_ARG;
-    if (new_forest->nleaf == 0) return AF_OK;
-    if (!d_old || !d_new || d_old == d_new) return AF_ERR_ARG;
-    if ((reinterpret_cast<uintptr_t>(d_old) | reinterpret_cast<uintptr_t>(d_new)) & 31u) return AF_ERR_LAYOUT;
+extern "C" af_status af_fill_ghosts(const af_config *cfg, const af_forest *forest, uint32_t dst_levels,
+                                    uint32_t src_levels, int32_t flags, void *d_state, void *stream) {
+    const af_state_pair st = single(d_state);
+    return af_fill_ghosts_pair(cfg, forest, dst_levels, src_levels, flags, &st, stream);
+}
+
+// Upward-closed level set: with its lowest level it holds every level up to lmax.
+static bool upward_closed(uint32_t levels, int lmax) {
+    if (levels == 0u) return true;
+    const int lo = __builtin_ctz(levels);
+    const uint32_t want = (lmax >= 31 ? 0xffffffffu : ((1u << (lmax + 1)) - 1u)) & ~((1u << lo) - 1u);
+    return (levels & want) == want;
+}
+
+extern "C" af_status af_ghost_plan_count(const af_config *cfg, const af_forest *forest, int32_t flags,
+                                         int64_t *d_counts, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(forest) || !d_counts) return AF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(d_counts) & 7u) return AF_ERR_LAYOUT;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const DevForest Fo = make_dev(*old_forest, cfg->n), Fn = make_dev(*new_forest, cfg->n);
-    if (cfg->prec == AF_F64)
-        transfer_kernel<double><<<new_forest->nleaf, 256, 0, s>>>(Fo, view<double>(*cfg, const_cast<void *>(d_old)), Fn,
-                                                                 view<double>(*cfg, d_new));
-    else
-        transfer_kernel<float><<<new_forest->nleaf, 256, 0, s>>>(Fo, view<float>(*cfg, const_cast<void *>(d_old)), Fn,
-                                                                view<float>(*cfg, d_new));
+    if (cudaMemsetAsync(d_counts, 0, 2 * sizeof(int64_t), s) != cudaSuccess) return AF_ERR_CUDA;
+    if (forest->nleaf == 0) return AF_OK;
+    plan_count_kernel<<<forest->nleaf, 256, 0, s>>>(make_dev(*forest, cfg->n), plane_stride(cfg->n), flags,
+                                                     reinterpret_cast<unsigned long long *>(d_counts));
     return launched();
 }
 
-extern "C" af_status af_reflux(const af_config *cfg, const af_forest *forest, uint32_t sync_levels, double dx0,
-                               double dy0, double *d_flux_reg, void *d_state, void *stream) {
+extern "C" af_status af_ghost_plan_build(const af_config *cfg, const af_forest *forest, int32_t flags, void *d_plan,
+                                         int64_t n_a, int64_t n_b, int64_t *d_scratch, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(forest) || !d_scratch || n_a < 0 || n_b < 0) return AF_ERR_ARG;
+    if (n_a + n_b > 0 && !d_plan) return AF_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_plan) | reinterpret_cast<uintptr_t>(d_scratch)) & 15u) return AF_ERR_LAYOUT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // scratch: two slot cursors and an overflow flag
+    if (cudaMemsetAsync(d_scratch, 0, 3 * sizeof(int64_t), s) != cudaSuccess) return AF_ERR_CUDA;
+    if (forest->nleaf == 0) return AF_OK;
+    plan_build_kernel<<<forest->nleaf, 256, 0, s>>>(
+        make_dev(*forest, cfg->n), plane_stride(cfg->n), flags, static_cast<GhostEntry *>(d_plan), n_a, n_b,
+        reinterpret_cast<unsigned long long *>(d_scratch), reinterpret_cast<int *>(d_scratch + 2));
+    return launched();
+}
+
+extern "C" af_status af_fill_ghosts_planned(const af_config *cfg, const af_forest *forest, uint32_t levels,
+                                            int32_t flags, const void *d_plan, int64_t n_a, int64_t n_b,
+                                            const af_state_pair *state, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(forest) || n_a < 0 || n_b < 0) return AF_ERR_ARG;
+    if (!upward_closed(levels, forest->lmax)) return AF_ERR_ARG;
+    if (n_a + n_b == 0 || levels == 0u) return AF_OK;
+    if (!d_plan) return AF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(d_plan) & 15u) return AF_ERR_LAYOUT;
+    if (const af_status e = check_pair(state)) return e;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const GhostEntry *plan = static_cast<const GhostEntry *>(d_plan);
+    const int same = (flags & AF_FILL_SAME_LEVEL_ONLY) ? 1 : 0;
+    auto grid = [](int64_t m) { return (int)(m / 256 + 1 < 152 * 16 ? m / 256 + 1 : 152 * 16); };
+    if (n_a > 0) {
+        if (cfg->prec == AF_F64)
+            plan_exec_a<double><<<grid(n_a), 256, 0, s>>>(view<double>(*cfg, *forest, *state), plan, n_a, levels, same);
+        else
+            plan_exec_a<float><<<grid(n_a), 256, 0, s>>>(view<float>(*cfg, *forest, *state), plan, n_a, levels, same);
+        if (launched() != AF_OK) return AF_ERR_CUDA;
+    }
+    if (n_b > 0 && !same) {
+        if (cfg->prec == AF_F64)
+            plan_exec_b<double><<<grid(n_b), 256, 0, s>>>(view<double>(*cfg, *forest, *state), cfg->n, plan + n_a, n_b,
+                                                         levels);
+        else
+            plan_exec_b<float><<<grid(n_b), 256, 0, s>>>(view<float>(*cfg, *forest, *state), cfg->n, plan + n_a, n_b,
+                                                        levels);
+        if (launched() != AF_OK) return AF_ERR_CUDA;
+    }
+    return AF_OK;
+}
+
+extern "C" af_status af_transfer_pair(const af_config *cfg, const af_forest *old_forest,
+                                      const af_state_pair *old_state, const af_forest *new_forest, void *d_new,
+                                      void *stream) {
+    if (!check_cfg(cfg) || !check_forest(old_forest) || !check_forest(new_forest)) return AF_ERR_ARG;
+    if (old_forest->B != new_forest->B || old_forest->lmax != new_forest->lmax) return AF_ERR_ARG;
+    if (new_forest->nleaf == 0) return AF_OK;
+    if (const af_status e = check_pair(old_state)) return e;
+    if (!d_new || d_new == old_state->buf[0] || d_new == old_state->buf[1]) return AF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(d_new) & 31u) return AF_ERR_LAYOUT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevForest Fo = make_dev(*old_forest, cfg->n), Fn = make_dev(*new_forest, cfg->n);
+    const af_state_pair sn = single(d_new);
+    if (cfg->prec == AF_F64)
+        transfer_kernel<double><<<new_forest->nleaf, 256, 0, s>>>(Fo, view<double>(*cfg, *old_forest, *old_state), Fn,
+                                                                 view<double>(*cfg, *new_forest, sn));
+    else
+        transfer_kernel<float><<<new_forest->nleaf, 256, 0, s>>>(Fo, view<float>(*cfg, *old_forest, *old_state), Fn,
+                                                                view<float>(*cfg, *new_forest, sn));
+    return launched();
+}
+
+extern "C" af_status af_transfer(const af_config *cfg, const af_forest *old_forest, const void *d_old,
+                                 const af_forest *new_forest, void *d_new, void *stream) {
+    if (!d_old) return AF_ERR_ARG;
+    const af_state_pair so = single(d_old);
+    return af_transfer_pair(cfg, old_forest, &so, new_forest, d_new, stream);
+}
+
+extern "C" af_status af_reflux_pair(const af_config *cfg, const af_forest *forest, uint32_t sync_levels, double dx0,
+                                    double dy0, double *d_flux_reg, const af_state_pair *state, void *stream) {
     if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
     if (!(dx0 > 0.0) || !(dy0 > 0.0)) return AF_ERR_ARG;
     if (forest->nleaf == 0) return AF_OK;
-    if (!d_flux_reg || !d_state) return AF_ERR_ARG;
-    if (reinterpret_cast<uintptr_t>(d_state) & 31u) return AF_ERR_LAYOUT;
+    if (!d_flux_reg) return AF_ERR_ARG;
+    if (const af_status e = check_pair(state)) return e;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const DevForest F = make_dev(*forest, cfg->n);
     const long long total = (long long)forest->nleaf * 4 * cfg->n;
     const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
     if (cfg->prec == AF_F64)
-        reflux_kernel<double><<<blocks, 256, 0, s>>>(F, view<double>(*cfg, d_state), sync_levels, dx0, dy0, d_flux_reg);
+        reflux_kernel<double><<<blocks, 256, 0, s>>>(F, view<double>(*cfg, *forest, *state), sync_levels, dx0, dy0,
+                                                     d_flux_reg);
     else
-        reflux_kernel<float><<<blocks, 256, 0, s>>>(F, view<float>(*cfg, d_state), sync_levels, dx0, dy0, d_flux_reg);
+        reflux_kernel<float><<<blocks, 256, 0, s>>>(F, view<float>(*cfg, *forest, *state), sync_levels, dx0, dy0,
+                                                    d_flux_reg);
+    return launched();
+}
+
+extern "C" af_status af_reflux(const af_config *cfg, const af_forest *forest, uint32_t sync_levels, double dx0,
+                               double dy0, double *d_flux_reg, void *d_state, void *stream) {
+    const af_state_pair st = single(d_state);
+    return af_reflux_pair(cfg, forest, sync_levels, dx0, dy0, d_flux_reg, &st, stream);
+}
+
+extern "C" af_status af_tag_pair(const af_config *cfg, const af_forest *forest, const af_state_pair *state,
+                                 int32_t comp, int32_t kind, double dx0, double dy0, double refine_thr,
+                                 double coarsen_thr, int8_t *d_tags, double *d_indicator, void *stream) {
+    if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
+    if (comp < 0 || comp >= cfg->ncomp || (kind != 0 && kind != 1)) return AF_ERR_ARG;
+    if (!(dx0 > 0.0) || !(dy0 > 0.0)) return AF_ERR_ARG;
+    if (forest->nleaf == 0) return AF_OK;
+    if (!d_tags) return AF_ERR_ARG;
+    if (const af_status e = check_pair(state)) return e;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevForest F = make_dev(*forest, cfg->n);
+    if (cfg->prec == AF_F64)
+        tag_kernel<double><<<forest->nleaf, 256, 0, s>>>(F, view<double>(*cfg, *forest, *state), comp, kind, dx0, dy0,
+                                                        refine_thr, coarsen_thr, d_tags, d_indicator);
+    else
+        tag_kernel<float><<<forest->nleaf, 256, 0, s>>>(F, view<float>(*cfg, *forest, *state), comp, kind, dx0, dy0,
+                                                       refine_thr, coarsen_thr, d_tags, d_indicator);
     return launched();
 }
 
 extern "C" af_status af_tag(const af_config *cfg, const af_forest *forest, const void *d_state, int32_t comp,
                             int32_t kind, double dx0, double dy0, double refine_thr, double coarsen_thr,
                             int8_t *d_tags, double *d_indicator, void *stream) {
-    if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
-    if (comp < 0 || comp >= cfg->ncomp || (kind != 0 && kind != 1)) return AF_ERR_ARG;
-    if (!(dx0 > 0.0) || !(dy0 > 0.0)) return AF_ERR_ARG;
-    if (forest->nleaf == 0) return AF_OK;
-    if (!d_state || !d_tags) return AF_ERR_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const DevForest F = make_dev(*forest, cfg->n);
-    if (cfg->prec == AF_F64)
-        tag_kernel<double><<<forest->nleaf, 256, 0, s>>>(F, view<double>(*cfg, const_cast<void *>(d_state)), comp, kind,
-                                                        dx0, dy0, refine_thr, coarsen_thr, d_tags, d_indicator);
-    else
-        tag_kernel<float><<<forest->nleaf, 256, 0, s>>>(F, view<float>(*cfg, const_cast<void *>(d_state)), comp, kind,
-                                                       dx0, dy0, refine_thr, coarsen_thr, d_tags, d_indicator);
-    return launched();
+    const af_state_pair st = single(d_state);
+    return af_tag_pair(cfg, forest, &st, comp, kind, dx0, dy0, refine_thr, coarsen_thr, d_tags, d_indicator, stream);
 }
 
 extern "C" int64_t af_mass_scratch_bytes(int32_t nleaf, int32_t ncomp) {
@@ -545,26 +851,41 @@ extern "C" int64_t af_mass_scratch_bytes(int32_t nleaf, int32_t ncomp) {
     return (int64_t)mass_blocks(nleaf) * ncomp * (int64_t)sizeof(double);
 }
 
-extern "C" af_status af_mass(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0,
-                             double dy0, void *d_scratch, double *d_mass, void *stream) {
+namespace af {
+namespace {
+// Both passes of the deterministic mass reduction into `part`.
+af_status launch_mass(const af_config &cfg, const af_forest &forest, const af_state_pair &st, double dx0, double dy0,
+                      double *part, double *d_mass, cudaStream_t s) {
+    const DevForest F = make_dev(forest, cfg.n);
+    const int nb = mass_blocks(forest.nleaf);
+    const int chunk = (forest.nleaf + nb - 1) / nb;
+    if (cfg.prec == AF_F64)
+        mass_partial<double><<<nb, kMassThreads, 0, s>>>(F, view<double>(cfg, forest, st), dx0, dy0, chunk, part);
+    else
+        mass_partial<float><<<nb, kMassThreads, 0, s>>>(F, view<float>(cfg, forest, st), dx0, dy0, chunk, part);
+    if (launched() != AF_OK) return AF_ERR_CUDA;
+    mass_final<<<1, kMassThreads, 0, s>>>(part, nb, cfg.ncomp, d_mass);
+    return launched();
+}
+}  // namespace
+}  // namespace af
+
+extern "C" af_status af_mass_pair(const af_config *cfg, const af_forest *forest, const af_state_pair *state,
+                                  double dx0, double dy0, void *d_scratch, double *d_mass, void *stream) {
     if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
     if (!(dx0 > 0.0) || !(dy0 > 0.0) || !d_mass || !d_scratch) return AF_ERR_ARG;
-    if (forest->nleaf > 0 && !d_state) return AF_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(d_scratch) | reinterpret_cast<uintptr_t>(d_mass)) & 7u) return AF_ERR_LAYOUT;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const DevForest F = make_dev(*forest, cfg->n);
-    const int nb = mass_blocks(forest->nleaf);
-    const int chunk = (forest->nleaf + nb - 1) / nb;
-    double *part = static_cast<double *>(d_scratch);
-    if (cfg->prec == AF_F64)
-        mass_partial<double><<<nb, kMassThreads, 0, s>>>(F, view<double>(*cfg, const_cast<void *>(d_state)), dx0, dy0,
-                                                        chunk, part);
-    else
-        mass_partial<float><<<nb, kMassThreads, 0, s>>>(F, view<float>(*cfg, const_cast<void *>(d_state)), dx0, dy0,
-                                                       chunk, part);
-    if (launched() != AF_OK) return AF_ERR_CUDA;
-    mass_final<<<1, kMassThreads, 0, s>>>(part, nb, cfg->ncomp, d_mass);
-    return launched();
+    if (forest->nleaf > 0)
+        if (const af_status e = check_pair(state)) return e;
+    af_state_pair st = state ? *state : single(nullptr);
+    return launch_mass(*cfg, *forest, st, dx0, dy0, static_cast<double *>(d_scratch), d_mass,
+                       static_cast<cudaStream_t>(stream));
+}
+
+extern "C" af_status af_mass(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0,
+                             double dy0, void *d_scratch, double *d_mass, void *stream) {
+    const af_state_pair st = single(d_state);
+    return af_mass_pair(cfg, forest, &st, dx0, dy0, d_scratch, d_mass, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -605,18 +926,7 @@ extern "C" af_status af_mass_noalloc(const af_config *cfg, const af_forest *fore
         }
         part = g_partials_addr[dev];
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const DevForest F = make_dev(*forest, cfg->n);
-    const int chunk = (forest->nleaf + nb - 1) / nb;
     // every partial sum read by mass_final is written by mass_partial first,
     // so nothing left in the array by an earlier call is used
-    if (cfg->prec == AF_F64)
-        mass_partial<double><<<nb, kMassThreads, 0, s>>>(F, view<double>(*cfg, const_cast<void *>(d_state)), dx0, dy0,
-                                                        chunk, part);
-    else
-        mass_partial<float><<<nb, kMassThreads, 0, s>>>(F, view<float>(*cfg, const_cast<void *>(d_state)), dx0, dy0,
-                                                       chunk, part);
-    if (launched() != AF_OK) return AF_ERR_CUDA;
-    mass_final<<<1, kMassThreads, 0, s>>>(part, nb, cfg->ncomp, d_mass);
-    return launched();
+    return launch_mass(*cfg, *forest, single(d_state), dx0, dy0, part, d_mass, static_cast<cudaStream_t>(stream));
 }

@@ -60,8 +60,9 @@ void get_advection(double nx, double ny, AdvectionWeights<T> &out) {
 
 template <typename T, int EQ>
 af_status launch(int k, const af_config &cfg, int nwork, const af_work *d_work, const void *d_in, void *d_out,
-                 double dt0, double dx0, double dy0, double *d_freg, cudaStream_t stream) {
+                 uint32_t swap, double dt0, double dx0, double dy0, double *d_freg, cudaStream_t stream) {
     StepArgs<T> A;
+    A.swap = swap;
     A.work = d_work;
     A.in = static_cast<const T *>(d_in);
     A.out = static_cast<T *>(d_out);
@@ -103,10 +104,12 @@ extern "C" int32_t af_step_default_tiling(const af_config *cfg) {
     return cfg ? af::default_tiling(cfg->n) : -1;
 }
 
-extern "C" af_status af_patch_step_tiled(const af_config *cfg, int32_t tiling_index, int32_t nwork,
-                                         const af_work *d_work, const void *d_in, void *d_out, double dt0,
-                                         double dx0, double dy0, double *d_flux_reg, void *stream) {
-    using namespace af;
+namespace af {
+namespace {
+
+af_status step_checked(const af_config *cfg, int32_t tiling_index, int32_t nwork, const af_work *d_work,
+                       const void *d_in, void *d_out, uint32_t swap, double dt0, double dx0, double dy0,
+                       double *d_flux_reg, void *stream) {
     if (cfg == nullptr || nwork < 0) return AF_ERR_ARG;
     if (tiling_index < 0 || tiling_index >= kNumTilings) return AF_ERR_ARG;
     if (cfg->n < 2 || cfg->n > 64) return AF_ERR_ARG;
@@ -133,11 +136,28 @@ extern "C" af_status af_patch_step_tiled(const af_config *cfg, int32_t tiling_in
     const int k = tiling_index;
     if (cfg->prec == AF_F64)
         return cfg->eq == AF_ACOUSTICS
-                   ? launch<double, AF_ACOUSTICS>(k, *cfg, nwork, d_work, d_in, d_out, dt0, dx0, dy0, d_flux_reg, s)
-                   : launch<double, AF_ADVECTION>(k, *cfg, nwork, d_work, d_in, d_out, dt0, dx0, dy0, d_flux_reg, s);
+                   ? launch<double, AF_ACOUSTICS>(k, *cfg, nwork, d_work, d_in, d_out, swap, dt0, dx0, dy0, d_flux_reg, s)
+                   : launch<double, AF_ADVECTION>(k, *cfg, nwork, d_work, d_in, d_out, swap, dt0, dx0, dy0, d_flux_reg, s);
     return cfg->eq == AF_ACOUSTICS
-               ? launch<float, AF_ACOUSTICS>(k, *cfg, nwork, d_work, d_in, d_out, dt0, dx0, dy0, d_flux_reg, s)
-               : launch<float, AF_ADVECTION>(k, *cfg, nwork, d_work, d_in, d_out, dt0, dx0, dy0, d_flux_reg, s);
+               ? launch<float, AF_ACOUSTICS>(k, *cfg, nwork, d_work, d_in, d_out, swap, dt0, dx0, dy0, d_flux_reg, s)
+               : launch<float, AF_ADVECTION>(k, *cfg, nwork, d_work, d_in, d_out, swap, dt0, dx0, dy0, d_flux_reg, s);
+}
+
+}  // namespace
+}  // namespace af
+
+extern "C" af_status af_patch_step_tiled(const af_config *cfg, int32_t tiling_index, int32_t nwork,
+                                         const af_work *d_work, const void *d_in, void *d_out, double dt0,
+                                         double dx0, double dy0, double *d_flux_reg, void *stream) {
+    return af::step_checked(cfg, tiling_index, nwork, d_work, d_in, d_out, 0u, dt0, dx0, dy0, d_flux_reg, stream);
+}
+
+extern "C" af_status af_patch_step_pair(const af_config *cfg, int32_t tiling_index, int32_t nwork,
+                                        const af_work *d_work, const af_state_pair *state, double dt0, double dx0,
+                                        double dy0, double *d_flux_reg, void *stream) {
+    if (state == nullptr) return AF_ERR_ARG;
+    return af::step_checked(cfg, tiling_index, nwork, d_work, state->buf[0], state->buf[1], state->parity, dt0, dx0,
+                            dy0, d_flux_reg, stream);
 }
 
 extern "C" af_status af_patch_step(const af_config *cfg, int32_t nwork, const af_work *d_work, const void *d_in,

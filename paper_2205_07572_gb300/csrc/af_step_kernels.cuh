@@ -37,7 +37,18 @@ struct StepArgs {
     T dtdx, dtdy;    // dt/dx and dt/dy (the same on every level)
     T fx, fy;        // flux scale: advection a/36, b/36; acoustics c/36
     double dt0;      // level-0 time step (flux registers)
+    uint32_t swap;   // bit l set: level l reads `out` and writes `in`
 };
+
+// Buffers of a work item of level l: read the current values, write the new.
+template <typename T>
+__device__ __forceinline__ const T *src_buf(const StepArgs<T> &A, int level) {
+    return ((A.swap >> level) & 1u) ? A.out : A.in;
+}
+template <typename T>
+__device__ __forceinline__ T *dst_buf(const StepArgs<T> &A, int level) {
+    return ((A.swap >> level) & 1u) ? const_cast<T *>(A.in) : A.out;
+}
 
 template <typename T, int EQ>
 struct WeightsOf;
@@ -105,7 +116,7 @@ __device__ __forceinline__ void stage_issue(const StepArgs<T> &A, const af_work 
                 sj = lj - sy * n;
             }
         }
-        const T *g = A.in + (int64_t)src * pw + ((sj + kGhost) * W + (si + kGhost));
+        const T *g = src_buf(A, wk.level) + (int64_t)src * pw + ((sj + kGhost) * W + (si + kGhost));
         T *sp = Sin + row * WX + col;
 #pragma unroll 4
         for (int cp = 0; cp < ncp; ++cp) {
@@ -132,7 +143,7 @@ __device__ __forceinline__ void stage_copy_out(const StepArgs<T> &A, const af_wo
         const int row = pos / ww, col = pos - row * ww;
         const int li = x0 - 1 + col, lj = y0 - 1 + row;
         if (li >= cxlo && li < cxhi && lj >= cylo && lj < cyhi) {
-            T *o = A.out + (int64_t)patch * pw + (int64_t)(lj + kGhost) * W + (li + kGhost);
+            T *o = dst_buf(A, wk.level) + (int64_t)patch * pw + (int64_t)(lj + kGhost) * W + (li + kGhost);
             const T *sp = Sin + row * WX + col;
             for (int cp = 0; cp < ncp; ++cp) o[cp * A.plane] = sp[cp * WSZ];
         }
@@ -268,7 +279,7 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
     const int tw = x1 - x0, th = y1 - y0;
     const int n = A.n, W_ = n + 2 * kGhost + 1;
     const int64_t pw = (int64_t)ncomp * kPlanes * A.plane;
-    T *outp = A.out + (int64_t)patch * pw;
+    T *outp = dst_buf(A, level) + (int64_t)patch * pw;
     // node lines stored by this tile: [x0, x1) plus x1 itself when the tile
     // ends on the outer edge of the advanced first ghost layer
     const int sxhi = (x1 == n + 1) ? x1 : x1 - 1;

@@ -411,3 +411,49 @@ def forest_state(n: int, ncomp: int, B: int, lmax: int, leaves, funcs, lo=(0.0, 
         wrapped = [lambda x, y, f=f: f(lo[0] + np.mod(x - lo[0], lx), lo[1] + np.mod(y - lo[1], ly)) for f in funcs]
         out[k] = g1.state(wrapped, nq=nq, ghosts=True, periodic=False)[0]
     return out.astype(dtype)
+
+
+def forest_state_fast(n: int, ncomp: int, B: int, level, ix, iy, funcs, lo=(0.0, 0.0), hi=(1.0, 1.0),
+                      nq: int = 2, dtype=np.float64, chunk: int = 2048) -> np.ndarray:
+    """Vectorised forest_state for large forests: leaves given as arrays, in
+    that order; every entry (ghost ring included) holds the periodically
+    wrapped functions' values (cell averages by nq x nq Gauss-Legendre)."""
+    lay = Layout(n, ncomp)
+    level, ix, iy = (np.asarray(a, dtype=np.int64) for a in (level, ix, iy))
+    P, w = len(level), lay.w
+    out = np.zeros((P, ncomp, 4, lay.plane), dtype=dtype)
+    lat = lay.lattice(out)
+    lx, ly = hi[0] - lo[0], hi[1] - lo[1]
+    idx = np.arange(w) - G
+    wraps = [lambda x, y, f=f: f(lo[0] + np.mod(x - lo[0], lx), lo[1] + np.mod(y - lo[1], ly)) for f in funcs]
+    for s in range(0, P, chunk):
+        e = min(P, s + chunk)
+        side = (B << level[s:e]).astype(np.float64)
+        dx, dy = lx / (side * n), ly / (side * n)                      # [p]
+        ox, oy = lo[0] + ix[s:e] * n * dx, lo[1] + iy[s:e] * n * dy
+        xl = ox[:, None] + idx[None, :] * dx[:, None]                   # [p, I]
+        yl = oy[:, None] + idx[None, :] * dy[:, None]                   # [p, J]
+        xc, yc = xl + 0.5 * dx[:, None], yl + 0.5 * dy[:, None]
+        XL, YL = xl[:, None, :], yl[:, :, None]                         # [p, J, I]
+        XC, YC = xc[:, None, :], yc[:, :, None]
+        DX, DY = dx[:, None, None], dy[:, None, None]
+        for c, f in enumerate(wraps):
+            lat[s:e, c, AVG] = cell_averages(f, XC, YC, DX, DY, nq)
+            lat[s:e, c, XMID] = f(XL, YC)
+            lat[s:e, c, CORNER] = f(XL, YL)
+            lat[s:e, c, YMID] = f(XC, YL)
+    return out
+
+
+def refine_band(B: int, lo, hi, inside):
+    """Refinement predicate on arrays: a level-l region (ix, iy) of the B x B
+    brick over [lo, hi] is refined if inside(x, y) holds at any of its 5 x 5
+    sample points (corners, edges and interior)."""
+    def pred(l, ix, iy):
+        side = B << np.asarray(l)
+        w, h = (hi[0] - lo[0]) / side, (hi[1] - lo[1]) / side
+        t = np.linspace(0.0, 1.0, 5)
+        x = lo[0] + (np.asarray(ix)[..., None, None] + t[None, :]) * np.asarray(w)[..., None, None]
+        y = lo[1] + (np.asarray(iy)[..., None, None] + t[:, None]) * np.asarray(h)[..., None, None]
+        return inside(x, y).any(axis=(-1, -2))
+    return pred

@@ -49,3 +49,75 @@ def test_forest_map_and_neighbours(amr):
     for l in F.levels:
         sl = F.level_slice(l)
         assert all(F.level[sl] == l)
+
+
+def test_batched_schedule_advances_each_level_by_its_substeps(amr, monkeypatch):
+    """Host logic of the batched driver, with the library calls recorded
+    instead of launched: at every time of the subcycled schedule one step
+    call covers exactly the work items of the levels due (a suffix of the
+    leaf order), each level is advanced 2^(l - lmin) times per coarse step
+    from the array its parity bit names, and the conservative fix plus ghost
+    exchange run at the synchronised times (Section 3.2)."""
+    from paper_2205_07572_gb300 import af
+    calls = []
+    monkeypatch.setattr(af, "patch_step_pair",
+                        lambda cfg, tiling, work, nwork, pair, *a, **k: calls.append(("step", work, nwork, pair.parity)))
+    monkeypatch.setattr(af, "fill_ghosts_pair", lambda cfg, F, dst, src, flags, pair, *a, **k:
+                        calls.append(("fill", dst, src, pair.parity)))
+    monkeypatch.setattr(af, "reflux_pair", lambda cfg, F, sync, *a, **k: calls.append(("reflux", sync)))
+    leaves = _sorted(S.balanced_forest(1, 2, 4, lambda l, x, y: x == y))
+    cfg = af.config(af.ACOUSTICS, af.F64, 8, c=1.0)
+    st = np.zeros((len(leaves), af.patch_words(8, 3)))
+    run = amr.AMRRun(cfg, 1, 4, leaves, st, (0, 0), (1, 1), 0.01, device="cpu")
+    calls.clear()
+    base = run.work_all.data_ptr()
+    counts = {l: 0 for l in run.forest.levels}
+    p_before = run.parity
+    lmin = run.forest.levels[0]
+    run.coarse_step()
+    assert run.parity == p_before ^ (1 << lmin)    # only the coarsest level flips
+    par = p_before
+    wl = run.work_all.numpy().view(np.int32).reshape(-1, 16)[:, 1]
+    for c in calls:
+        if c[0] == "step":
+            first = (c[1] - base) // 64
+            due = set(wl[first:first + c[2]].tolist())
+            assert first + c[2] == run.nwork and due == set(range(min(due), 5)) & set(run.forest.levels)
+            assert c[3] == par
+            for l in due:
+                counts[l] += 1
+            par ^= sum(1 << l for l in range(min(due), 5))
+        elif c[0] == "fill":
+            assert c[1] == c[2] and c[3] == par
+    assert counts == {l: 1 << (l - lmin) for l in run.forest.levels}
+    syncs = [c[1] for c in calls if c[0] == "reflux"]
+    nsub = 1 << (4 - lmin)
+    expect = []
+    for s in range(nsub):
+        m = sum(1 << l for l in range(lmin, 5) if (s + 1) % (1 << (4 - l)) == 0)
+        if bin(m).count("1") > 1:
+            expect.append(m)
+    assert syncs == expect and len(syncs) >= 1
+    assert run.launches_per_coarse_step() == nsub + 4 * len(expect)
+    assert run.cell_updates_per_coarse_step() == sum(
+        int((run.forest.level == l).sum()) * 64 << (l - lmin) for l in run.forest.levels)
+
+
+def test_native_regrid_rejects_bad_input(amr):
+    from paper_2205_07572_gb300 import af
+    F = amr.Forest(1, 3, [(1, x, y) for y in range(2) for x in range(2)], device="cpu")
+    assert amr.regrid_leaves(F, np.zeros(4, np.int8), 1) == F.leaves
+    assert len(amr.regrid_leaves(F, np.array([1, 0, 0, 0], np.int8), 1)) == 7
+    import ctypes as C
+    L = amr._lib()
+    lv = np.array([1, 1], np.int32)
+    xy = np.array([0, 0], np.int32)
+    cnt = C.c_int32(0)
+    tags = np.zeros(2, np.int8)
+    st = L.af_forest_regrid(2, 1, 1, 3, amr._ip(lv), amr._ip(xy), amr._ip(xy), tags.ctypes.data, 0, None, None,
+                            None, C.byref(cnt))
+    assert st == 1  # duplicate leaf: AF_ERR_ARG
+    lv2 = np.array([5], np.int32)
+    st = L.af_forest_regrid(1, 1, 1, 3, amr._ip(lv2), amr._ip(xy), amr._ip(xy), tags.ctypes.data, 0, None, None,
+                            None, C.byref(cnt))
+    assert st == 1  # level above lmax

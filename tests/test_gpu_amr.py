@@ -170,7 +170,7 @@ def test_tag_and_mass_match_oracle(af, kind):
     assert (tags_ref == 1).any() and (tags_ref != 1).any()
 
 
-def _runs(af, eq, prec, n, lmin, lmax, funcs, cfl, leaves=None):
+def _runs(af, eq, prec, n, lmin, lmax, funcs, cfl, leaves=None, mode="batched", graphs=False):
     from paper_2205_07572_gb300.amr import AMRRun
     nc = 1 if eq == 0 else 3
     leaves = leaves or _sorted(_diag_forest(lmin, lmax))
@@ -181,7 +181,8 @@ def _runs(af, eq, prec, n, lmin, lmax, funcs, cfl, leaves=None):
     dt0 = cfl * dx0 / (1.0 if eq == 0 else 1.0)
     Fo = OracleForest(eq, n, 1, lmax, leaves, (0, 0), (1, 1), dt0, 1.0, 0.5, 1.0, state=st)
     Fo.sync_fill((1 << (lmax + 1)) - 1)
-    run = AMRRun(af.config(eq, prec, n, 1.0, 0.5, 1.0), 1, lmax, leaves, st, (0, 0), (1, 1), dt0)
+    run = AMRRun(af.config(eq, prec, n, 1.0, 0.5, 1.0), 1, lmax, leaves, st, (0, 0), (1, 1), dt0, mode=mode,
+                 graphs=graphs)
     return Fo, run
 
 
@@ -194,14 +195,16 @@ def _compare(Fo, run, n, nc, tol):
         assert _nerr(g[:, c], r[:, c]) < tol, (c, _nerr(g[:, c], r[:, c]))
 
 
+@pytest.mark.parametrize("mode", ["batched", "per_level", "per_patch"])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("eq", [0, 1])
-def test_subcycled_amr_run_matches_oracle(af, eq, prec):
+def test_subcycled_amr_run_matches_oracle(af, eq, prec, mode):
     """Fixed diagonal forest, levels 2-3, several coarse steps with
-    subcycling, reflux and ghost exchange (Section 3.2)."""
+    subcycling, reflux and ghost exchange (Section 3.2), in each of the
+    driver's launch modes."""
     n = 8
     funcs = [S.sinsin_plus_gaussian] if eq == 0 else S.pulse_plus_vortex()
-    Fo, run = _runs(af, eq, prec, n, 2, 3, funcs, 0.6 if eq == 0 else 0.4)
+    Fo, run = _runs(af, eq, prec, n, 2, 3, funcs, 0.6 if eq == 0 else 0.4, mode=mode)
     m0 = run.mass()
     for _ in range(3):
         Fo.coarse_step()
@@ -245,3 +248,122 @@ def test_dynamic_regrid_run_matches_oracle(af, prec):
     torch.cuda.synchronize()
     assert len(set(l for l, _, _ in Fo.leaves)) >= 2
     _compare(Fo, run, n, 1, TOL[prec] * (10 if prec else 1))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replayed_amr_run_matches_oracle(af, prec):
+    """Levels 2-4, batched launches captured in CUDA graphs: the first coarse
+    step from each level parity runs eagerly, the second is captured, the
+    rest are replays -- six coarse steps exercise both graphs."""
+    n = 8
+    leaves = _sorted(S.balanced_forest(1, 2, 4, lambda l, x, y: x == y))
+    Fo, run = _runs(af, 1, prec, n, 2, 4, S.pulse_plus_vortex(), 0.4, leaves=leaves, graphs=True)
+    m0 = run.mass()
+    for _ in range(6):
+        Fo.coarse_step()
+        run.coarse_step()
+    torch.cuda.synchronize()
+    assert len([g for g in run.graphs.values() if g is not None]) == 2
+    _compare(Fo, run, n, 3, TOL[prec] * (10 if prec else 1))
+    if prec == 0:
+        assert np.abs(run.mass() - m0).max() < 1e-13 * max(1.0, np.abs(m0).max())
+
+
+def test_pair_entry_points_match_single_array(af):
+    """af_*_pair on a state split between two arrays (levels 2 and 4 current
+    in buf[1], level 3 in buf[0]; the stale entries are NaN) give the results
+    of the single-array calls on the assembled state."""
+    n, lmax, nc = 8, 4, 3
+    leaves = _sorted(S.balanced_forest(1, 2, 4, lambda l, x, y: x == y))
+    st = S.forest_state(n, nc, 1, lmax, leaves, S.pulse_plus_vortex(), nq=2).reshape(len(leaves), -1)
+    st = np.nan_to_num(st)  # plane padding: only the stale halves hold NaN
+    F = _device_forest(af, leaves, lmax)
+    cfg = af.config(1, 0, n, c=1.0)
+    parity = (1 << 2) | (1 << 4)
+    one = torch.from_numpy(st).cuda()
+    b0 = torch.full_like(one, float("nan"))
+    b1 = torch.full_like(one, float("nan"))
+    for l in F.levels:
+        sl = F.level_slice(l)
+        (b1 if (parity >> l) & 1 else b0)[sl] = one[sl]
+    pair = af.state_pair(b0, b1, parity)
+
+    def assemble():
+        out = b0.clone()
+        for l in F.levels:
+            if (parity >> l) & 1:
+                sl = F.level_slice(l)
+                out[sl] = b1[sl]
+        return out
+
+    allm = (1 << (lmax + 1)) - 1
+    af.fill_ghosts(cfg, F.c, allm, allm, 0, one)
+    af.fill_ghosts_pair(cfg, F.c, allm, allm, 0, pair)
+    freg = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, (len(leaves), 4 * nc * n))).cuda()
+    freg2 = freg.clone()
+    af.reflux(cfg, F.c, 0b11100, 1 / 8, 1 / 8, freg, one)
+    af.reflux_pair(cfg, F.c, 0b11100, 1 / 8, 1 / 8, freg2, pair)
+    torch.cuda.synchronize()
+    assert torch.equal(assemble(), one)
+    assert torch.equal(freg, freg2)
+    t1 = torch.zeros(len(leaves), dtype=torch.int8, device="cuda")
+    t2 = torch.zeros_like(t1)
+    i1 = torch.zeros(len(leaves), dtype=torch.float64, device="cuda")
+    i2 = torch.zeros_like(i1)
+    af.tag(cfg, F.c, one, 0, 0, 1 / 8, 1 / 8, 0.05, 0.01, t1, i1)
+    af.tag_pair(cfg, F.c, pair, 0, 0, 1 / 8, 1 / 8, 0.05, 0.01, t2, i2)
+    sc = torch.zeros(af.mass_scratch_bytes(len(leaves), nc) // 8, dtype=torch.float64, device="cuda")
+    m1 = torch.zeros(nc, dtype=torch.float64, device="cuda")
+    m2 = torch.zeros_like(m1)
+    af.mass(cfg, F.c, one, 1 / 8, 1 / 8, sc, m1)
+    af.mass_pair(cfg, F.c, pair, 1 / 8, 1 / 8, sc, m2)
+    torch.cuda.synchronize()
+    assert torch.equal(t1, t2) and torch.equal(i1, i2) and torch.equal(m1, m2)
+    from paper_2205_07572_gb300.amr import regrid_leaves
+    new = regrid_leaves(F, np.where(np.arange(len(leaves)) % 3 == 0, 1, -1).astype(np.int8), 2)
+    Fn = _device_forest(af, new, lmax)
+    n1 = torch.zeros((len(new), st.shape[1]), dtype=torch.float64, device="cuda")
+    n2 = torch.zeros_like(n1)
+    af.transfer(cfg, F.c, one, Fn.c, n1)
+    af.transfer_pair(cfg, F.c, pair, Fn.c, n2)
+    torch.cuda.synchronize()
+    assert torch.equal(n1, n2)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("eq", [0, 1])
+def test_planned_fill_equals_direct_fill_bitwise(af, eq, prec):
+    """af_fill_ghosts_planned == af_fill_ghosts bit for bit (all levels, and
+    the synchronised sets of the finest two and three levels), on a state
+    split between two arrays; the plan counts match the entries written."""
+    n, lmax = 8, 4
+    nc = 1 if eq == 0 else 3
+    leaves = _sorted(_diag_forest(2, 4, lambda l, x, y: l == 3 and x == 5 and y == 2))
+    st = np.nan_to_num(S.random_state(S.Layout(n, nc), len(leaves), seed=77).reshape(len(leaves), -1))
+    F = _device_forest(af, leaves, lmax)
+    cfg = af.config(eq, prec, n, 1.0, 0.5, 1.0)
+    tdt = torch.float64 if prec == 0 else torch.float32
+    plan, n_a, n_b = af.ghost_plan(cfg, F.c)
+    assert n_a > 0 and n_b > 0
+    allm = (1 << (lmax + 1)) - 1
+    for levels in (allm, 0b11000, 0b11100):
+        one = torch.from_numpy(st).to(tdt).cuda()
+        af.fill_ghosts(cfg, F.c, levels, levels, 0, one)
+        parity = 0b01010
+        b0 = torch.from_numpy(st).to(tdt).cuda()
+        b1 = torch.full_like(b0, float("nan"))
+        for l in F.levels:
+            if (parity >> l) & 1:
+                sl = F.level_slice(l)
+                b1[sl] = b0[sl]
+                b0[sl] = float("nan")
+        af.fill_ghosts_planned(cfg, F.c, levels, 0, plan, n_a, n_b, af.state_pair(b0, b1, parity))
+        torch.cuda.synchronize()
+        got = b0.clone()
+        for l in F.levels:
+            if (parity >> l) & 1:
+                sl = F.level_slice(l)
+                got[sl] = b1[sl]
+        assert torch.equal(got, one), levels
+    with pytest.raises(af.AFError):
+        af.fill_ghosts_planned(cfg, F.c, 0b01100, 0, plan, n_a, n_b, af.state_pair(one, None, 0))
