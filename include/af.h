@@ -396,6 +396,68 @@ af_status af_mass_pair(const af_config *cfg, const af_forest *forest, const af_s
 af_status af_mass_noalloc(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0,
                           double dy0, double *d_mass, void *stream);
 
+/* ======================================================================
+ * Learned refinement tagger.  The paper tags a patch from a per-patch
+ * criterion (Section 3; the undivided-difference indicator of Sections 4.4
+ * and 4.5.2, af_tag kind 1).  These entry points replace that criterion by a
+ * small network trained on the plain criterion's own tags: from a patch's
+ * cell averages with a two-cell halo at one regrid, it predicts the tag the
+ * plain criterion gives at the next one, so refinement can move ahead of
+ * the solution.  The paper has no such network; this is its definition
+ * (F = 32 channels, C = ncomp, S = n + 4, n = 8 or 16):
+ *   X[c, y, x] = bf16((Q_c(x-2, y-2) - mean of the patch's Q_c) / (2 h_l thr))
+ *   A1 = bf16(relu(conv3x3(X, bf16(W1)) + emb[level]))       [F, S-2, S-2]
+ *   Z2 = conv3x3(A1, bf16(W2)) + b2                           [F, S-4, S-4]
+ *   M[g] = max(0, max over pixels of Z2[g]);  logit = w3 . M + b3
+ * conv3x3(A, W)[g, y, x] = sum_{f, ky, kx} W[g, f, ky, kx] A[f, y+ky, x+kx]
+ * (no padding), FP32 arithmetic.  The parameters are one FP32 vector
+ * (af_cnn_param_count floats): W1 [F][C][3][3], emb [16][F], W2 [F][F][3][3],
+ * b2 [F], w3 [F], b3.  X is BF16 (raw uint16 storage), [nsample][C][S][S].
+ * Training minimises sum_p weight_p BCE(logit_p, label_p) / sum_p weight_p
+ * with Adam.  All arrays are device arrays owned by the caller.
+ * ====================================================================== */
+int64_t af_cnn_param_count(int32_t ncomp);
+
+/* X for every leaf of the forest (nleaf x C x S x S BF16) from the current
+ * state: cells outside the patch are read from the same-level neighbour
+ * d_nbr[8p + d] (af_forest_neighbours order) where there is one, else from
+ * the leaf's own ghost ring (exchanged by af_fill_ghosts).  h_l = dx0 / 2^l;
+ * thr is the plain criterion's refinement threshold. */
+af_status af_cnn_inputs(const af_config *cfg, const af_forest *forest, const af_state_pair *state,
+                        const int32_t *d_nbr, double dx0, double thr, uint16_t *d_x, void *stream);
+
+/* Forward pass: logits, the pooled maxima M [nsample][F] and their first
+ * row-major positions d_arg [nsample][F] (-1 where M = 0), which the
+ * backward pass reuses.  d_level[k] in 0..15. */
+af_status af_cnn_forward(int32_t ncomp, int32_t n, int32_t nsample, const uint16_t *d_x, const int32_t *d_level,
+                         const float *d_params, float *d_logit, float *d_m, int32_t *d_arg, void *stream);
+
+/* Floats of scratch af_cnn_backward needs for nblocks CTAs. */
+int64_t af_cnn_partial_floats(int32_t ncomp, int32_t nblocks);
+
+/* Gradient of the weighted loss with respect to the parameters into d_grad
+ * (overwritten), from the outputs of af_cnn_forward with the same
+ * parameters.  weight_sum = sum of d_weight over the batch.  Deterministic:
+ * nblocks CTAs write partial sums to d_partial, which are then added in a
+ * fixed order.  The BF16 roundings are passed through as identities. */
+af_status af_cnn_backward(int32_t ncomp, int32_t n, int32_t nsample, const uint16_t *d_x, const int32_t *d_level,
+                          const float *d_params, const float *d_logit, const float *d_m, const int32_t *d_arg,
+                          const float *d_label, const float *d_weight, double weight_sum, float *d_partial,
+                          int32_t nblocks, float *d_grad, void *stream);
+
+/* One Adam step (Kingma & Ba): moments d_m, d_v updated in place, bias
+ * corrections for step `step` (>= 1). */
+af_status af_cnn_adam(int64_t nparam, float *d_params, float *d_m, float *d_v, const float *d_grad, int32_t step,
+                      double lr, double beta1, double beta2, double eps, void *stream);
+
+/* Final tags from the network and the plain criterion's tags d_plain (af_tag):
+ * where the network's confidence |2 sigmoid(logit) - 1| < cmin the plain tag
+ * is used (and *d_nfallback, device int32, is incremented); otherwise 1 if
+ * the network predicts refinement, else the plain tag with refinement
+ * removed (-1 stays, 1 becomes 0). */
+af_status af_cnn_tags(int32_t nleaf, const float *d_logit, const int8_t *d_plain, double cmin, int8_t *d_tags,
+                      int32_t *d_nfallback, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

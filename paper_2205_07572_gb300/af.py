@@ -360,3 +360,54 @@ def fill_ghosts_planned(cfg: Config, forest: ForestC, levels: int, flags: int, p
                         pair: StatePair, stream=None):
     _check(lib().af_fill_ghosts_planned(C.byref(cfg), C.byref(forest), levels, flags, ptr(plan), n_a, n_b,
                                         C.byref(pair), stream_handle(stream)), "af_fill_ghosts_planned")
+
+
+# ------------------------------------------------------- learned tagger
+_EXTRA += [
+    ("af_cnn_param_count", C.c_int64, [C.c_int32]),
+    ("af_cnn_inputs", C.c_int, [C.POINTER(Config), _FP, _SP, _VP, C.c_double, C.c_double, _VP, _VP]),
+    ("af_cnn_forward", C.c_int, [C.c_int32, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("af_cnn_partial_floats", C.c_int64, [C.c_int32, C.c_int32]),
+    ("af_cnn_backward", C.c_int, [C.c_int32, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                  C.c_double, _VP, C.c_int32, _VP, _VP]),
+    ("af_cnn_adam", C.c_int, [C.c_int64, _VP, _VP, _VP, _VP, C.c_int32, C.c_double, C.c_double, C.c_double,
+                              C.c_double, _VP]),
+    ("af_cnn_tags", C.c_int, [C.c_int32, _VP, _VP, C.c_double, _VP, _VP, _VP]),
+]
+if _lib is not None:
+    _register_more(_lib)
+
+
+def cnn_param_count(ncomp: int) -> int:
+    return int(lib().af_cnn_param_count(ncomp))
+
+
+def cnn_inputs(cfg: Config, forest: ForestC, pair: StatePair, nbr, dx0: float, thr: float, x, stream=None):
+    _check(lib().af_cnn_inputs(C.byref(cfg), C.byref(forest), C.byref(pair), ptr(nbr), dx0, thr, ptr(x),
+                               stream_handle(stream)), "af_cnn_inputs")
+
+
+def cnn_forward(ncomp: int, n: int, nsample: int, x, level, params, logit, m, arg, stream=None):
+    _check(lib().af_cnn_forward(ncomp, n, nsample, ptr(x), ptr(level), ptr(params), ptr(logit), ptr(m), ptr(arg),
+                                stream_handle(stream)), "af_cnn_forward")
+
+
+def cnn_partial_floats(ncomp: int, nblocks: int) -> int:
+    return int(lib().af_cnn_partial_floats(ncomp, nblocks))
+
+
+def cnn_backward(ncomp: int, n: int, nsample: int, x, level, params, logit, m, arg, label, weight,
+                 weight_sum: float, partial, nblocks: int, grad, stream=None):
+    _check(lib().af_cnn_backward(ncomp, n, nsample, ptr(x), ptr(level), ptr(params), ptr(logit), ptr(m), ptr(arg),
+                                 ptr(label), ptr(weight), float(weight_sum), ptr(partial), nblocks, ptr(grad),
+                                 stream_handle(stream)), "af_cnn_backward")
+
+
+def cnn_adam(nparam: int, params, m, v, grad, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().af_cnn_adam(nparam, ptr(params), ptr(m), ptr(v), ptr(grad), step, lr, beta1, beta2, eps,
+                             stream_handle(stream)), "af_cnn_adam")
+
+
+def cnn_tags(nleaf: int, logit, plain, cmin: float, tags, nfallback, stream=None):
+    _check(lib().af_cnn_tags(nleaf, ptr(logit), ptr(plain), cmin, ptr(tags), ptr(nfallback),
+                             stream_handle(stream)), "af_cnn_tags")

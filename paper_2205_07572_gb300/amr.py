@@ -173,26 +173,33 @@ class AMRRun:
         F = self.forest
         self.b = torch.zeros_like(self.a) if self.mode == "batched" else self.a.clone()
         self.freg = torch.zeros((F.nleaf, 4, self.cfg.ncomp, self.cfg.n), dtype=torch.float64, device=self.device)
-        w = af.build_step_work(self.cfg, np.arange(F.nleaf), F.level, F.nbr, tiling=self.tiling)
-        nwork = len(w) // 64
-        wl = w.view(np.int32).reshape(nwork, 16)[:, 1] if nwork else np.zeros(0, np.int32)
-        self.work_all = torch.from_numpy(w).to(self.device)
-        # first work item of every level (items are in leaf order)
-        self.work_start = [int(np.searchsorted(wl, l, side="left")) for l in range(self.lmax + 2)]
-        self.nwork = nwork
-        if self.mode == "per_patch":
-            wp = w.view(np.int32).reshape(nwork, 16)[:, 0] if nwork else np.zeros(0, np.int32)
-            self.patch_work = [(int(s), int(e)) for s, e in
-                               zip(np.searchsorted(wp, np.arange(F.nleaf), side="left"),
-                                   np.searchsorted(wp, np.arange(F.nleaf), side="right"))]
+        # work items are in leaf order, so every level's items are contiguous
+        self.set_tiling(self.tiling)
         self.scratch = torch.zeros(max(1, af.mass_scratch_bytes(F.nleaf, self.cfg.ncomp) // 8),
                                    dtype=torch.float64, device=self.device)
         self.mass_out = torch.zeros(self.cfg.ncomp, dtype=torch.float64, device=self.device)
         self.graphs = {}
+        self.d_nbr = torch.from_numpy(F.nbr).to(self.device)
         if self.planned_fill and str(self.device) != "cpu":
             self.plan = af.ghost_plan(self.cfg, F.c, 0, self.device)
         else:
             self.plan = None
+
+    def set_tiling(self, tiling: int):
+        """Rebuild the work list for another compiled tiling (drops captured graphs)."""
+        self.tiling = int(tiling)
+        F = self.forest
+        w = af.build_step_work(self.cfg, np.arange(F.nleaf), F.level, F.nbr, tiling=self.tiling)
+        nwork = len(w) // 64
+        wi = w.view(np.int32).reshape(nwork, 16) if nwork else np.zeros((0, 16), np.int32)
+        self.work_all = __import__("torch").from_numpy(w).to(self.device)
+        self.work_start = [int(np.searchsorted(wi[:, 1], l, side="left")) for l in range(self.lmax + 2)]
+        self.nwork = nwork
+        if self.mode == "per_patch":
+            p = np.arange(F.nleaf)
+            self.patch_work = list(zip(np.searchsorted(wi[:, 0], p, side="left").tolist(),
+                                       np.searchsorted(wi[:, 0], p, side="right").tolist()))
+        self.graphs = {}
 
     def fill(self, dst: int, src: int, flags: int = 0, stream=None):
         if self.plan is not None and dst == src and not (flags & af.FILL_ALL_PATCHES):
@@ -336,6 +343,30 @@ class AMRRun:
         self._setup()
         self.fill(self.all_levels, self.all_levels)
         return True
+
+    def cnn_inputs(self, thr: float):
+        """Learned tagger inputs of every leaf (BF16 storage, int16 tensor)."""
+        import torch
+        S = self.cfg.n + 4
+        x = torch.empty((self.forest.nleaf, self.cfg.ncomp, S, S), dtype=torch.int16, device=self.device)
+        af.cnn_inputs(self.cfg, self.forest.c, self.pair, self.d_nbr, self.dx0, thr, x)
+        return x
+
+    def tags_learned(self, tagger, comp: int, kind: int, refine_thr: float, coarsen_thr: float, cmin: float):
+        """Tags from the learned tagger with the plain criterion (af_tag) as
+        fallback where the network is not confident; returns (tags, number of
+        fallbacks)."""
+        import torch
+        nl = self.forest.nleaf
+        plain = torch.zeros(nl, dtype=torch.int8, device=self.device)
+        af.tag_pair(self.cfg, self.forest.c, self.pair, comp, kind, self.dx0, self.dy0, refine_thr, coarsen_thr,
+                    plain, None)
+        x = self.cnn_inputs(refine_thr)
+        logit, _, _ = tagger.forward(x, self.forest.d_level)
+        tags = torch.zeros(nl, dtype=torch.int8, device=self.device)
+        nf = torch.zeros(1, dtype=torch.int32, device=self.device)
+        af.cnn_tags(nl, logit, plain, cmin, tags, nf)
+        return tags.cpu().numpy(), int(nf.item())
 
     def mass(self):
         af.mass_pair(self.cfg, self.forest.c, self.pair, self.dx0, self.dy0, self.scratch, self.mass_out)
