@@ -386,9 +386,6 @@ def amr_bench(case: str, coarse_steps: int, warmup: int, per_patch: bool = True)
     c = AMR_CASES[case]
     k32, out["tuned_ms_f32"] = amr_tune(case, leaves, st, "f32")
     k64, out["tuned_ms_f64"] = amr_tune(case, leaves, st, "f64")
-    dx0 = (c["hi"][0] - c["lo"][0]) / (c["B"] * AMR_N)
-    speed = max(abs(c["a"]), abs(c["b"])) if c["eq"] == 0 else 1.0
-    t_end = (coarse_steps + max(4, warmup)) * CFL * dx0 / speed
     # graphs: the first coarse step from each level parity runs eagerly, the
     # second is captured, so four warm-up steps leave only replays timed
     r32, run32 = amr_time(case, leaves, st, "f32", "batched", True, coarse_steps, max(4, warmup), tiling=k32)
@@ -397,8 +394,8 @@ def amr_bench(case: str, coarse_steps: int, warmup: int, per_patch: bool = True)
     out["batched_f64"] = r64
     out["l1_f32_vs_f64"] = amr_l1_between(case, run32, run64)
     if c["eq"] == 0:
-        out["l1_vs_exact"] = {"f32": amr_l1_exact(case, run32, t_end), "f64": amr_l1_exact(case, run64, t_end),
-                              "t": t_end}
+        out["l1_vs_exact"] = {"f32": amr_l1_exact(case, run32, run32.time),
+                              "f64": amr_l1_exact(case, run64, run64.time), "t": run32.time}
     del run32, run64
     out["per_level_f64"], _ = amr_time(case, leaves, st, "f64", "per_level", False, max(1, coarse_steps // 2), 1)
     if per_patch:
@@ -408,16 +405,164 @@ def amr_bench(case: str, coarse_steps: int, warmup: int, per_patch: bool = True)
     rg32, g32 = amr_time(case, leaves, st, "f32", "batched", False, nrg, 1, regrid=True, tiling=k32)
     rg64, g64 = amr_time(case, leaves, st, "f64", "batched", False, nrg, 1, regrid=True, tiling=k64)
     out["regrid_every_coarse_step_f32"], out["regrid_every_coarse_step_f64"] = rg32, rg64
-    t_rg = (nrg + 1) * CFL * dx0 / speed
     if c["eq"] == 0:
-        out["regrid_l1_vs_exact"] = {"f32": amr_l1_exact(case, g32, t_rg), "f64": amr_l1_exact(case, g64, t_rg),
-                                     "t": t_rg}
+        out["regrid_l1_vs_exact"] = {"f32": amr_l1_exact(case, g32, g32.time),
+                                     "f64": amr_l1_exact(case, g64, g64.time), "t": g32.time}
     out["regrid_same_forest_f32_f64"] = g32.forest.leaves == g64.forest.leaves
     if out["regrid_same_forest_f32_f64"]:
         out["regrid_l1_f32_vs_f64"] = amr_l1_between(case, g32, g64)
     del g32, g64
     base = out.get("per_patch_f64", out["per_level_f64"])["value"]
     out["speedup_batched_f32_vs_per_patch_f64"] = r32["value"] / base
+    return out
+
+
+# ----------------------------------------------------------- learned tagging
+def adapt_initial(cfg, B, lmin, lmax, lo, hi, funcs, tag):
+    """Initial forest by the method's own adaptation (tag and regrid the exact
+    initial data once per level), and its state."""
+    import synth as S
+    from paper_2205_07572_gb300.amr import AMRRun, regrid_leaves
+    side = B << lmin
+    leaves = [(lmin, x, y) for y in range(side) for x in range(side)]
+    for _ in range(lmax - lmin):
+        lv = np.array(leaves, dtype=np.int64).reshape(-1, 3)
+        st = S.forest_state_fast(cfg.n, cfg.ncomp, B, lv[:, 0], lv[:, 1], lv[:, 2], funcs, lo, hi)
+        run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, 1e-9)
+        t, _ = run.tags(*tag)
+        new = regrid_leaves(run.forest, np.maximum(t, 0), lmin)
+        if new == run.forest.leaves:
+            break
+        leaves = new
+    lv = np.array(leaves, dtype=np.int64).reshape(-1, 3)
+    return leaves, S.forest_state_fast(cfg.n, cfg.ncomp, B, lv[:, 0], lv[:, 1], lv[:, 2], funcs, lo, hi)
+
+
+def learned_tagging(B=3, lmin=3, lmax=6, train_radii=(0.2, 0.3), test_radius=0.25, train_steps=384,
+                    test_steps=160, horizon=4, epochs=4, batch=4096, cmin=0.5, seed=0):
+    """Acoustics ring wave on the 3 x 3 brick [-1.5, 1.5]^2, 16 x 16-cell
+    patches, FP32 stencil.  The tagger is trained on runs of the method
+    (plain criterion, regrid every `horizon` coarse steps) started from rings
+    of other radii, to predict whether the plain criterion will tag a leaf at
+    any of the next `horizon` coarse steps.  From the test ring: its tags are
+    judged against the plain criterion's, and three runs of test_steps coarse
+    steps are compared by the L1 distance of p to a uniform run at the finest
+    level and by cell updates per second (regrids included): the plain
+    criterion regridding every coarse step, the plain criterion regridding
+    every `horizon` steps, and the learned tagger (plain fallback below
+    confidence cmin) regridding every `horizon` steps."""
+    import torch
+    import synth as S
+    from paper_2205_07572_gb300 import af
+    from paper_2205_07572_gb300.amr import AMRRun
+    from paper_2205_07572_gb300.tagger import Tagger, collect, prepare, uniform_global, l1_vs_uniform
+    lo, hi = (-1.5, -1.5), (1.5, 1.5)
+    n = AMR_N
+    cfg = af.config(af.ACOUSTICS, af.F32, n, c=1.0)
+    dx0 = (hi[0] - lo[0]) / (B * n)
+    dt0 = CFL * dx0
+    tag = (0, 1, 4.0, 1.0)
+    zero = lambda x, y: 0.0 * x
+    out = {"workload": (f"acoustics ring waves exp(-(r-r0)^2/0.001) cos(80 pi r) on the {B}x{B} brick "
+                        f"[-1.5,1.5]^2, levels {lmin}-{lmax}, 16x16 patches, FP32; train r0 {list(train_radii)}, "
+                        f"test r0 {test_radius}; regrid horizon {horizon} coarse steps"), "horizon": horizon}
+    t0 = time.perf_counter()
+    parts = []
+    for r0 in train_radii:
+        leaves, st = adapt_initial(cfg, B, lmin, lmax, lo, hi, [S.ring_wave_at(r0), zero, zero], tag)
+        run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
+        parts.append(collect(run, train_steps, tag, lmin, tag[2], horizon=horizon))
+        del run
+    data = {k: torch.cat([p[k] for p in parts]) for k in parts[0]}
+    torch.cuda.synchronize()
+    out["collect_s"] = round(time.perf_counter() - t0, 2)
+    data = prepare(data, batch, seed=seed)
+    out["samples"] = int(data["level"].numel())
+    out["positive_fraction"] = data["positives"] / out["samples"]
+    tg = Tagger(3, n, seed=seed)
+    ev0 = tg.evaluate(data)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    tg.fit(data, epochs=epochs, batch=batch)
+    torch.cuda.synchronize()
+    out["train_s"] = round(time.perf_counter() - t1, 3)
+    out["train_samples_per_s"] = epochs * (out["samples"] // batch) * batch / out["train_s"]
+    out["train_eval"] = {"before": ev0, "after": tg.evaluate(data)}
+    del data, parts
+    funcs = [S.ring_wave_at(test_radius), zero, zero]
+    leaves, st = adapt_initial(cfg, B, lmin, lmax, lo, hi, funcs, tag)
+    run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
+    test = prepare(collect(run, test_steps, tag, lmin, tag[2], horizon=horizon), batch, seed=seed + 1)
+    out["test_eval"] = tg.evaluate(test)
+    del run, test
+
+    def tagged_run(learned: bool, every: int):
+        run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
+        leaves_sum = cu = falls = regrids = 0
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        for k in range(test_steps):
+            if k % every == 0:
+                if learned:
+                    tags, nf = run.tags_learned(tg, *tag, cmin)
+                    falls += nf
+                else:
+                    tags, _ = run.tags(*tag)
+                regrids += 1
+                run.regrid(tags, lmin)
+            leaves_sum += run.forest.nleaf
+            cu += run.cell_updates_per_coarse_step()
+            run.coarse_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t2
+        r = {"regrids": regrids, "mean_leaves": leaves_sum / test_steps, "cell_updates": cu,
+             "cell_updates_per_s": cu / el, "wall_s": round(el, 4), "t": run.time}
+        if learned:
+            r["fallback_fraction"] = falls / max(1, leaves_sum)
+        return r, run
+
+    res, finals = {}, {}
+    for name, learned, every in (("plain_every_step", False, 1), (f"plain_every_{horizon}", False, horizon),
+                                 (f"learned_every_{horizon}", True, horizon)):
+        res[name], finals[name] = tagged_run(learned, every)
+    # reference: uniform finest level, run to the same time
+    side = B << lmax
+    ref_leaves = [(lmax, x, y) for y in range(side) for x in range(side)]
+    lv = np.array(ref_leaves, dtype=np.int64)
+    rst = S.forest_state_fast(n, 3, B, lv[:, 0], lv[:, 1], lv[:, 2], funcs, lo, hi)
+    ref = AMRRun(cfg, B, lmax, ref_leaves, rst, lo, hi, dt0)
+    del rst
+    T = res["plain_every_step"]["t"]
+    for _ in range(int(round(T / ref.coarse_dt()))):
+        ref.coarse_step()
+    out["reference"] = {"leaves": len(ref_leaves), "t": ref.time}
+    g = uniform_global(ref, 0)
+    del ref
+    for name, run in finals.items():
+        res[name]["l1_p_vs_uniform"] = l1_vs_uniform(run, g, 0)
+    del finals
+    out["runs"] = res
+    pe, pr, lr_ = res["plain_every_step"], res[f"plain_every_{horizon}"], res[f"learned_every_{horizon}"]
+    out["l1_learned_over_plain_same_regrids"] = lr_["l1_p_vs_uniform"] / pr["l1_p_vs_uniform"]
+    out["l1_learned_over_plain_every_step"] = lr_["l1_p_vs_uniform"] / pe["l1_p_vs_uniform"]
+    out["throughput_learned_over_plain_every_step"] = lr_["cell_updates_per_s"] / pe["cell_updates_per_s"]
+    # inference cost on the initial forest of the test ring
+    run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
+    x = run.cnn_inputs(tag[2])
+    fwd = tg.outputs(run.forest.nleaf)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tg.forward(x, run.forest.d_level, fwd)
+    e0.record(stream)
+    for _ in range(10):
+        run.cnn_inputs(tag[2])
+        tg.forward(x, run.forest.d_level, fwd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    flops = run.forest.nleaf * 2 * 32 * ((n + 2) ** 2 * 3 * 9 + n * n * 32 * 9)
+    out["inference"] = {"leaves": run.forest.nleaf, "ms_inputs_and_forward": ms,
+                        "tflops": flops / (ms * 1e-3) / 1e12}
     return out
 
 
@@ -460,6 +605,8 @@ def main():
                     help="which stencil precision(s) to time (profiling runs use one)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the end-to-end, literal-size, adaptive-mesh and CPU-baseline measurements")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="only the learned-tagging experiment")
     ap.add_argument("--amr-only", action="store_true",
                     help="time only the adaptive-mesh workloads (one JSON object per workload)")
     args = ap.parse_args()
@@ -511,6 +658,10 @@ def main():
             for case in AMR_CASES:
                 print(json.dumps({"amr": case, **amr_bench(case, 8, 4)}), flush=True)
         return
+    if args.learned_only:
+        if rank == 0:
+            print(json.dumps({"learned_tagging": learned_tagging()}), flush=True)
+        return
     if args.prec != "both":
         r = run_ours(args.prec, args.steps, warm, rank, world, dist)
         if rank == 0:
@@ -532,6 +683,7 @@ def main():
         lit64 = literal_config2("f64", 10) if extras else None
         cpu = None if (args.no_cpu_baseline or not extras) else oracle_sample(20)
         amr = {case: amr_bench(case, 8, 4) for case in AMR_CASES} if extras else None
+        learned = learned_tagging() if extras else None
         v64 = world * cells / (r64["ms"] * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": "cell updates/s", "n_gpus": world,
@@ -551,6 +703,7 @@ def main():
                          "algorithmic_bytes_per_launch": cells * BYTES_PER_CELL["f32"]},
             "literal_512x512": {"f32": lit32, "f64": lit64, "note": "L2-resident (34 MB FP64 state)"},
             "amr": amr,
+            "learned_tagging": learned,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

@@ -156,6 +156,7 @@ class AMRRun:
         st = np.asarray(state).reshape(len(leaves), -1)[[order[leaf] for leaf in self.forest.leaves]]
         self.a = torch.as_tensor(st).to(device=device, dtype=self.dtype).contiguous()
         self.parity = 0
+        self.time = 0.0
         self._setup()
         self.fill(self.all_levels, self.all_levels)
 
@@ -266,8 +267,13 @@ class AMRRun:
                     af.reflux(self.cfg, self.forest.c, sync, self.dx0, self.dy0, self.freg, self.a, stream)
                 self.fill(sync, sync, stream=stream)
 
+    def coarse_dt(self) -> float:
+        """Time step of the coarsest level present (one coarse step)."""
+        return self.dt0 / (1 << self.forest.levels[0])
+
     def coarse_step(self):
         """Advance all levels by the step of the coarsest level present."""
+        self.time += self.coarse_dt()
         if not self.use_graphs:
             self._schedule()
             return

@@ -113,23 +113,27 @@ class Tagger:
         return {"accuracy": acc, "recall": recall, "precision": prec, "loss": float(bce.item())}
 
 
-def collect(run, coarse_steps: int, tag: tuple, lmin: int, thr: float, regrid: bool = True):
-    """Samples from a run of the method with the plain criterion: for each
-    coarse step, every leaf's input X at the start of the step and, as its
-    label, whether the plain criterion tags it for refinement at the end of
-    the step.  Then the run is regridded with those tags, as the method does.
+def collect(run, coarse_steps: int, tag: tuple, lmin: int, thr: float, horizon: int = 1, regrid: bool = True):
+    """Samples from a run of the method with the plain criterion, regridded
+    every `horizon` coarse steps: at each regrid, every leaf's input X and, as
+    its label, whether the plain criterion tags it for refinement at the end
+    of any of the next `horizon` coarse steps (on the same forest).  The run
+    is then regridded with the last of those tags, as the method does.
     Returns device tensors (x uint16 BF16 storage, level int32, label float)."""
     import torch
     xs, levels, labels = [], [], []
     comp, kind, rthr, cthr = tag
-    for _ in range(coarse_steps):
+    for _ in range(max(1, coarse_steps // horizon)):
         x = run.cnn_inputs(thr)
         lv = run.forest.d_level.clone()
-        run.coarse_step()
-        tags, _ = run.tags(comp, kind, rthr, cthr)
+        need = np.zeros(run.forest.nleaf, dtype=bool)
+        for _ in range(horizon):
+            run.coarse_step()
+            tags, _ = run.tags(comp, kind, rthr, cthr)
+            need |= tags == 1
         xs.append(x)
         levels.append(lv)
-        labels.append(torch.from_numpy((tags == 1).astype(np.float32)).to(run.device))
+        labels.append(torch.from_numpy(need.astype(np.float32)).to(run.device))
         if regrid:
             run.regrid(tags, lmin)
     return {"x": torch.cat(xs), "level": torch.cat(levels), "label": torch.cat(labels)}
@@ -153,3 +157,48 @@ def prepare(data, batch: int, seed: int = 0, pos_weight=None):
     out["pos_weight"] = pw
     out["positives"] = int(npos)
     return out
+
+
+# ------------------------------------------------------------ evaluation
+def interior_averages(run, comp: int = 0):
+    """Host [nleaf, n, n] interior cell averages of one component (current state)."""
+    n, nc = run.cfg.n, run.cfg.ncomp
+    lay_w = n + 5
+    plane = af.plane_stride(n)
+    host = run.current().double().cpu().numpy().reshape(run.forest.nleaf, nc, 4, plane)
+    lat = host[:, comp, 0, :lay_w * lay_w].reshape(-1, lay_w, lay_w)
+    return lat[:, 2:n + 2, 2:n + 2]
+
+
+def uniform_global(run, comp: int = 0):
+    """Interior averages of a run whose leaves all have one level, as one
+    global [side*n, side*n] array (row = y)."""
+    F = run.forest
+    lv = F.level[0]
+    assert (F.level == lv).all()
+    n = run.cfg.n
+    side = F.B << int(lv)
+    a = interior_averages(run, comp)
+    g = np.zeros((side * n, side * n))
+    for k in range(F.nleaf):
+        x, y = F.ix[k], F.iy[k]
+        g[y * n:(y + 1) * n, x * n:(x + 1) * n] = a[k]
+    return g
+
+
+def l1_vs_uniform(run, ref_global, comp: int = 0) -> float:
+    """sum over leaves and cells of |Q - Q_ref| dx_l dy_l, Q_ref the uniform
+    finer run's averages over the leaf cell (exact for cell averages)."""
+    F = run.forest
+    n = run.cfg.n
+    a = interior_averages(run, comp)
+    fine = ref_global.shape[0]
+    total = 0.0
+    for k in range(F.nleaf):
+        l = int(F.level[k])
+        side = F.B << l
+        r = fine // (side * n)
+        blk = ref_global[F.iy[k] * n * r:(F.iy[k] + 1) * n * r, F.ix[k] * n * r:(F.ix[k] + 1) * n * r]
+        ref = blk.reshape(n, r, n, r).mean(axis=(1, 3))
+        total += float(np.abs(a[k] - ref).sum()) * (run.dx0 / (1 << l)) * (run.dy0 / (1 << l))
+    return total

@@ -140,6 +140,14 @@ def ring_wave(x, y):
     return np.exp(-((r - 0.25) ** 2) / 0.001) * np.cos(80 * np.pi * r)
 
 
+def ring_wave_at(r0: float, width: float = 0.001, k: float = 80.0):
+    """Ring wave exp(-(r-r0)^2/width) cos(k pi r) around the origin."""
+    def f(x, y):
+        r = np.sqrt(x * x + y * y)
+        return np.exp(-((r - r0) ** 2) / width) * np.cos(k * np.pi * r)
+    return f
+
+
 def wave_packet(x, y):
     """exp(-r^2/0.01) cos(60 pi x), centred at (0.5, 0.5)."""
     r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2
