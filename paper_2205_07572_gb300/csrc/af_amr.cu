@@ -137,30 +137,43 @@ __device__ __forceinline__ void lattice_of(const DevForest &F, int q, int k, lon
 // its corners c.., edge midpoints x./y. and average: the tensor Lagrange
 // interpolant on {-1,0,1}^2 whose centre value follows from the average,
 // (9/4) Q - (1/16) sum(corners) - (1/4) sum(edge midpoints).
-__device__ __forceinline__ double recon_eval(double c00, double c10, double c01, double c11, double xl, double xr,
-                                             double yb, double yt, double avg, double xi, double eta) {
-    const double cen = 2.25 * avg - 0.0625 * (c00 + c10 + c01 + c11) - 0.25 * (xl + xr + yb + yt);
-    const double lx0 = 0.5 * xi * (xi - 1.0), lx1 = 1.0 - xi * xi, lx2 = 0.5 * xi * (xi + 1.0);
-    const double ly0 = 0.5 * eta * (eta - 1.0), ly1 = 1.0 - eta * eta, ly2 = 0.5 * eta * (eta + 1.0);
+// Evaluated in the state's precision R (FP32 for an FP32 state: GB300's
+// FP64 rate is a small fraction of its FP32 rate).
+template <typename R>
+__device__ __forceinline__ R recon_eval(R c00, R c10, R c01, R c11, R xl, R xr, R yb, R yt, R avg, R xi, R eta) {
+    const R cen = R(2.25) * avg - R(0.0625) * (c00 + c10 + c01 + c11) - R(0.25) * (xl + xr + yb + yt);
+    const R lx0 = R(0.5) * xi * (xi - R(1)), lx1 = R(1) - xi * xi, lx2 = R(0.5) * xi * (xi + R(1));
+    const R ly0 = R(0.5) * eta * (eta - R(1)), ly1 = R(1) - eta * eta, ly2 = R(0.5) * eta * (eta + R(1));
     return ly0 * (lx0 * c00 + lx1 * yb + lx2 * c10) + ly1 * (lx0 * xl + lx1 * cen + lx2 * xr) +
            ly2 * (lx0 * c01 + lx1 * yt + lx2 * c11);
 }
 
+// Simpson's rule over a cell from the values f(a, b) at its 3 x 3 points
+// (a, b in {0, 1, 2}): exact for the biquadratic reconstruction.
+template <typename R, typename Fn>
+__device__ __forceinline__ R simpson9(Fn f) {
+    const R w[3] = {R(1) / R(6), R(2) / R(3), R(1) / R(6)};
+    R s = R(0);
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) s += w[a] * w[b] * f(a, b);
+    return s;
+}
+
 // Value of the reconstruction of leaf q, component c, at (x, y).
 template <typename T>
-__device__ double recon_at(const DevForest &F, const StateView<T> &S, int q, int c, long long x, long long y) {
+__device__ T recon_at(const DevForest &F, const StateView<T> &S, int q, int c, long long x, long long y) {
     const long long hw = hwid(F, __ldg(F.level + q));
     const long long dx = reld(F, x, leaf_x0(F, q)), dy = reld(F, y, leaf_y0(F, q));
     long long ci = dx >= 0 ? dx / hw : -1, cj = dy >= 0 ? dy / hw : -1;
     ci = ci < 0 ? 0 : (ci > F.n - 1 ? F.n - 1 : ci);
     cj = cj < 0 ? 0 : (cj > F.n - 1 ? F.n - 1 : cj);
-    const double xi = 2.0 * (double)(dx - ci * hw) / (double)hw - 1.0;
-    const double eta = 2.0 * (double)(dy - cj * hw) / (double)hw - 1.0;
+    const T xi = (T)(2.0 * (double)(dx - ci * hw) / (double)hw - 1.0);  // exact: a multiple of 1/2
+    const T eta = (T)(2.0 * (double)(dy - cj * hw) / (double)hw - 1.0);
     const int i = (int)ci, j = (int)cj;
     // Point values on the leaf's boundary lines are read from their owner:
     // a leaf whose neighbours are all same-level does not keep the copies in
     // its ghost ring current (its step reads the neighbours directly).
-    auto node = [&](int k, int ii, int jj) -> double {
+    auto node = [&](int k, int ii, int jj) -> T {
         if (ii > 0 && ii < F.n && jj > 0 && jj < F.n) return *S.at(q, c, k, ii, jj);
         long long nx, ny;
         const long long x0 = leaf_x0(F, q), y0 = leaf_y0(F, q);
@@ -173,12 +186,12 @@ __device__ double recon_at(const DevForest &F, const StateView<T> &S, int q, int
         lattice_of(F, o, lo == __ldg(F.level + q) ? k : kCorner, nx, ny, oi, oj);
         return *S.at(o, c, lo == __ldg(F.level + q) ? k : kCorner, oi, oj);
     };
-    const double c00 = node(kCorner, i, j), c10 = node(kCorner, i + 1, j);
-    const double c01 = node(kCorner, i, j + 1), c11 = node(kCorner, i + 1, j + 1);
-    const double xl = node(kXmid, i, j), xr = node(kXmid, i + 1, j);
-    const double yb = node(kYmid, i, j), yt = node(kYmid, i, j + 1);
-    const double avg = *S.at(q, c, kAvg, i, j);
-    return recon_eval(c00, c10, c01, c11, xl, xr, yb, yt, avg, xi, eta);
+    const T c00 = node(kCorner, i, j), c10 = node(kCorner, i + 1, j);
+    const T c01 = node(kCorner, i, j + 1), c11 = node(kCorner, i + 1, j + 1);
+    const T xl = node(kXmid, i, j), xr = node(kXmid, i + 1, j);
+    const T yb = node(kYmid, i, j), yt = node(kYmid, i, j + 1);
+    const T avg = *S.at(q, c, kAvg, i, j);
+    return recon_eval<T>(c00, c10, c01, c11, xl, xr, yb, yt, avg, xi, eta);
 }
 
 // Value for an entry of plane k of a destination at level lp from owner q
@@ -208,15 +221,11 @@ __device__ double transfer(const DevForest &F, const StateView<T> &S, int lp, in
         lattice_of(F, q, kCorner, x, y, i, j);
         return *S.at(q, c, kCorner, i, j);
     }
-    if (k != kAvg) return recon_at<T>(F, S, q, c, x, y);
+    if (k != kAvg) return (double)recon_at<T>(F, S, q, c, x, y);
     // Simpson's rule over the destination cell (half width h), exact for the
     // coarse biquadratic
     const long long h = hwid(F, lp) / 2;
-    const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
-    double s = 0.0;
-    for (int b = 0; b < 3; ++b)
-        for (int a = 0; a < 3; ++a) s += w[a] * w[b] * recon_at<T>(F, S, q, c, x + (a - 1) * h, y + (b - 1) * h);
-    return s;
+    return (double)simpson9<T>([&](int a, int b) { return recon_at<T>(F, S, q, c, x + (a - 1) * h, y + (b - 1) * h); });
 }
 
 __device__ __forceinline__ void entry_xy(const DevForest &F, int p, int k, int i, int j, long long &x, long long &y) {
@@ -412,29 +421,21 @@ __global__ void plan_exec_b(StateView<T> S, int n, const GhostEntry *__restrict_
         const int W = S.W;
         // value at quarter-cell position (u, v) of the source leaf, with the
         // cell chosen as the direct exchange chooses it
-        auto at = [&](const T *b, int u, int v) -> double {
+        auto at = [&](const T *b, int u, int v) -> T {
             int ci = u / 4, cj = v / 4;
             ci = ci > n - 1 ? n - 1 : ci;
             cj = cj > n - 1 ? n - 1 : cj;
-            const double xi = 0.5 * (double)(u - 4 * ci) - 1.0, eta = 0.5 * (double)(v - 4 * cj) - 1.0;
+            const T xi = (T)(0.5 * (double)(u - 4 * ci) - 1.0), eta = (T)(0.5 * (double)(v - 4 * cj) - 1.0);
             const T *cr = b + kCorner * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
             const T *xm = b + kXmid * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
             const T *ym = b + kYmid * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
             const T *av = b + kAvg * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
-            return recon_eval(cr[0], cr[1], cr[W], cr[W + 1], xm[0], xm[1], ym[0], ym[W], av[0], xi, eta);
+            return recon_eval<T>(cr[0], cr[1], cr[W], cr[W + 1], xm[0], xm[1], ym[0], ym[W], av[0], xi, eta);
         };
         for (int c = 0; c < S.ncomp; ++c) {
             const T *b = q + c * cs;
-            double v;
-            if (g.kind == kGPoint) {
-                v = at(b, u0, v0);
-            } else {
-                const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
-                v = 0.0;
-                for (int bb = 0; bb < 3; ++bb)
-                    for (int a = 0; a < 3; ++a) v += w[a] * w[bb] * at(b, u0 + a - 1, v0 + bb - 1);
-            }
-            dst[c * cs] = (T)v;
+            dst[c * cs] = g.kind == kGPoint ? at(b, u0, v0)
+                                            : simpson9<T>([&](int a, int bb) { return at(b, u0 + a - 1, v0 + bb - 1); });
         }
     }
 }
