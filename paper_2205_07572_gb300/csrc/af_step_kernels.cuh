@@ -88,6 +88,7 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 template <typename T, int NT, int WX, int WSZ>
 __device__ __forceinline__ void stage_issue(const StepArgs<T> &A, const af_work &wk, T *Sin) {
     const int patch = wk.patch, x0 = wk.x0, y0 = wk.y0;
+    const T *const in = src_buf(A, wk.level);
     const int ww = wk.x1 - x0 + 3, wh = wk.y1 - y0 + 3;
     int nb[8];
 #pragma unroll
@@ -116,7 +117,7 @@ __device__ __forceinline__ void stage_issue(const StepArgs<T> &A, const af_work 
                 sj = lj - sy * n;
             }
         }
-        const T *g = src_buf(A, wk.level) + (int64_t)src * pw + ((sj + kGhost) * W + (si + kGhost));
+        const T *g = in + (int64_t)src * pw + ((sj + kGhost) * W + (si + kGhost));
         T *sp = Sin + row * WX + col;
 #pragma unroll 4
         for (int cp = 0; cp < ncp; ++cp) {
@@ -132,6 +133,7 @@ __device__ __forceinline__ void stage_issue(const StepArgs<T> &A, const af_work 
 // complete patch (advanced entries are overwritten afterwards).
 template <typename T, int NT, int WX, int WSZ>
 __device__ __forceinline__ void stage_copy_out(const StepArgs<T> &A, const af_work &wk, const T *Sin) {
+    T *const out = dst_buf(A, wk.level);
     const int patch = wk.patch, x0 = wk.x0, y0 = wk.y0, x1 = wk.x1, y1 = wk.y1;
     const int ww = x1 - x0 + 3, wh = y1 - y0 + 3;
     const int n = A.n, W = n + 2 * kGhost + 1;
@@ -143,7 +145,7 @@ __device__ __forceinline__ void stage_copy_out(const StepArgs<T> &A, const af_wo
         const int row = pos / ww, col = pos - row * ww;
         const int li = x0 - 1 + col, lj = y0 - 1 + row;
         if (li >= cxlo && li < cxhi && lj >= cylo && lj < cyhi) {
-            T *o = dst_buf(A, wk.level) + (int64_t)patch * pw + (int64_t)(lj + kGhost) * W + (li + kGhost);
+            T *o = out + (int64_t)patch * pw + (int64_t)(lj + kGhost) * W + (li + kGhost);
             const T *sp = Sin + row * WX + col;
             for (int cp = 0; cp < ncp; ++cp) o[cp * A.plane] = sp[cp * WSZ];
         }
@@ -408,6 +410,14 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
     }
 }
 
+// Resident CTAs per SM the register allocation must allow: FP32 acoustics
+// is issue-bound and needs about 24 warps per SM to hide its shared-memory
+// and staging latency (80 registers at 128 threads).
+template <typename T, int EQ, int NT>
+__host__ __device__ constexpr int min_ctas() {
+    return (EQ == AF_ACOUSTICS && sizeof(T) == 4) ? (768 / NT > 0 ? 768 / NT : 1) : 1;
+}
+
 // Shared-memory geometry of a TMX x TMY tile.
 template <int TMX, int TMY>
 struct Geo {
@@ -417,14 +427,14 @@ struct Geo {
 
 // One tile per CTA.
 template <typename T, int EQ, int NT, int TMX, int TMY>
-__global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ StepArgs<T> A,
+__global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel(const __grid_constant__ StepArgs<T> A,
                                                   const __grid_constant__ typename WeightsOf<T, EQ>::type W) {
     using Gm = Geo<TMX, TMY>;
     constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Sin = reinterpret_cast<T *>(smem_raw);
     T *ST = Sin + ncomp * kPlanes * Gm::WSZ;
-    const af_work &wk = A.work[blockIdx.x];
+    const af_work wk = A.work[blockIdx.x];  // by value: read once
     if (wk.x1 - wk.x0 > TMX || wk.y1 - wk.y0 > TMY) return;  // built for another tiling
     stage_issue<T, NT, Gm::WX, Gm::WSZ>(A, wk, Sin);
     cp_async_commit();
@@ -442,7 +452,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const __grid_constant__ StepAr
 // staged windows: while tile t is computed, the copies of the next tile are
 // already in flight.
 template <typename T, int EQ, int NT, int TMX, int TMY>
-__global__ void __launch_bounds__(NT) step_kernel_pipe(const __grid_constant__ StepArgs<T> A,
+__global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel_pipe(const __grid_constant__ StepArgs<T> A,
                                                        const __grid_constant__ typename WeightsOf<T, EQ>::type W,
                                                        int nwork) {
     using Gm = Geo<TMX, TMY>;
@@ -463,7 +473,7 @@ __global__ void __launch_bounds__(NT) step_kernel_pipe(const __grid_constant__ S
         cp_async_commit();
         cp_async_wait_one();
         __syncthreads();
-        const af_work &wk = A.work[t];
+        const af_work wk = A.work[t];
         if (fits(wk)) {
             const T *Sin = S0 + buf * wbuf;
             if (wk.flags & 1) {
