@@ -673,6 +673,11 @@ def main():
     r64 = run_ours("f64", max(3, args.steps // 4), warm, rank, world, dist)
     hbm, src = measured_peaks()
     cells = r32["cells"]
+    # DRAM bytes (read + write) of one launch of the 32 x 8 FP32 tiling on this
+    # workload, from an ncu capture of the current kernel; other tilings were
+    # not captured
+    t = r32["tiling"]
+    traffic = 2.153e9 if (tuple(t["tile"]) == (32, 8) and t["threads"] == 128) else None
     value = world * cells / (r32["ms"] * 1e-3)
     achieved = cells * BYTES_PER_CELL["f32"] / (r32["ms"] * 1e-3) / 1e9
     line = None
@@ -697,7 +702,7 @@ def main():
                      "achieved_gbs": cells * BYTES_PER_CELL["f64"] / (r64["ms"] * 1e-3) / 1e9,
                      "clocks": r64["clocks"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": traffic,
                          "kernel": "step_kernel<float, acoustics>",
                          "peak_source": f"{src} HBM copy bandwidth",
                          "algorithmic_bytes_per_launch": cells * BYTES_PER_CELL["f32"]},

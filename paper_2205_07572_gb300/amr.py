@@ -137,7 +137,8 @@ class AMRRun:
     """Adaptive run: subcycled steps (Section 3.2), reflux, ghost exchange, regrid."""
 
     def __init__(self, cfg: af.Config, B: int, lmax: int, leaves, state, lo, hi, dt0: float, device="cuda",
-                 mode: str = "batched", graphs: bool = False, tiling=None, planned_fill: bool = True):
+                 mode: str = "batched", graphs: bool = False, tiling=None, planned_fill: bool = True,
+                 ext_tiling=None):
         import torch
         if mode not in MODES:
             raise ValueError(f"mode must be one of {MODES}")
@@ -149,6 +150,9 @@ class AMRRun:
         self.dy0 = (hi[1] - lo[1]) / (B * cfg.n)
         self.dt0 = dt0
         self.tiling = af.default_tiling(cfg) if tiling is None else int(tiling)
+        # batched mode: leaves with a non-same-level neighbour advance their
+        # first ghost layer too ((n+2)^2 cells); they may use their own tiling
+        self.ext_tiling = None if (ext_tiling is None or mode != "batched") else int(ext_tiling)
         self.dtype = torch.float64 if cfg.prec == af.F64 else torch.float32
         self.words = af.patch_words(cfg.n, cfg.ncomp)
         self.forest = Forest(B, lmax, leaves, device)
@@ -188,13 +192,25 @@ class AMRRun:
 
     def set_tiling(self, tiling: int):
         """Rebuild the work list for another compiled tiling (drops captured graphs)."""
+        import torch
         self.tiling = int(tiling)
         F = self.forest
-        w = af.build_step_work(self.cfg, np.arange(F.nleaf), F.level, F.nbr, tiling=self.tiling)
-        nwork = len(w) // 64
-        wi = w.view(np.int32).reshape(nwork, 16) if nwork else np.zeros((0, 16), np.int32)
-        self.work_all = __import__("torch").from_numpy(w).to(self.device)
-        self.work_start = [int(np.searchsorted(wi[:, 1], l, side="left")) for l in range(self.lmax + 2)]
+        ext = (F.nbr < 0).any(axis=1) if F.nleaf else np.zeros(0, bool)
+        if self.ext_tiling is None:
+            groups = [(np.arange(F.nleaf), self.tiling)]
+        else:
+            groups = [(np.nonzero(~ext)[0], self.tiling), (np.nonzero(ext)[0], self.ext_tiling)]
+        # one work list per group, each in leaf order (levels contiguous)
+        self.work_groups = []
+        for idx, til in groups:
+            w = af.build_step_work(self.cfg, idx, F.level[idx], F.nbr[idx], tiling=til)
+            nw = len(w) // 64
+            wl = w.view(np.int32).reshape(nw, 16)[:, 1] if nw else np.zeros(0, np.int32)
+            starts = [int(np.searchsorted(wl, l, side="left")) for l in range(self.lmax + 2)]
+            self.work_groups.append((torch.from_numpy(w).to(self.device), nw, starts, til))
+        self.work_all, nwork, self.work_start, _ = self.work_groups[0]
+        wi = (self.work_all.cpu().numpy().view(np.int32).reshape(nwork, 16) if nwork
+              else np.zeros((0, 16), np.int32))
         self.nwork = nwork
         if self.mode == "per_patch":
             p = np.arange(F.nleaf)
@@ -221,11 +237,12 @@ class AMRRun:
     def advance_from(self, lstar: int, stream=None):
         """One step of dt_l on every leaf of every level l >= lstar (the
         levels due at one time of the subcycled schedule)."""
-        s, e = self.work_start[lstar], self.nwork
         if self.mode == "batched":
-            if e > s:
-                af.patch_step_pair(self.cfg, self.tiling, self._work_ptr(s), e - s, self.pair, self.dt0, self.dx0,
-                                   self.dy0, self.freg, stream)
+            for work, nw, starts, til in self.work_groups:
+                s = starts[lstar]
+                if nw > s:
+                    af.patch_step_pair(self.cfg, til, work.data_ptr() + 64 * s, nw - s, self.pair, self.dt0,
+                                       self.dx0, self.dy0, self.freg, stream)
             self.parity ^= self.all_levels & ~((1 << lstar) - 1)
             return
         for l in range(self.lmax, lstar - 1, -1):
@@ -315,7 +332,7 @@ class AMRRun:
         for s in range(1 << (lmx - lmin)):
             due = [l for l in levels if s % (1 << (lmx - l)) == 0]
             if self.mode == "batched":
-                n += 1
+                n += sum(1 for _, nw, starts, _ in self.work_groups if nw > starts[min(due)])
             elif self.mode == "per_level":
                 n += len(due)
             else:
