@@ -28,6 +28,16 @@ class Cfg(C.Structure):
                 ("a", C.c_double), ("b", C.c_double), ("c", C.c_double)]
 
 
+SOLID_BODY, SWIRL = 0, 1   # velocity fields of the variable-velocity advection
+
+
+class VarCfg(C.Structure):
+    """Variable-velocity advection (Sections 4.2, 4.3): field, mesh widths,
+    time step, position of the patch's node line 0, time t^n."""
+    _fields_ = [("n", C.c_int32), ("field", C.c_int32), ("dx", C.c_double), ("dy", C.c_double),
+                ("dt", C.c_double), ("x0", C.c_double), ("y0", C.c_double), ("t", C.c_double)]
+
+
 def build(force: bool = False) -> str:
     """Compile liboracle.so (gcc -O2 -fopenmp).  Returns the library path."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
@@ -76,6 +86,17 @@ def lib():
         L.orc_transfer.restype = None
         L.orc_transfer.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, ip, dp, C.c_int, ip, ip,
                                    ip, dp]
+        vp = C.POINTER(VarCfg)
+        L.orc_var_velocity.restype = None
+        L.orc_var_velocity.argtypes = [vp, C.c_double, C.c_double, C.c_double, dp]
+        L.orc_var_foot.restype = None
+        L.orc_var_foot.argtypes = [vp, C.c_double, C.c_double, C.c_double, dp]
+        L.orc_node_evolve_var.restype = C.c_double
+        L.orc_node_evolve_var.argtypes = [vp, dp, C.c_int, C.c_int, C.c_int, C.c_double]
+        L.orc_step_patch_var.restype = None
+        L.orc_step_patch_var.argtypes = [vp, dp, dp, dp]
+        L.orc_run_uniform_var.restype = None
+        L.orc_run_uniform_var.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, dp, dp, C.c_int]
         _lib = L
     return _lib
 
@@ -124,3 +145,38 @@ def run_uniform(cf: Cfg, px: int, py: int, nsteps: int, state: np.ndarray, nthre
 
 def max_threads() -> int:
     return int(lib().orc_max_threads())
+
+
+# ------------------------------------------------ variable-velocity advection
+def var_velocity(vc: VarCfg, x: float, y: float, t: float) -> np.ndarray:
+    out = np.zeros(2)
+    lib().orc_var_velocity(C.byref(vc), x, y, t, _dp(out))
+    return out
+
+
+def var_foot(vc: VarCfg, x: float, y: float, tau: float) -> np.ndarray:
+    out = np.zeros(2)
+    lib().orc_var_foot(C.byref(vc), x, y, tau, _dp(out))
+    return out
+
+
+def node_evolve_var(vc: VarCfg, patch, node_type: int, i: int, j: int, tau: float) -> float:
+    patch = np.ascontiguousarray(patch, dtype=np.float64)
+    return float(lib().orc_node_evolve_var(C.byref(vc), _dp(patch), node_type, i, j, tau))
+
+
+def step_patch_var(vc: VarCfg, patch, freg=None) -> np.ndarray:
+    patch = np.ascontiguousarray(patch, dtype=np.float64)
+    out = np.empty_like(patch)
+    lib().orc_step_patch_var(C.byref(vc), _dp(patch), _dp(out), None if freg is None else _dp(freg))
+    return out
+
+
+def run_uniform_var(vc: VarCfg, px: int, py: int, lo, nsteps: int, state: np.ndarray, nthreads: int = 0):
+    """Advance a periodic px x py patch array nsteps steps from time vc.t
+    (returns the new array; vc.t is advanced)."""
+    st = np.ascontiguousarray(state, dtype=np.float64).copy()
+    tmp = np.empty_like(st)
+    nt = nthreads if nthreads > 0 else max_threads()
+    lib().orc_run_uniform_var(C.byref(vc), px, py, float(lo[0]), float(lo[1]), nsteps, _dp(st), _dp(tmp), nt)
+    return st

@@ -430,6 +430,229 @@ void orc_step_patch(const orc_cfg *cf, const double *in, double *out, double *fr
     free(Gf);
 }
 
+/* ------------------------------------------- Sections 4.2 and 4.3 (variable
+ * velocity) ------------------------------------------------------------------
+ * q_t + (a q)_x + (b q)_y = 0 with a divergence-free velocity, one component.
+ *   field 0, solid-body rotation (Section 4.2, Eq. solidbodyODE):
+ *     a = -pi y, b = pi x; the characteristics are rotations about the origin
+ *     (Eq. characteristics_advtwo), so the foot of a node traced back by tau
+ *     is the node rotated by -pi tau.  Flux through an x-face: Simpson's rule
+ *     in y and t of a(x_face, y) q(x_face, y, t) -- the velocity at each of
+ *     the three face points, constant in time.
+ *   field 1, swirl (Section 4.3): stream function
+ *     Psi = sin^2(pi x) sin^2(pi y) cos(pi t) / pi, velocities by the
+ *     centred differences of Eq. swirlODE over one mesh width; the foot is
+ *     found by one classical Runge-Kutta step of size -tau; flux through an
+ *     x-face by Eq. swirlF: at each time level the velocity at the face
+ *     centre times Simpson's rule of q along the face (likewise Eq. swirlG).
+ * Positions are physical: x0, y0 locate node line 0 of the patch.
+ * Pinned by: exact rotation of quadratic data (solid body), constant states
+ * preserved (Remark of Section 4.2, Theorem of Section 4.3), third-order
+ * convergence, and Table 3 of the paper (swirl).                            */
+void orc_fill_periodic(int n, int ncomp, int px, int py, double *state);
+
+typedef struct {
+    int32_t n;
+    int32_t field; /* 0 solid-body rotation, 1 swirl */
+    double dx, dy, dt;
+    double x0, y0; /* position of node line 0 (lower-left corner of cell 0) */
+    double t;      /* time t^n */
+} orc_var;
+
+static double swirl_psi(double x, double y, double t) {
+    double sx = sin(M_PI * x), sy = sin(M_PI * y);
+    return sx * sx * sy * sy * cos(M_PI * t) / M_PI;
+}
+
+/* Velocity (a, b) at (x, y, t). */
+static void var_velocity(const orc_var *v, double x, double y, double t, double *a, double *b) {
+    if (v->field == 0) {
+        *a = -M_PI * y;
+        *b = M_PI * x;
+        return;
+    }
+    *a = -(swirl_psi(x, y + 0.5 * v->dy, t) - swirl_psi(x, y - 0.5 * v->dy, t)) / v->dy;
+    *b = (swirl_psi(x + 0.5 * v->dx, y, t) - swirl_psi(x - 0.5 * v->dx, y, t)) / v->dx;
+}
+
+/* Foot at time t^n of the characteristic through (x, y) at t^n + tau. */
+static void var_foot(const orc_var *v, double x, double y, double tau, double *xf, double *yf) {
+    if (v->field == 0) {
+        double c = cos(M_PI * tau), s = sin(M_PI * tau);
+        *xf = x * c + y * s;
+        *yf = -x * s + y * c;
+        return;
+    }
+    double h = -tau, t1 = v->t + tau;
+    double k1a, k1b, k2a, k2b, k3a, k3b, k4a, k4b;
+    var_velocity(v, x, y, t1, &k1a, &k1b);
+    var_velocity(v, x + 0.5 * h * k1a, y + 0.5 * h * k1b, t1 + 0.5 * h, &k2a, &k2b);
+    var_velocity(v, x + 0.5 * h * k2a, y + 0.5 * h * k2b, t1 + 0.5 * h, &k3a, &k3b);
+    var_velocity(v, x + h * k3a, y + h * k3b, t1 + h, &k4a, &k4b);
+    *xf = x + h / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
+    *yf = y + h / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
+}
+
+/* Value of q^n at (xf, yf): the reconstruction of the cell holding it. */
+static double var_eval(const lay_t *L, const double *patch, const orc_var *v, double xf, double yf) {
+    double fx = (xf - v->x0) / v->dx, fy = (yf - v->y0) / v->dy;
+    double kx = floor(fx), ky = floor(fy);
+    int ci = (int)kx, cj = (int)ky;
+    if (ci < -NG) ci = -NG;
+    if (ci > L->n + NG - 1) ci = L->n + NG - 1;
+    if (cj < -NG) cj = -NG;
+    if (cj > L->n + NG - 1) cj = L->n + NG - 1;
+    double xi = 2.0 * (fx - ci) - 1.0, eta = 2.0 * (fy - cj) - 1.0;
+    double q[3][3];
+    cell_nodal(L, patch, 0, ci, cj, q);
+    return recon_deriv(q, xi, eta, 0, 0);
+}
+
+/* Position of node (type, i, j). */
+static void var_node_xy(const orc_var *v, int type, int i, int j, double *x, double *y) {
+    *x = v->x0 + ((double)i + (type == ND_YMID ? 0.5 : 0.0)) * v->dx;
+    *y = v->y0 + ((double)j + (type == ND_XMID ? 0.5 : 0.0)) * v->dy;
+}
+
+/* Exported for the pins: the velocity and the characteristic foot. */
+void orc_var_velocity(const orc_var *v, double x, double y, double t, double *ab) {
+    var_velocity(v, x, y, t, &ab[0], &ab[1]);
+}
+void orc_var_foot(const orc_var *v, double x, double y, double tau, double *xy) {
+    var_foot(v, x, y, tau, &xy[0], &xy[1]);
+}
+
+/* Exported for the pins: node (type, i, j) of one patch evolved by tau. */
+double orc_node_evolve_var(const orc_var *v, const double *patch, int type, int i, int j, double tau) {
+    lay_t L = lay_make(v->n, 1);
+    double x, y, xf, yf;
+    var_node_xy(v, type, i, j, &x, &y);
+    var_foot(v, x, y, tau, &xf, &yf);
+    return var_eval(&L, patch, v, xf, yf);
+}
+
+/* One step of one patch, as orc_step_patch (same entries advanced, same flux
+ * registers) with the fluxes described above. */
+void orc_step_patch_var(const orc_var *v, const double *in, double *out, double *freg) {
+    lay_t L = lay_make(v->n, 1);
+    const int n = v->n, nl = n + 3;
+    memcpy(out, in, sizeof(double) * lay_patch_words(&L));
+    size_t per = (size_t)nl * nl;
+    double *qn = (double *)calloc((size_t)3 * 3 * per, sizeof(double));
+#define QV(t, ty, i, j) qn[(((size_t)(t) * 3 + (ty)) * per) + (size_t)((j) + 1) * nl + ((i) + 1)]
+    static const int plane_of[3] = {PL_CORNER, PL_XMID, PL_YMID};
+    for (int ty = 0; ty < 3; ++ty) {
+        int imax = (ty == ND_YMID) ? n + 1 : n + 2;
+        int jmax = (ty == ND_XMID) ? n + 1 : n + 2;
+        for (int j = -1; j < jmax; ++j)
+            for (int i = -1; i < imax; ++i) {
+                double x, y, xf, yf;
+                var_node_xy(v, ty, i, j, &x, &y);
+                QV(0, ty, i, j) = PLc(&L, in, 0, plane_of[ty])[IX(&L, i, j)];
+                var_foot(v, x, y, 0.5 * v->dt, &xf, &yf);
+                QV(1, ty, i, j) = var_eval(&L, in, v, xf, yf);
+                var_foot(v, x, y, v->dt, &xf, &yf);
+                QV(2, ty, i, j) = var_eval(&L, in, v, xf, yf);
+            }
+    }
+    const double wt[3] = {1.0, 4.0, 1.0};
+    const double tk[3] = {v->t, v->t + 0.5 * v->dt, v->t + v->dt};
+    double *F = (double *)calloc(per, sizeof(double));
+    double *G = (double *)calloc(per, sizeof(double));
+    for (int j = -1; j < n + 1; ++j)
+        for (int i = -1; i < n + 2; ++i) {
+            double xs = v->x0 + i * v->dx;
+            double ys[3] = {v->y0 + j * v->dy, v->y0 + (j + 0.5) * v->dy, v->y0 + (j + 1) * v->dy};
+            double acc = 0.0;
+            for (int t = 0; t < 3; ++t) {
+                double q[3] = {QV(t, ND_CORNER, i, j), QV(t, ND_XMID, i, j), QV(t, ND_CORNER, i, j + 1)};
+                if (v->field == 0) {
+                    for (int s = 0; s < 3; ++s) {
+                        double a, b;
+                        var_velocity(v, xs, ys[s], tk[t], &a, &b);
+                        acc += wt[t] * wt[s] * a * q[s];
+                    }
+                } else {
+                    double a, b;
+                    var_velocity(v, xs, ys[1], tk[t], &a, &b);
+                    acc += wt[t] * a * (q[0] + 4.0 * q[1] + q[2]);
+                }
+            }
+            F[(size_t)(j + 1) * nl + (i + 1)] = acc / 36.0;
+        }
+    for (int j = -1; j < n + 2; ++j)
+        for (int i = -1; i < n + 1; ++i) {
+            double ys = v->y0 + j * v->dy;
+            double xs[3] = {v->x0 + i * v->dx, v->x0 + (i + 0.5) * v->dx, v->x0 + (i + 1) * v->dx};
+            double acc = 0.0;
+            for (int t = 0; t < 3; ++t) {
+                double q[3] = {QV(t, ND_CORNER, i, j), QV(t, ND_YMID, i, j), QV(t, ND_CORNER, i + 1, j)};
+                if (v->field == 0) {
+                    for (int s = 0; s < 3; ++s) {
+                        double a, b;
+                        var_velocity(v, xs[s], ys, tk[t], &a, &b);
+                        acc += wt[t] * wt[s] * b * q[s];
+                    }
+                } else {
+                    double a, b;
+                    var_velocity(v, xs[1], ys, tk[t], &a, &b);
+                    acc += wt[t] * b * (q[0] + 4.0 * q[1] + q[2]);
+                }
+            }
+            G[(size_t)(j + 1) * nl + (i + 1)] = acc / 36.0;
+        }
+#define FV(i, j) F[(size_t)((j) + 1) * nl + ((i) + 1)]
+#define GV(i, j) G[(size_t)((j) + 1) * nl + ((i) + 1)]
+    const double *ain = PLc(&L, in, 0, PL_AVG);
+    double *aout = PL(&L, out, 0, PL_AVG);
+    for (int j = -1; j < n + 1; ++j)
+        for (int i = -1; i < n + 1; ++i)
+            aout[IX(&L, i, j)] = ain[IX(&L, i, j)] - v->dt / v->dx * (FV(i + 1, j) - FV(i, j)) -
+                                 v->dt / v->dy * (GV(i, j + 1) - GV(i, j));
+    for (int ty = 0; ty < 3; ++ty) {
+        int imax = (ty == ND_YMID) ? n + 1 : n + 2;
+        int jmax = (ty == ND_XMID) ? n + 1 : n + 2;
+        double *pl = PL(&L, out, 0, plane_of[ty]);
+        for (int j = -1; j < jmax; ++j)
+            for (int i = -1; i < imax; ++i) pl[IX(&L, i, j)] = QV(2, ty, i, j);
+    }
+    if (freg)
+        for (int k = 0; k < n; ++k) {
+            freg[0 * n + k] += v->dt * FV(0, k);
+            freg[1 * n + k] += v->dt * FV(n, k);
+            freg[2 * n + k] += v->dt * GV(k, 0);
+            freg[3 * n + k] += v->dt * GV(k, n);
+        }
+#undef QV
+#undef FV
+#undef GV
+    free(qn);
+    free(F);
+    free(G);
+}
+
+/* Uniform periodic run with variable velocity: px x py patches tiling the box
+ * with lower-left corner (lo_x, lo_y); v->t is the start time and advances. */
+void orc_run_uniform_var(orc_var *v, int px, int py, double lo_x, double lo_y, int nsteps, double *state,
+                         double *tmp, int nthreads) {
+    lay_t L = lay_make(v->n, 1);
+    long pw = lay_patch_words(&L);
+    int np = px * py;
+    (void)nthreads;
+    for (int s = 0; s < nsteps; ++s) {
+        orc_fill_periodic(v->n, 1, px, py, state);
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1)
+        for (int p = 0; p < np; ++p) {
+            orc_var vp = *v;
+            vp.x0 = lo_x + (p % px) * v->n * v->dx;
+            vp.y0 = lo_y + (p / px) * v->n * v->dy;
+            orc_step_patch_var(&vp, state + p * pw, tmp + p * pw, NULL);
+        }
+        memcpy(state, tmp, sizeof(double) * pw * np);
+        v->t += v->dt;
+    }
+}
+
 /* --------------------------------------------------------- Section 3.1 (3.)
  * Same-level ghost fill on a px x py array of patches tiling a periodic box:
  * every ghost entry (lattice entries outside [g, g+N)^2 of every plane) is a

@@ -148,6 +148,11 @@ def ring_wave_at(r0: float, width: float = 0.001, k: float = 80.0):
     return f
 
 
+def swirl_gaussians(x, y):
+    """Two Gaussians exp(-100 |x - c|^2) at (0.5, 0.25) and (0.5, 0.75) (Section 4.3)."""
+    return np.exp(-100.0 * ((x - 0.5) ** 2 + (y - 0.25) ** 2)) + np.exp(-100.0 * ((x - 0.5) ** 2 + (y - 0.75) ** 2))
+
+
 def wave_packet(x, y):
     """exp(-r^2/0.01) cos(60 pi x), centred at (0.5, 0.5)."""
     r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2
