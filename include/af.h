@@ -74,7 +74,9 @@ typedef struct {
     int16_t x0, x1;     /* cells [x0, x1) of the patch, in [-1, N+1] */
     int16_t y0, y1;
     int32_t flags;      /* bit 0: the patch advances its first ghost layer too */
-    int32_t pad_[3];
+    int32_t ix, iy;     /* column and row of the patch among the patches of its level
+                           (af_build_step_work_at; used only by af_patch_step_var) */
+    int32_t pad_;
 } af_work;
 
 /* Human-readable name of a status code (static storage). */
@@ -132,6 +134,15 @@ int32_t af_step_default_tiling(const af_config *cfg);
 af_status af_build_step_work_tiled(const af_config *cfg, int32_t tiling, int32_t npatch, const int32_t *h_patch,
                                    const int32_t *h_level, const int32_t *h_nbr, af_work *h_work,
                                    int32_t capacity, int32_t *nwork);
+
+/* af_build_step_work_tiled that also records each patch's position:
+ * h_ix[k], h_iy[k] = column and row of patch k among the patches of its
+ * level (so its lower-left corner is at (x_lo + ix n dx_l, y_lo + iy n dy_l));
+ * needed by af_patch_step_var, ignored by the constant-velocity steps.
+ * NULL means 0. */
+af_status af_build_step_work_at(const af_config *cfg, int32_t tiling, int32_t npatch, const int32_t *h_patch,
+                                const int32_t *h_level, const int32_t *h_ix, const int32_t *h_iy,
+                                const int32_t *h_nbr, af_work *h_work, int32_t capacity, int32_t *nwork);
 
 /* One Active Flux time step (Section 2) for every work item:
  *   1. point values at t^{n+1/2}, t^{n+1} at corners and edge midpoints from
@@ -195,6 +206,41 @@ af_status af_patch_step_pair(const af_config *cfg, int32_t tiling, int32_t nwork
                              const af_state_pair *state, double dt0, double dx0, double dy0,
                              double *d_flux_reg, void *stream);
 
+
+/* Variable-velocity advection q_t + (a q)_x + (b q)_y = 0 (one component),
+ * with the velocity fields of Sections 4.2 and 4.3:
+ *   AF_FIELD_SOLID_BODY  a = -pi y, b = pi x (Eq. solidbodyODE); point values
+ *       by back-tracing along the exact rotation (Eq. characteristics_advtwo);
+ *       flux through a face by Simpson's rule in space and time of a q with
+ *       the velocity at each face point;
+ *   AF_FIELD_SWIRL  stream function Psi = sin^2(pi x) sin^2(pi y) cos(pi t)/pi,
+ *       velocities by its centred differences over one mesh width of the
+ *       patch's level (Eq. swirlODE), evaluated through
+ *       sin^2 A - sin^2 B = sin(A+B) sin(A-B) (the same numbers, without
+ *       cancellation); feet by one classical Runge-Kutta step of size -tau;
+ *       fluxes of Eqs. swirlF, swirlG (velocity at the face centre times
+ *       Simpson's rule along the face, at t^n, t^{n+1/2}, t^{n+1}); these
+ *       fluxes keep constant states constant (Theorem of Section 4.3). */
+#define AF_FIELD_SOLID_BODY 0
+#define AF_FIELD_SWIRL 1
+typedef struct {
+    int32_t field;
+    int32_t pad_;
+    double x_lo, y_lo; /* lower-left corner of the domain: node line 0 of patch (0, 0) */
+    double x_hi, y_hi; /* upper-right corner (bounds the speed for the CFL check) */
+    double t;          /* time t^n at the start of the step */
+} af_velocity;
+
+/* One Active Flux step of variable-velocity advection on a state pair (see
+ * af_state_pair), as af_patch_step_pair otherwise: cfg->eq = AF_ADVECTION,
+ * ncomp 1 (cfg->a, cfg->b unused); d_work from af_build_step_work_at (patch
+ * positions).  Level l uses dx0 / 2^l, dy0 / 2^l, dt0 / 2^l; every work item
+ * starts at vel->t.  AF_ERR_CFL unless the largest speed on the domain and
+ * its two ghost layers times dt_l stays within one mesh width (the foot must
+ * lie in a cell next to its node).  Flux registers receive dt_l * F. */
+af_status af_patch_step_var(const af_config *cfg, int32_t tiling, int32_t nwork, const af_work *d_work,
+                            const af_state_pair *state, const af_velocity *vel, double dt0, double dx0, double dy0,
+                            double *d_flux_reg, void *stream);
 
 /* ======================================================================
  * Adaptive mesh refinement (Section 3): a forest of quadtrees over a B x B

@@ -20,7 +20,7 @@ import ctypes as C
 
 import numpy as np
 
-from . import ADVECTION, _dp, cfg, lib
+from . import ADVECTION, VarCfg, _dp, cfg, lib
 
 
 def _ip(a):
@@ -29,7 +29,10 @@ def _ip(a):
 
 class OracleForest:
     def __init__(self, eq: int, n: int, B: int, lmax: int, leaves, lo, hi, dt0: float, a=0.0, b=0.0, c=1.0,
-                 state=None):
+                 state=None, field=None, t0: float = 0.0):
+        """field: None (constant velocity a, b, or acoustics) or a velocity
+        field of orc_step_patch_var (variable-velocity advection)."""
+        self.field, self.time = field, float(t0)
         self.eq, self.n, self.B, self.lmax = eq, n, B, lmax
         self.ncomp = 1 if eq == ADVECTION else 3
         self.lo, self.hi = lo, hi
@@ -63,14 +66,20 @@ class OracleForest:
                            _dp(self.state), _dp(out))
         self.state = out
 
-    def advance(self, l: int):
-        """One step of dt_l on every leaf of level l (same-level copy first)."""
+    def advance(self, l: int, t: float = 0.0):
+        """One step of dt_l from time t on every leaf of level l (same-level
+        copy first)."""
         self.fill(1 << l, 1 << l, True)
         cf = self.cfg_level(l)
         for p in np.nonzero(self.level == l)[0]:
             fr = self.freg[p]
             out = np.empty_like(self.state[p])
-            lib().orc_step_patch(C.byref(cf), _dp(self.state[p]), _dp(out), _dp(fr))
+            if self.field is None:
+                lib().orc_step_patch(C.byref(cf), _dp(self.state[p]), _dp(out), _dp(fr))
+            else:
+                vc = VarCfg(self.n, self.field, cf.dx, cf.dy, cf.dt, self.lo[0] + self.ix[p] * self.n * cf.dx,
+                            self.lo[1] + self.iy[p] * self.n * cf.dy, t)
+                lib().orc_step_patch_var(C.byref(vc), _dp(self.state[p]), _dp(out), _dp(fr))
             self.state[p] = out
 
     def reflux(self, sync_mask: int):
@@ -86,10 +95,11 @@ class OracleForest:
         levels = self.levels
         lmin, lmx = levels[0], levels[-1]
         S = 1 << (lmx - lmin)
+        t0, dtf = self.time, self.dt0 / (1 << lmx)
         for s in range(S):
             for l in range(lmx, lmin - 1, -1):
                 if l in levels and s % (1 << (lmx - l)) == 0:
-                    self.advance(l)
+                    self.advance(l, t0 + s * dtf)
             t = s + 1
             sync = 0
             for l in range(lmin, lmx + 1):
@@ -98,6 +108,7 @@ class OracleForest:
             if bin(sync).count("1") > 1:
                 self.reflux(sync)
                 self.sync_fill(sync)
+        self.time = t0 + self.dt0 / (1 << lmin)
 
     # ----------------------------------------------------------------- tags
     def tags(self, comp: int, kind: int, refine_thr: float, coarsen_thr: float):

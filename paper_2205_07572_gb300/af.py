@@ -33,7 +33,7 @@ class Config(C.Structure):
 class Work(C.Structure):
     _fields_ = [("patch", C.c_int32), ("level", C.c_int32), ("nbr", C.c_int32 * 8),
                 ("x0", C.c_int16), ("x1", C.c_int16), ("y0", C.c_int16), ("y1", C.c_int16),
-                ("flags", C.c_int32), ("pad_", C.c_int32 * 3)]
+                ("flags", C.c_int32), ("ix", C.c_int32), ("iy", C.c_int32), ("pad_", C.c_int32)]
 
 
 assert C.sizeof(Work) == 64
@@ -71,6 +71,9 @@ def lib():
         L.af_step_tilings.argtypes = [C.c_void_p, C.c_int32]
         L.af_step_default_tiling.restype = C.c_int32
         L.af_step_default_tiling.argtypes = [C.POINTER(Config)]
+        L.af_build_step_work_at.restype = C.c_int
+        L.af_build_step_work_at.argtypes = [C.POINTER(Config), C.c_int32, C.c_int32, _IP, _IP, _IP, _IP, _IP,
+                                            C.POINTER(Work), C.c_int32, _IP]
         _register_more(L)
         _lib = L
     return _lib
@@ -146,22 +149,26 @@ def default_tiling(cfg: Config) -> int:
     return int(lib().af_step_default_tiling(C.byref(cfg)))
 
 
-def build_step_work(cfg: Config, patches, levels=None, nbr=None, tiling=None) -> np.ndarray:
-    """Host work list of af_patch_step as a uint8 array (64 bytes per entry)."""
+def build_step_work(cfg: Config, patches, levels=None, nbr=None, tiling=None, ix=None, iy=None) -> np.ndarray:
+    """Host work list of af_patch_step as a uint8 array (64 bytes per entry);
+    ix, iy (patch positions) are needed by patch_step_var only."""
     patches = np.ascontiguousarray(patches, dtype=np.int32)
     lv = None if levels is None else np.ascontiguousarray(levels, dtype=np.int32)
     nb = None if nbr is None else np.ascontiguousarray(nbr, dtype=np.int32).reshape(-1)
+    px = None if ix is None else np.ascontiguousarray(ix, dtype=np.int32)
+    py = None if iy is None else np.ascontiguousarray(iy, dtype=np.int32)
     npatch = len(patches)
     L = lib()
     k = default_tiling(cfg) if tiling is None else int(tiling)
     cnt = C.c_int32(0)
     ip = lambda a: None if a is None else a.ctypes.data_as(_IP)
-    st = L.af_build_step_work_tiled(C.byref(cfg), k, npatch, ip(patches), ip(lv), ip(nb), None, 0, C.byref(cnt))
+    st = L.af_build_step_work_at(C.byref(cfg), k, npatch, ip(patches), ip(lv), ip(px), ip(py), ip(nb), None, 0,
+                                 C.byref(cnt))
     if st != 0 and cnt.value == 0:
         _check(st, "af_build_step_work")
     buf = (Work * max(cnt.value, 1))()
-    st = L.af_build_step_work_tiled(C.byref(cfg), k, npatch, ip(patches), ip(lv), ip(nb), buf, cnt.value,
-                                    C.byref(cnt))
+    st = L.af_build_step_work_at(C.byref(cfg), k, npatch, ip(patches), ip(lv), ip(px), ip(py), ip(nb), buf,
+                                 cnt.value, C.byref(cnt))
     _check(st, "af_build_step_work")
     return np.frombuffer(buf, dtype=np.uint8, count=64 * cnt.value).copy()
 
@@ -411,3 +418,30 @@ def cnn_adam(nparam: int, params, m, v, grad, step: int, lr: float, beta1=0.9, b
 def cnn_tags(nleaf: int, logit, plain, cmin: float, tags, nfallback, stream=None):
     _check(lib().af_cnn_tags(nleaf, ptr(logit), ptr(plain), cmin, ptr(tags), ptr(nfallback),
                              stream_handle(stream)), "af_cnn_tags")
+
+
+
+# ------------------------------------------------- variable-velocity advection
+FIELD_SOLID_BODY, FIELD_SWIRL = 0, 1
+
+
+class Velocity(C.Structure):
+    _fields_ = [("field", C.c_int32), ("pad_", C.c_int32), ("x_lo", C.c_double), ("y_lo", C.c_double),
+                ("x_hi", C.c_double), ("y_hi", C.c_double), ("t", C.c_double)]
+
+
+_EXTRA += [("af_patch_step_var", C.c_int, [C.POINTER(Config), C.c_int32, C.c_int32, _VP, _SP, C.POINTER(Velocity),
+                                           C.c_double, C.c_double, C.c_double, _VP, _VP])]
+if _lib is not None:
+    _register_more(_lib)
+
+
+def velocity(field: int, lo, hi, t: float) -> Velocity:
+    return Velocity(field, 0, float(lo[0]), float(lo[1]), float(hi[0]), float(hi[1]), float(t))
+
+
+def patch_step_var(cfg: Config, tiling: int, work, nwork: int, pair: StatePair, vel: Velocity, dt0: float,
+                   dx0: float, dy0: float, flux_reg=None, stream=None) -> None:
+    _check(lib().af_patch_step_var(C.byref(cfg), int(tiling), int(nwork), ptr(work), C.byref(pair), C.byref(vel),
+                                   float(dt0), float(dx0), float(dy0), ptr(flux_reg), stream_handle(stream)),
+           "af_patch_step_var")

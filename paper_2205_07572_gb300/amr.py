@@ -138,12 +138,17 @@ class AMRRun:
 
     def __init__(self, cfg: af.Config, B: int, lmax: int, leaves, state, lo, hi, dt0: float, device="cuda",
                  mode: str = "batched", graphs: bool = False, tiling=None, planned_fill: bool = True,
-                 ext_tiling=None):
+                 ext_tiling=None, field=None):
         import torch
         if mode not in MODES:
             raise ValueError(f"mode must be one of {MODES}")
         self.cfg, self.B, self.lmax, self.device = cfg, B, lmax, device
-        self.mode, self.use_graphs = mode, bool(graphs) and mode == "batched"
+        # field: None, or a velocity field of af_patch_step_var (variable-
+        # velocity advection); the swirl depends on time, which a captured
+        # graph would freeze, so it runs without graphs
+        self.field = field
+        self.mode = mode
+        self.use_graphs = bool(graphs) and mode == "batched" and field != af.FIELD_SWIRL
         self.planned_fill = planned_fill
         self.lo, self.hi = lo, hi
         self.dx0 = (hi[0] - lo[0]) / (B * cfg.n)
@@ -203,7 +208,7 @@ class AMRRun:
         # one work list per group, each in leaf order (levels contiguous)
         self.work_groups = []
         for idx, til in groups:
-            w = af.build_step_work(self.cfg, idx, F.level[idx], F.nbr[idx], tiling=til)
+            w = af.build_step_work(self.cfg, idx, F.level[idx], F.nbr[idx], tiling=til, ix=F.ix[idx], iy=F.iy[idx])
             nw = len(w) // 64
             wl = w.view(np.int32).reshape(nw, 16)[:, 1] if nw else np.zeros(0, np.int32)
             starts = [int(np.searchsorted(wl, l, side="left")) for l in range(self.lmax + 2)]
@@ -234,15 +239,20 @@ class AMRRun:
         return self.work_all.data_ptr() + 64 * start
 
     # -------------------------------------------------------------- steps
-    def advance_from(self, lstar: int, stream=None):
-        """One step of dt_l on every leaf of every level l >= lstar (the
-        levels due at one time of the subcycled schedule)."""
+    def advance_from(self, lstar: int, stream=None, t: float = 0.0):
+        """One step of dt_l from time t on every leaf of every level l >= lstar
+        (the levels due at one time of the subcycled schedule)."""
         if self.mode == "batched":
             for work, nw, starts, til in self.work_groups:
                 s = starts[lstar]
                 if nw > s:
-                    af.patch_step_pair(self.cfg, til, work.data_ptr() + 64 * s, nw - s, self.pair, self.dt0,
-                                       self.dx0, self.dy0, self.freg, stream)
+                    if self.field is None:
+                        af.patch_step_pair(self.cfg, til, work.data_ptr() + 64 * s, nw - s, self.pair, self.dt0,
+                                           self.dx0, self.dy0, self.freg, stream)
+                    else:
+                        af.patch_step_var(self.cfg, til, work.data_ptr() + 64 * s, nw - s, self.pair,
+                                          af.velocity(self.field, self.lo, self.hi, t), self.dt0, self.dx0,
+                                          self.dy0, self.freg, stream)
             self.parity ^= self.all_levels & ~((1 << lstar) - 1)
             return
         for l in range(self.lmax, lstar - 1, -1):
@@ -251,6 +261,7 @@ class AMRRun:
     def advance(self, l: int, stream=None):
         """One step of dt_l on every leaf of level l (per_level / per_patch)."""
         assert self.mode != "batched"
+        assert self.field is None, "variable-velocity runs use the batched mode"
         s, e = self.work_start[l], self.work_start[l + 1]
         if e == s:
             return
@@ -270,9 +281,10 @@ class AMRRun:
         synchronised: conservative fix, then ghost exchange among them."""
         levels = self.forest.levels
         lmin, lmx = levels[0], levels[-1]
+        t0, dtf = self.time, self.dt0 / (1 << lmx)
         for s in range(1 << (lmx - lmin)):
             due = [l for l in levels if s % (1 << (lmx - l)) == 0]
-            self.advance_from(min(due), stream)
+            self.advance_from(min(due), stream, t0 + s * dtf)
             sync = 0
             for l in range(lmin, lmx + 1):
                 if (s + 1) % (1 << (lmx - l)) == 0:
@@ -290,9 +302,10 @@ class AMRRun:
 
     def coarse_step(self):
         """Advance all levels by the step of the coarsest level present."""
-        self.time += self.coarse_dt()
+        dtc = self.coarse_dt()
         if not self.use_graphs:
             self._schedule()
+            self.time += dtc
             return
         import torch
         key = self.parity
@@ -304,6 +317,7 @@ class AMRRun:
             if key not in self.graphs:
                 self.graphs[key] = None
                 self._schedule()
+                self.time += dtc
                 return
             g = torch.cuda.CUDAGraph()
             side = torch.cuda.Stream()
@@ -317,6 +331,7 @@ class AMRRun:
         g, p1 = self.graphs[key]
         g.replay()
         self.parity = p1
+        self.time += dtc
 
     def cell_updates_per_coarse_step(self) -> int:
         levels = self.forest.levels

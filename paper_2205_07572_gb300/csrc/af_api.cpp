@@ -23,9 +23,10 @@ extern "C" int64_t af_patch_words(int32_t n, int32_t ncomp) {
     return n < 1 || ncomp < 1 ? 0 : (int64_t)ncomp * af::kPlanes * af::plane_stride(n);
 }
 
-extern "C" af_status af_build_step_work_tiled(const af_config *cfg, int32_t tiling_index, int32_t npatch,
-                                              const int32_t *h_patch, const int32_t *h_level, const int32_t *h_nbr,
-                                              af_work *h_work, int32_t capacity, int32_t *nwork) {
+extern "C" af_status af_build_step_work_at(const af_config *cfg, int32_t tiling_index, int32_t npatch,
+                                           const int32_t *h_patch, const int32_t *h_level, const int32_t *h_ix,
+                                           const int32_t *h_iy, const int32_t *h_nbr, af_work *h_work,
+                                           int32_t capacity, int32_t *nwork) {
     using namespace af;
     if (cfg == nullptr || nwork == nullptr || npatch < 0 || capacity < 0) return AF_ERR_ARG;
     if (cfg->n < 2 || cfg->n > 64) return AF_ERR_ARG;
@@ -65,9 +66,18 @@ extern "C" af_status af_build_step_work_tiled(const af_config *cfg, int32_t tili
                 o.y0 = (int16_t)(lo + (w * ty) / nty);
                 o.y1 = (int16_t)(lo + (w * (ty + 1)) / nty);
                 o.flags = ext ? 1 : 0;
+                o.ix = h_ix ? h_ix[k] : 0;
+                o.iy = h_iy ? h_iy[k] : 0;
             }
     }
     return AF_OK;
+}
+
+extern "C" af_status af_build_step_work_tiled(const af_config *cfg, int32_t tiling_index, int32_t npatch,
+                                              const int32_t *h_patch, const int32_t *h_level, const int32_t *h_nbr,
+                                              af_work *h_work, int32_t capacity, int32_t *nwork) {
+    return af_build_step_work_at(cfg, tiling_index, npatch, h_patch, h_level, nullptr, nullptr, h_nbr, h_work,
+                                 capacity, nwork);
 }
 
 extern "C" af_status af_build_step_work(const af_config *cfg, int32_t npatch, const int32_t *h_patch,

@@ -27,9 +27,13 @@ class UniformRun:
     """px x py patches of n x n cells, periodic, advanced by af_patch_step."""
 
     def __init__(self, cfg: af.Config, px: int, py: int, dx: float, dy: float, dt: float, device="cuda",
-                 state=None, flux_reg: bool = False, tiling=None):
+                 state=None, flux_reg: bool = False, tiling=None, field=None, lo=(0.0, 0.0), t0: float = 0.0):
+        """field: None (constant velocity cfg.a, cfg.b or acoustics) or
+        af.FIELD_SOLID_BODY / af.FIELD_SWIRL (variable-velocity advection on
+        the box with lower-left corner lo, starting at time t0)."""
         import torch
         self.cfg, self.px, self.py = cfg, px, py
+        self.field, self.lo, self.t = field, (float(lo[0]), float(lo[1])), float(t0)
         self.dx, self.dy, self.dt = dx, dy, dt
         self.npatch = px * py
         self.words = af.patch_words(cfg.n, cfg.ncomp)
@@ -48,13 +52,22 @@ class UniformRun:
         """Rebuild the work list for a compiled tiling (None: the default)."""
         import torch
         self.tiling = af.default_tiling(self.cfg) if tiling is None else int(tiling)
-        w = af.build_step_work(self.cfg, np.arange(self.npatch), nbr=self.nbr, tiling=self.tiling)
+        p = np.arange(self.npatch)
+        w = af.build_step_work(self.cfg, p, nbr=self.nbr, tiling=self.tiling, ix=p % self.px, iy=p // self.px)
         self.nwork = len(w) // 64
         self.work = torch.from_numpy(w).to(self.device)
 
     def step(self, stream=None):
-        af.patch_step(self.cfg, self.work, self.nwork, self.a, self.b, self.dt, self.dx, self.dy,
-                      self.freg, stream, tiling=self.tiling)
+        if self.field is None:
+            af.patch_step(self.cfg, self.work, self.nwork, self.a, self.b, self.dt, self.dx, self.dy,
+                          self.freg, stream, tiling=self.tiling)
+        else:
+            n = self.cfg.n
+            hi = (self.lo[0] + self.px * n * self.dx, self.lo[1] + self.py * n * self.dy)
+            af.patch_step_var(self.cfg, self.tiling, self.work, self.nwork, af.state_pair(self.a, self.b, 0),
+                              af.velocity(self.field, self.lo, hi, self.t), self.dt, self.dx, self.dy, self.freg,
+                              stream)
+        self.t += self.dt
         self.a, self.b = self.b, self.a
 
     @property
