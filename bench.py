@@ -566,6 +566,71 @@ def learned_tagging(B=3, lmin=3, lmax=6, train_radii=(0.2, 0.3), test_radius=0.2
     return out
 
 
+# ------------------------------------------------ variable-velocity advection
+TABLE3 = {4: 5.722927e-06, 5: 7.268088e-07}   # Section 4.3, Table 3 (uniform, t = 1)
+
+
+def var_velocity_bench(steps: int = 20):
+    """Swirl (Section 4.3, constant-preserving flux, RK4 back-tracing), 16x16
+    patches on the periodic unit square: the paper's Table 3 runs (levels 4
+    and 5, two Gaussians, t = 1, CFL 0.5) on the GPU with their L1 errors, and
+    the FP32 / FP64 step rate on 4096^2 cells; solid-body rotation rate too."""
+    import torch
+    import synth as S
+    from paper_2205_07572_gb300 import af
+    from paper_2205_07572_gb300.uniform import UniformRun
+    out = {"workload": "swirl: stream function sin^2 sin^2 cos(pi t)/pi, 16x16 patches, periodic unit square; "
+                       "solid-body rotation on [-1,1]^2"}
+    n = 16
+    tab = {}
+    for level, px in ((4, 16), (5, 32)):
+        grid = S.UniformGrid(S.Layout(n, 1), px, px)
+        st = S.periodic_state(grid, [S.swirl_gaussians], nq=4)
+        nsteps, dt = S.steps_to(1.0, 0.5 * grid.dx)
+        res = {}
+        for prec in ("f64", "f32"):
+            cfg = af.config(af.ADVECTION, af.F32 if prec == "f32" else af.F64, n)
+            run = UniformRun(cfg, px, px, grid.dx, grid.dy, dt, state=st, field=af.FIELD_SWIRL)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(nsteps):
+                run.step()
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            host = run.state.double().cpu().numpy().reshape(st.shape)
+            res[prec] = {"l1": grid.l1_error(host, 0, S.swirl_gaussians, nq=4), "wall_s": round(el, 4)}
+        tab[f"level{level}_{px * n}x{px * n}"] = {**res, "paper": TABLE3[level], "steps": nsteps}
+    out["table3"] = tab
+    rates = {}
+    for field, name, lo, hi, vmax in ((af.FIELD_SWIRL, "swirl", (0.0, 0.0), (1.0, 1.0), 1.0),
+                                      (af.FIELD_SOLID_BODY, "solid_body", (-1.0, -1.0), (1.0, 1.0), np.pi * 1.01)):
+        px = 256
+        grid = S.UniformGrid(S.Layout(n, 1), px, px, lo, hi)
+        f = S.swirl_gaussians if field == af.FIELD_SWIRL else S.gaussian(0.3, 0.2, 0.1)
+        st = S.periodic_state(grid, [f], nq=2, dtype=np.float32)
+        for prec in ("f32", "f64"):
+            cfg = af.config(af.ADVECTION, af.F32 if prec == "f32" else af.F64, n)
+            run = UniformRun(cfg, px, px, grid.dx, grid.dy, 0.45 * grid.dx / vmax, state=st, field=field, lo=lo)
+            for _ in range(3):
+                run.step()
+            torch.cuda.synchronize()
+            stream = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k = steps if prec == "f32" else max(3, steps // 4)
+            e0.record(stream)
+            for _ in range(k):
+                run.step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            cells = px * px * n * n
+            bpc = 8 * (4 if prec == "f32" else 8)
+            rates[f"{name}_{prec}"] = {"value": cells / (ms * 1e-3), "unit": "cell updates/s", "ms_per_step": ms,
+                                       "achieved_gbs": cells * bpc / (ms * 1e-3) / 1e9, "cells": cells}
+    out["rates_4096x4096"] = rates
+    return out
+
+
 # ----------------------------------------------------------- CPU oracle arm
 def oracle_sample(steps: int, budget_s: float = 15.0):
     """Time the FP64 oracle on a bounded sample of the workload: an 8 x 8 block
@@ -605,6 +670,7 @@ def main():
                     help="which stencil precision(s) to time (profiling runs use one)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the end-to-end, literal-size, adaptive-mesh and CPU-baseline measurements")
+    ap.add_argument("--var-only", action="store_true", help="only the variable-velocity advection runs")
     ap.add_argument("--learned-only", action="store_true",
                     help="only the learned-tagging experiment")
     ap.add_argument("--amr-only", action="store_true",
@@ -658,6 +724,10 @@ def main():
             for case in AMR_CASES:
                 print(json.dumps({"amr": case, **amr_bench(case, 8, 4)}), flush=True)
         return
+    if args.var_only:
+        if rank == 0:
+            print(json.dumps({"variable_velocity": var_velocity_bench()}), flush=True)
+        return
     if args.learned_only:
         if rank == 0:
             print(json.dumps({"learned_tagging": learned_tagging()}), flush=True)
@@ -689,6 +759,7 @@ def main():
         cpu = None if (args.no_cpu_baseline or not extras) else oracle_sample(20)
         amr = {case: amr_bench(case, 8, 4) for case in AMR_CASES} if extras else None
         learned = learned_tagging() if extras else None
+        var = var_velocity_bench() if extras else None
         v64 = world * cells / (r64["ms"] * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": "cell updates/s", "n_gpus": world,
@@ -709,6 +780,7 @@ def main():
             "literal_512x512": {"f32": lit32, "f64": lit64, "note": "L2-resident (34 MB FP64 state)"},
             "amr": amr,
             "learned_tagging": learned,
+            "variable_velocity": var,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

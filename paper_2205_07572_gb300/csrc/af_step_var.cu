@@ -25,6 +25,11 @@ struct VarArgs {
     double x_lo, y_lo;  // node line 0 of patch (0, 0)
     double t;           // t^n
     double dx0, dy0;    // level-0 mesh widths
+    // swirl, per level l (host-computed once per call): cos(pi t) at t^n,
+    // t^n + dt_l/4, t^n + dt_l/2, t^n + dt_l, and sin(pi h) / (pi h) for
+    // h = dx_l, dy_l
+    double cl[AF_MAX_LEVEL + 1][4];
+    double kl[AF_MAX_LEVEL + 1][2];
 };
 
 __device__ __forceinline__ float spi(float x) { return sinpif(x); }
@@ -32,14 +37,37 @@ __device__ __forceinline__ double spi(double x) { return sinpi(x); }
 __device__ __forceinline__ float cpi(float x) { return cospif(x); }
 __device__ __forceinline__ double cpi(double x) { return cospi(x); }
 
+__device__ __forceinline__ void scpi(float x, float &s, float &c) { sincospif(x, &s, &c); }
+__device__ __forceinline__ void scpi(double x, double &s, double &c) { sincospi(x, &s, &c); }
+
 // Swirl velocity: the centred differences of Eq. swirlODE written as
-// -sin^2(pi x) sin(2 pi y) cos(pi t) sin(pi dy) / (pi dy) and its mirror.
-// kx = sin(pi dx) / (pi dx), ky likewise; ct = cos(pi t).
+// -sin^2(pi x) sin(2 pi y) cos(pi t) sin(pi dy) / (pi dy) and its mirror,
+// with sin(2 pi y) = 2 sin(pi y) cos(pi y).  kx = sin(pi dx) / (pi dx), ky
+// likewise; ct = cos(pi t).
 template <typename T>
 __device__ __forceinline__ void swirl_v(T x, T y, T ct, T kx, T ky, T &a, T &b) {
-    const T sx = spi(x), sy = spi(y);
-    a = -sx * sx * spi(T(2) * y) * ct * ky;
-    b = sy * sy * spi(T(2) * x) * ct * kx;
+    T sx, cx, sy, cy;
+    scpi(x, sx, cx);
+    scpi(y, sy, cy);
+    a = -sx * sx * (T(2) * sy * cy) * ct * ky;
+    b = sy * sy * (T(2) * sx * cx) * ct * kx;
+}
+
+// Time-independent factor of the swirl velocity at a face centre:
+// a(x, y, t) = ax * cos(pi t) (x-faces), b(x, y, t) = by * cos(pi t) (y-faces).
+template <typename T>
+__device__ __forceinline__ T swirl_ax(T x, T y, T ky) {
+    T sx, cx, sy, cy;
+    scpi(x, sx, cx);
+    scpi(y, sy, cy);
+    return -sx * sx * (T(2) * sy * cy) * ky;
+}
+template <typename T>
+__device__ __forceinline__ T swirl_by(T x, T y, T kx) {
+    T sx, cx, sy, cy;
+    scpi(x, sx, cx);
+    scpi(y, sy, cy);
+    return sy * sy * (T(2) * sx * cx) * kx;
 }
 
 // Per-tile constants of one level.
@@ -122,14 +150,10 @@ __global__ void __launch_bounds__(NT) step_var_kernel(const __grid_constant__ Va
     L.xo = (T)(V.x_lo + (double)wk.ix * n * ldexp(V.dx0, -level));
     L.yo = (T)(V.y_lo + (double)wk.iy * n * ldexp(V.dy0, -level));
     if constexpr (FIELD == AF_FIELD_SWIRL) {
-        const double dtl = ldexp(A.dt0, -level);
-        L.c[0] = (T)cospi(V.t);
-        L.c[1] = (T)cospi(V.t + 0.25 * dtl);
-        L.c[2] = (T)cospi(V.t + 0.5 * dtl);
-        L.c[3] = (T)cospi(V.t + dtl);
-        const double hx = ldexp(V.dx0, -level), hy = ldexp(V.dy0, -level);
-        L.kx = (T)(sinpi(hx) / (M_PI * hx));
-        L.ky = (T)(sinpi(hy) / (M_PI * hy));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) L.c[q] = (T)V.cl[level][q];
+        L.kx = (T)V.kl[level][0];
+        L.ky = (T)V.kl[level][1];
     }
     T *outp = dst_buf(A, level) + (int64_t)wk.patch * kPlanes * A.plane;
     const int sxhi = (x1 == n + 1) ? x1 : x1 - 1;
@@ -183,6 +207,8 @@ __global__ void __launch_bounds__(NT) step_var_kernel(const __grid_constant__ Va
         // x-face on node line i + di (di = 0 left, 1 right); y-face on j + dj
         auto xflux = [&](int di) -> T {
             const T xs = L.xo + (T)(i + di) * L.dx;
+            T ax = T(0);
+            if constexpr (FIELD == AF_FIELD_SWIRL) ax = swirl_ax(xs, L.yo + ((T)j + T(0.5)) * L.dy, L.ky);
             T acc = T(0);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -192,8 +218,7 @@ __global__ void __launch_bounds__(NT) step_var_kernel(const __grid_constant__ Va
                     acc += w[k] * (-T(M_PI)) *
                            (y0s * ql + T(4) * (y0s + T(0.5) * L.dy) * qm + (y0s + L.dy) * qu);
                 } else {
-                    T a, b;
-                    swirl_v(xs, L.yo + ((T)j + T(0.5)) * L.dy, L.c[k == 0 ? 0 : (k == 1 ? 2 : 3)], L.kx, L.ky, a, b);
+                    const T a = ax * L.c[k == 0 ? 0 : (k == 1 ? 2 : 3)];
                     acc += w[k] * a * (ql + T(4) * qm + qu);
                 }
             }
@@ -201,6 +226,8 @@ __global__ void __launch_bounds__(NT) step_var_kernel(const __grid_constant__ Va
         };
         auto yflux = [&](int dj) -> T {
             const T ys = L.yo + (T)(j + dj) * L.dy;
+            T by = T(0);
+            if constexpr (FIELD == AF_FIELD_SWIRL) by = swirl_by(L.xo + ((T)i + T(0.5)) * L.dx, ys, L.kx);
             T acc = T(0);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -210,8 +237,7 @@ __global__ void __launch_bounds__(NT) step_var_kernel(const __grid_constant__ Va
                     const T x0s = L.xo + (T)i * L.dx;
                     acc += w[k] * T(M_PI) * (x0s * ql + T(4) * (x0s + T(0.5) * L.dx) * qm + (x0s + L.dx) * qr);
                 } else {
-                    T a, b;
-                    swirl_v(L.xo + ((T)i + T(0.5)) * L.dx, ys, L.c[k == 0 ? 0 : (k == 1 ? 2 : 3)], L.kx, L.ky, a, b);
+                    const T b = by * L.c[k == 0 ? 0 : (k == 1 ? 2 : 3)];
                     acc += w[k] * b * (ql + T(4) * qm + qr);
                 }
             }
@@ -310,6 +336,15 @@ extern "C" af_status af_patch_step_var(const af_config *cfg, int32_t tiling_inde
         V.t = vel->t;
         V.dx0 = dx0;
         V.dy0 = dy0;
+        for (int l = 0; l <= AF_MAX_LEVEL; ++l) {
+            const double dtl = std::ldexp(dt0, -l), hx = std::ldexp(dx0, -l), hy = std::ldexp(dy0, -l);
+            V.cl[l][0] = std::cos(M_PI * vel->t);
+            V.cl[l][1] = std::cos(M_PI * (vel->t + 0.25 * dtl));
+            V.cl[l][2] = std::cos(M_PI * (vel->t + 0.5 * dtl));
+            V.cl[l][3] = std::cos(M_PI * (vel->t + dtl));
+            V.kl[l][0] = std::sin(M_PI * hx) / (M_PI * hx);
+            V.kl[l][1] = std::sin(M_PI * hy) / (M_PI * hy);
+        }
     };
     if (cfg->prec == AF_F64) {
         dev::VarArgs<double> V{};
