@@ -13,10 +13,6 @@ constexpr int kTileMax = 32;   // cells per tile side in af_patch_step
 constexpr int kPlanes = 4;     // avg, xmid, corner, ymid (Section 2, Fig. 1)
 enum Plane { kAvg = 0, kXmid = 1, kCorner = 2, kYmid = 3 };
 
-inline int64_t plane_stride(int n) {
-    const int64_t w = n + 2 * kGhost + 1;
-    return (w * w + 7) / 8 * 8;
-}
 
 // ---------------------------------------------------------------------------
 // Acoustic stencil weights (Eqs. ERFormula, sphe-mean).
@@ -39,6 +35,10 @@ inline int64_t plane_stride(int n) {
 #else
 #define AF_HD
 #endif
+AF_HD constexpr int64_t plane_stride(int n) {
+    return ((int64_t)(n + 2 * kGhost + 1) * (n + 2 * kGhost + 1) + 7) / 8 * 8;
+}
+
 AF_HD constexpr int x_idx(int k) {
     constexpr int t[15] = {2, 3, 7, 8, 9, 10, 11, 12, 16, 17, 18, 21, 22, 23, 24};
     return t[k];
