@@ -417,6 +417,34 @@ def amr_bench(case: str, coarse_steps: int, warmup: int, per_patch: bool = True)
     return out
 
 
+def amr_profile_run(steps: int, warmup: int, case: str = "acoustics_levels3-7"):
+    """Batched FP32 coarse steps (no graph capture, so every kernel is its own
+    launch) of one adaptive workload on its initial forest."""
+    import torch
+    from paper_2205_07572_gb300 import af
+    from paper_2205_07572_gb300.amr import AMRRun
+    c = AMR_CASES[case]
+    leaves, st = amr_initial(case)
+    cfg = af.config(c["eq"], af.F32, AMR_N, c["a"], c["b"], 1.0)
+    dx0 = (c["hi"][0] - c["lo"][0]) / (c["B"] * AMR_N)
+    run = AMRRun(cfg, c["B"], c["lmax"], leaves, st, c["lo"], c["hi"], CFL * dx0, tiling=4)
+    for _ in range(warmup):
+        run.coarse_step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        run.coarse_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    cu = run.cell_updates_per_coarse_step()
+    return {"workload": c["desc"], "leaves": run.forest.nleaf, "ms_per_coarse_step": ms,
+            "value": cu / (ms * 1e-3), "unit": "cell updates/s", "launches_per_coarse_step":
+            run.launches_per_coarse_step(), "graphs": False}
+
+
 # ----------------------------------------------------------- learned tagging
 def adapt_initial(cfg, B, lmin, lmax, lo, hi, funcs, tag):
     """Initial forest by the method's own adaptation (tag and regrid the exact
@@ -671,6 +699,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the end-to-end, literal-size, adaptive-mesh and CPU-baseline measurements")
     ap.add_argument("--var-only", action="store_true", help="only the variable-velocity advection runs")
+    ap.add_argument("--amr-profile", action="store_true",
+                    help="only batched FP32 coarse steps of the acoustics levels 3-7 forest (for a launch list)")
     ap.add_argument("--learned-only", action="store_true",
                     help="only the learned-tagging experiment")
     ap.add_argument("--amr-only", action="store_true",
@@ -723,6 +753,10 @@ def main():
         if rank == 0:
             for case in AMR_CASES:
                 print(json.dumps({"amr": case, **amr_bench(case, 8, 4)}), flush=True)
+        return
+    if args.amr_profile:
+        if rank == 0:
+            print(json.dumps(amr_profile_run(args.steps, warm)), flush=True)
         return
     if args.var_only:
         if rank == 0:

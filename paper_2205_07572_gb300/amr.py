@@ -354,7 +354,7 @@ class AMRRun:
                 n += sum(self.forest.level_slice(l).stop - self.forest.level_slice(l).start for l in due)
             sync = sum(1 for l in range(lmin, lmx + 1) if (s + 1) % (1 << (lmx - l)) == 0)
             if sync > 1:
-                n += 1 + 3
+                n += 1 + (2 if self.plan is not None else 3)   # reflux + exchange passes
         return n
 
     # ---------------------------------------------------- tags and regrid

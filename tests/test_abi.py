@@ -79,3 +79,42 @@ def test_host_side_errors(af):
         af.patch_step(adv, work, 1, buf_a, buf_b, 1.1 * dx, dx, dx, stream=0)
     assert e.value.status == 2               # Eq. cfl-adv
     af.patch_step(adv, work, 0, buf_a, buf_b, 0.5 * dx, dx, dx, stream=0)  # nothing to do: OK
+
+
+def test_work_items_carry_patch_positions(af):
+    cfg = af.config(af.ADVECTION, af.F64, 16)
+    w = af.build_step_work(cfg, [0, 1, 2], levels=[1, 1, 2], ix=[3, 1, 7], iy=[0, 2, 5])
+    items = np.frombuffer(w.tobytes(), dtype=np.int32).reshape(-1, 16)
+    # af_work: patch, level, nbr[8], x0/x1, y0/y1 (int16 pairs), flags, ix, iy, pad
+    assert items[:, 0].tolist() == [0, 1, 2]
+    assert items[:, 13].tolist() == [3, 1, 7] and items[:, 14].tolist() == [0, 2, 5]
+    plain = np.frombuffer(af.build_step_work(cfg, [0]).tobytes(), dtype=np.int32).reshape(-1, 16)
+    assert plain[0, 13] == 0 and plain[0, 14] == 0
+
+
+def test_variable_velocity_host_side_errors(af):
+    """af_patch_step_var refuses on the host: a foot farther than one mesh
+    width (AF_ERR_CFL, with the speed bounded over the domain and its ghost
+    layers), aliased arrays, acoustics, unknown fields."""
+    cfg = af.config(af.ADVECTION, af.F64, 16)
+    buf_a, buf_b, work = 1 << 20, 2 << 20, 3 << 20   # fake, aligned, never dereferenced
+    dx = 2.0 / 64
+    solid = af.velocity(af.FIELD_SOLID_BODY, (-1, -1), (1, 1), 0.0)
+    pair = af.state_pair(buf_a, buf_b, 0)
+    with pytest.raises(af.AFError) as e:      # pi * (1 + 3 dx) * dt > dx
+        af.patch_step_var(cfg, 0, work, 1, pair, solid, 0.32 * dx, dx, dx, stream=0)
+    assert e.value.status == 2
+    with pytest.raises(af.AFError) as e:
+        af.patch_step_var(cfg, 0, work, 1, af.state_pair(buf_a, buf_a, 0), solid, 0.2 * dx, dx, dx, stream=0)
+    assert e.value.status == 1
+    swirl = af.velocity(af.FIELD_SWIRL, (0, 0), (1, 1), 0.3)
+    with pytest.raises(af.AFError) as e:      # |v| <= 1
+        af.patch_step_var(cfg, 0, work, 1, pair, swirl, 1.01 * dx, dx, dx, stream=0)
+    assert e.value.status == 2
+    bad = af.velocity(7, (0, 0), (1, 1), 0.0)
+    with pytest.raises(af.AFError):
+        af.patch_step_var(cfg, 0, work, 1, pair, bad, 0.2 * dx, dx, dx, stream=0)
+    acu = af.config(af.ACOUSTICS, af.F64, 16, c=1.0)
+    with pytest.raises(af.AFError):
+        af.patch_step_var(acu, 0, work, 1, pair, swirl, 0.2 * dx, dx, dx, stream=0)
+    af.patch_step_var(cfg, 0, work, 0, pair, swirl, 0.2 * dx, dx, dx, stream=0)   # nothing to do: OK
