@@ -172,10 +172,12 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
                        "tuned_ms": {str(tilings[k]): round(v, 4) for k, v in table.items()}}}
 
 
-def run_e2e(prec: str, steps: int, warmup: int, tiling=None):
+def run_e2e(prec: str, steps: int, warmup: int, tiling=None, bands: int = 16):
     """Same step through the public API with the state kept in pinned HOST
     memory: every step copies it host->device, runs af_patch_step, and copies
-    the result back (host<->device copies inside the timed region)."""
+    the result back (host<->device copies inside the timed region), in bands
+    of patch rows so that the copies in, the step and the copies out overlap
+    (UniformRun.step_host; bands=1 is the plain sequence)."""
     import torch
     from paper_2205_07572_gb300 import af
     grid, st = initial_state(prec)
@@ -187,9 +189,7 @@ def run_e2e(prec: str, steps: int, warmup: int, tiling=None):
     stream = torch.cuda.current_stream()
 
     def one():
-        run.a.copy_(host, non_blocking=True)
-        af.patch_step(cfg, run.work, run.nwork, run.a, run.b, dt, grid.dx, grid.dy, None, stream, tiling=run.tiling)
-        host.copy_(run.b, non_blocking=True)
+        run.step_host(host, bands)
 
     for _ in range(warmup):
         one()
@@ -205,7 +205,8 @@ def run_e2e(prec: str, steps: int, warmup: int, tiling=None):
     nbytes = host.numel() * host.element_size()
     cells = grid.npatch * N_CELLS * N_CELLS
     return {"value": cells / (ms * 1e-3), "unit": "cell updates/s", "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "ms_per_step": ms}
+            "d2h_bytes_per_step": nbytes, "ms_per_step": ms, "bands": bands,
+            "link_gbs": 2 * nbytes / (ms * 1e-3) / 1e9}
 
 
 def literal_config2(prec: str, steps: int):

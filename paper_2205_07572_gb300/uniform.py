@@ -70,6 +70,55 @@ class UniformRun:
         self.t += self.dt
         self.a, self.b = self.b, self.a
 
+    def step_host(self, host, bands: int = 16):
+        """One step of a state kept in (pinned) host memory, updated in place:
+        [npatch, words] like the device arrays.  The grid is split into bands
+        of patch rows; each band is copied in, advanced and copied back on
+        three streams, so the two copy directions and the step overlap.  A
+        band is advanced once it and the neighbouring bands (periodically)
+        are on the device.  Everything is enqueued behind, and joined back
+        into, the current stream; the caller synchronises."""
+        import torch
+        if self.field is not None:
+            raise ValueError("step_host runs constant-velocity steps")
+        bands = max(1, min(int(bands), self.py))
+        key = (self.tiling, bands)
+        if getattr(self, "_bands_key", None) != key:
+            edges = [round(k * self.py / bands) for k in range(bands + 1)]
+            self._bands = []
+            for b in range(bands):
+                p = np.arange(edges[b] * self.px, edges[b + 1] * self.px)
+                w = af.build_step_work(self.cfg, p, nbr=self.nbr[p], tiling=self.tiling)
+                self._bands.append((int(p[0]), int(p[-1]) + 1, torch.from_numpy(w).to(self.device), len(w) // 64))
+            self._streams = [torch.cuda.Stream() for _ in range(3)]
+            self._bands_key = key
+        s_in, s_cmp, s_out = self._streams
+        cur = torch.cuda.current_stream()
+        for st in self._streams:
+            st.wait_stream(cur)
+        uploaded = []
+        for p0, p1, _, _ in self._bands:
+            with torch.cuda.stream(s_in):
+                self.a[p0:p1].copy_(host[p0:p1], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s_in)
+            uploaded.append(ev)
+        order = list(range(1, bands)) + [0]
+        for b in order:
+            for nb in {(b - 1) % bands, b, (b + 1) % bands}:
+                s_cmp.wait_event(uploaded[nb])
+            p0, p1, work, nwork = self._bands[b]
+            af.patch_step(self.cfg, work, nwork, self.a, self.b, self.dt, self.dx, self.dy, self.freg, s_cmp,
+                          tiling=self.tiling)
+            done = torch.cuda.Event()
+            done.record(s_cmp)
+            s_out.wait_event(done)
+            with torch.cuda.stream(s_out):
+                host[p0:p1].copy_(self.b[p0:p1], non_blocking=True)
+        cur.wait_stream(s_out)
+        cur.wait_stream(s_cmp)
+        self.t += self.dt
+
     @property
     def state(self):
         return self.a

@@ -251,3 +251,24 @@ def test_every_tiling_matches_oracle(af, prec, eq, n):
         for comp in range(nc):
             err = np.abs(g[comp] - pref[comp]).max() / np.abs(pref[comp]).max()
             assert err < TOL[prec] * (10 if prec else 1), ("periodic", k, comp, err)
+
+
+@pytest.mark.parametrize("bands", [1, 5, 16])
+def test_host_state_step_matches_device_step(af, bands):
+    """UniformRun.step_host (state in pinned host memory, banded copies
+    overlapping the step) gives the device step's result bit for bit."""
+    from paper_2205_07572_gb300.uniform import UniformRun
+    n, px = 8, 16
+    grid = S.UniformGrid(S.Layout(n, 3), px, px)
+    st = S.periodic_state(grid, S.pulse_plus_vortex(), nq=2)
+    cfg = af.config(af.ACOUSTICS, af.F64, n, c=1.0)
+    dev = UniformRun(cfg, px, px, grid.dx, grid.dy, 0.4 * grid.dx, state=st)
+    hrun = UniformRun(cfg, px, px, grid.dx, grid.dy, 0.4 * grid.dx, state=None)
+    host = torch.from_numpy(st.reshape(dev.a.shape).copy()).pin_memory()
+    for _ in range(3):
+        dev.step()
+        hrun.step_host(host, bands)
+    torch.cuda.synchronize()
+    got = host.numpy().reshape(st.shape)
+    ref = dev.state.cpu().numpy().reshape(st.shape)
+    assert np.array_equal(S.unpack_owned(grid, got), S.unpack_owned(grid, ref))
