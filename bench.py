@@ -128,6 +128,22 @@ def initial_state(prec: str):
     return grid, st
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time per step (replicas: every rank advances its own
+    copy of the workload, so the job takes as long as its slowest rank)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput of `world` replicas over the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
     import torch
     from paper_2205_07572_gb300 import af
@@ -157,11 +173,7 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
         dist.barrier()
     torch.cuda.synchronize()
     ck = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / steps
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, dist, "cuda")
     cells = grid.npatch * N_CELLS * N_CELLS
     # sanity: the state stays finite
     assert torch.isfinite(run.state).all().item()
@@ -783,7 +795,7 @@ def main():
     # not captured
     t = r32["tiling"]
     traffic = 2.153e9 if (tuple(t["tile"]) == (32, 8) and t["threads"] == 128) else None
-    value = world * cells / (r32["ms"] * 1e-3)
+    value = job_rate(cells, world, r32["ms"])
     achieved = cells * BYTES_PER_CELL["f32"] / (r32["ms"] * 1e-3) / 1e9
     line = None
     if rank == 0:
