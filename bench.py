@@ -85,7 +85,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -128,6 +128,17 @@ def initial_state(prec: str):
     return grid, st
 
 
+def _busy(run, seconds: float):
+    """Untimed steps for about `seconds` (keeps the GPU under the bench load
+    while the clocks are sampled)."""
+    import torch
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for _ in range(8):
+            run.step()
+        torch.cuda.synchronize()
+
+
 def max_over_ranks(ms: float, dist, device) -> float:
     """The slowest rank's time per step (replicas: every rank advances its own
     copy of the workload, so the job takes as long as its slowest rank)."""
@@ -156,13 +167,17 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
     from paper_2205_07572_gb300 import tune
     best, table = tune.tune(run, steps=3 if prec == "f64" else 10, warmup=1)
     stream = torch.cuda.current_stream()
+    # The timed region is far shorter than nvidia-smi's sampling interval, so
+    # the clocks are sampled over a window of the same step loop around it
+    # (about 0.3 s of untimed steps before the warm-up and after the timed steps).
+    clocks = ClockSampler(torch.cuda.current_device())
+    _busy(run, 0.3)
     for _ in range(warmup):
         run.step()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(steps):
@@ -172,7 +187,9 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    _busy(run, 0.3)
     ck = clocks.stop()
+    ck["window"] = "same step loop, ~0.3 s before the warm-up to ~0.3 s after the timed steps"
     ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, dist, "cuda")
     cells = grid.npatch * N_CELLS * N_CELLS
     # sanity: the state stays finite
