@@ -206,6 +206,15 @@ af_status af_patch_step_pair(const af_config *cfg, int32_t tiling, int32_t nwork
                              const af_state_pair *state, double dt0, double dx0, double dy0,
                              double *d_flux_reg, void *stream);
 
+/* Tiles that span a patch's interior columns are staged by bulk (TMA) copies
+ * whose completion the kernel awaits with an iteration limit (seconds).  A
+ * tile whose wait gives up leaves its outputs unwritten and increments a
+ * device counter.  This call synchronises with the device, writes the
+ * counter to *count and, if reset != 0, sets it to zero.  AF_ERR_ARG if count
+ * is NULL, AF_ERR_CUDA if the copy fails.  The counter is armed from the
+ * first af_patch_step* call made outside CUDA stream capture. */
+af_status af_step_wait_timeouts(uint32_t *count, int32_t reset);
+
 
 /* Variable-velocity advection q_t + (a q)_x + (b q)_y = 0 (one component),
  * with the velocity fields of Sections 4.2 and 4.3:

@@ -445,3 +445,15 @@ def patch_step_var(cfg: Config, tiling: int, work, nwork: int, pair: StatePair, 
     _check(lib().af_patch_step_var(C.byref(cfg), int(tiling), int(nwork), ptr(work), C.byref(pair), C.byref(vel),
                                    float(dt0), float(dx0), float(dy0), ptr(flux_reg), stream_handle(stream)),
            "af_patch_step_var")
+
+
+_EXTRA += [("af_step_wait_timeouts", C.c_int, [C.POINTER(C.c_uint32), C.c_int32])]
+if _lib is not None:
+    _register_more(_lib)
+
+
+def step_wait_timeouts(reset: bool = False) -> int:
+    """Tiles whose bounded wait on a bulk copy gave up (synchronises)."""
+    v = C.c_uint32(0)
+    _check(lib().af_step_wait_timeouts(C.byref(v), 1 if reset else 0), "af_step_wait_timeouts")
+    return int(v.value)

@@ -21,6 +21,7 @@ struct WeightKey {
 };
 
 std::mutex g_mu;
+
 WeightKey g_skey{-1, 0, 0}, g_dkey{-1, 0, 0};
 AcousticSymWeights<double> g_sw;
 bool g_sw_ok = false;
@@ -166,4 +167,15 @@ extern "C" af_status af_patch_step(const af_config *cfg, int32_t nwork, const af
     if (cfg == nullptr) return AF_ERR_ARG;
     return af_patch_step_tiled(cfg, af::default_tiling(cfg->n), nwork, d_work, d_in, d_out, dt0, dx0, dy0,
                                d_flux_reg, stream);
+}
+
+extern "C" af_status af_step_wait_timeouts(uint32_t *count, int32_t reset) {
+    if (count == nullptr) return AF_ERR_ARG;
+    unsigned int a = 0, b = 0, c = 0;
+    af_status st = af::wait_timeouts_f32(&a, reset != 0);
+    if (st == AF_OK) st = af::wait_timeouts_f64(&b, reset != 0);
+    if (st == AF_OK) st = af::wait_timeouts_f32_n16(&c, reset != 0);
+    if (st != AF_OK) return st;
+    *count = a + b + c;
+    return AF_OK;
 }

@@ -10,4 +10,5 @@ template af_status launch_step_nn<float, AF_ACOUSTICS, 16>(int, const StepArgs<f
 template af_status launch_step_nn<float, AF_ADVECTION, 16>(int, const StepArgs<float> &,
                                                            const WeightsOf<float, AF_ADVECTION>::type &, int,
                                                            cudaStream_t);
+af_status wait_timeouts_f32_n16(unsigned int *count, bool reset) { return wait_timeouts_here(count, reset); }
 }  // namespace af

@@ -8,4 +8,5 @@ template af_status launch_step<double, AF_ACOUSTICS>(int, const StepArgs<double>
                                                     const WeightsOf<double, AF_ACOUSTICS>::type &, int, cudaStream_t);
 template af_status launch_step<double, AF_ADVECTION>(int, const StepArgs<double> &,
                                                     const WeightsOf<double, AF_ADVECTION>::type &, int, cudaStream_t);
+af_status wait_timeouts_f64(unsigned int *count, bool reset) { return wait_timeouts_here(count, reset); }
 }  // namespace af

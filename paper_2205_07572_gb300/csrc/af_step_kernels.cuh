@@ -421,12 +421,161 @@ __host__ __device__ constexpr int min_ctas() {
     return (EQ == AF_ACOUSTICS && sizeof(T) == 4) ? (768 / NT > 0 ? 768 / NT : 1) : 1;
 }
 
-// Shared-memory geometry of a TMX x TMY tile.
+// Shared-memory geometry of a TMX x TMY tile.  The window is TMX + 3 node
+// columns wide; its pitch is two more, the lattice width of TMX-cell patches,
+// so that their full-width tiles can be staged in bulk; each plane has room
+// for the window origin's offset and the bulk copies' rounding to 16 bytes
+// (12 elements), and a size that keeps every plane 16-byte aligned.
 template <int TMX, int TMY>
 struct Geo {
-    static constexpr int WX = TMX + 3, WY = TMY + 3, WSZ = WX * WY;  // window
+    static constexpr int WX = TMX + 2 * kGhost + 1, WY = TMY + 3, WSZ = (WX * WY + 12 + 3) / 4 * 4;  // window
     static constexpr int TX = TMX + 1, TY = TMY + 1, TSZ = TX * TY;  // T arrays
 };
+
+// ---------------------------------------------------------------------------
+// Bulk staging.  When the window pitch equals the lattice width (WX = n + 5)
+// and the tile spans the patch's interior columns (x0 = 0, x1 = n), the
+// window rows y0-1 .. y1+1 of each plane -- ghost columns included -- are one
+// contiguous span of the patch lattice, and one bulk (TMA) copy per plane
+// stages them, signalling an mbarrier.  Entries in a direction with a
+// same-level neighbour are then overwritten with that neighbour's values (the
+// fused same-level ghost copy of Section 3.1), exactly the entries the
+// element-wise staging takes from the neighbour; the staged window is the same.
+
+// Iteration limit of a wait on a bulk copy (each try_wait suspends for at
+// most a few microseconds, so this is seconds, far beyond any real copy).
+constexpr unsigned kWaitLimit = 1u << 22;
+
+// Tiles whose wait gave up, one counter per translation unit that
+// instantiates step kernels (read by wait_timeouts_here).
+static __device__ unsigned int g_wait_timeouts;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// One bulk copy global -> shared of `bytes` (both addresses 16-byte aligned,
+// bytes a multiple of 16) completing on `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// Wait for phase `parity` of `bar`; false if the iteration limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const unsigned a = smem_addr(bar);
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Offset (elements) of the window origin from the start of the shared
+// window buffer: room for the rounding of a bulk copy's start down to 16
+// bytes, plus the 16-byte phase of the window origin of a tile with y0 = 0.
+template <typename T, int WX>
+__host__ __device__ constexpr int win_off() {
+    return 16 / (int)sizeof(T) + ((kGhost - 1) * WX + kGhost - 1) % (16 / (int)sizeof(T));
+}
+
+// True if work item wk is staged in bulk by a kernel with window pitch WX:
+// the pitch is the lattice width, the tile spans the interior columns, and
+// its window origin has the 16-byte phase win_off assumes (y0 * WX a
+// multiple of 16 bytes: every tile of the compiled tilings).
+template <typename T, int WX>
+__device__ __forceinline__ bool bulk_tile(const StepArgs<T> &A, const af_work &wk) {
+    constexpr int E = 16 / (int)sizeof(T);
+    return A.n + 2 * kGhost + 1 == WX && wk.x0 == 0 && wk.x1 == A.n && wk.y0 >= 0 && wk.y1 <= A.n &&
+           (wk.y0 * WX) % E == 0;
+}
+
+// Stage work item wk (bulk_tile true) into the window at Sin (= window
+// buffer + win_off), so that every plane's copy starts on a 16-byte
+// boundary.  Returns false (in every thread) if a wait gave up;
+// g_wait_timeouts is then incremented.  Ends with a CTA barrier.
+template <typename T, int NT, int WX, int WSZ, int NC>
+__device__ __forceinline__ bool stage_bulk(const StepArgs<T> &A, const af_work &wk, T *Sin, uint64_t *bar) {
+    constexpr int n = WX - 2 * kGhost - 1;
+    constexpr int E = 16 / (int)sizeof(T);
+    constexpr int ncp = NC * kPlanes;
+    constexpr int64_t plane = plane_stride(n), pw = ncp * plane;
+    const T *const in = src_buf(A, wk.level);
+    const int y0 = wk.y0, y1 = wk.y1, wh = y1 - y0 + 3;
+    const int g_org = (y0 - 1 + kGhost) * WX + (kGhost - 1);  // lattice offset of window entry (0, 0)
+    const int g_lo = (g_org - 1) / E * E;                     // row start (lattice column 0), rounded down
+    const int g_hi = (g_org - 1 + wh * WX + E - 1) / E * E;    // end of the last row, rounded up
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)((g_hi - g_lo) * (int)sizeof(T));
+        mbar_expect_tx(bar, bytes * ncp);
+        const T *src = in + (int64_t)wk.patch * pw + g_lo;
+        T *dst = Sin + (g_lo - g_org);
+#pragma unroll
+        for (int cp = 0; cp < ncp; ++cp) bulk_copy_g2s(dst + cp * WSZ, src + cp * plane, bytes, bar);
+    }
+    // Window entries outside the patch interior: columns -1, n, n+1 of every
+    // window row, and rows -1 (y0 = 0) and n .. y1+1 of columns 0 .. n-1.
+    int nb[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) nb[d] = wk.nbr[d];
+    const int nlo = y0 == 0 ? 1 : 0, nhi = y1 + 2 > n ? y1 + 2 - n : 0;
+    const int ncol = 3 * wh, nh = ncol + (nlo + nhi) * n;
+    bool waited = false, ok = true;
+    for (int t = threadIdx.x; t < nh; t += NT) {
+        int li, lj;
+        if (t < ncol) {
+            const int c = t / wh;
+            li = c == 0 ? -1 : n - 1 + c;
+            lj = y0 - 1 + (t - c * wh);
+        } else {
+            const int u = t - ncol, r = u / n;
+            li = u - r * n;
+            lj = r < nlo ? -1 : n + r - nlo;
+        }
+        const int sx = li < 0 ? -1 : (li >= n ? 1 : 0);
+        const int sy = lj < 0 ? -1 : (lj >= n ? 1 : 0);
+        const int d = dir_index(sx, sy);
+        int q = nb[0];
+#pragma unroll
+        for (int e = 1; e < 8; ++e) q = (d == e) ? nb[e] : q;
+        if (q < 0) continue;  // no same-level neighbour: the patch's own ghost entry, already staged
+        const T *g = in + (int64_t)q * pw + ((lj - sy * n + kGhost) * WX + (li - sx * n + kGhost));
+        T v[ncp];
+#pragma unroll
+        for (int cp = 0; cp < ncp; ++cp) v[cp] = __ldg(g + cp * plane);
+        if (!waited) {  // the bulk copy must land before its entries are overwritten
+            ok = mbar_wait(bar, 0);
+            waited = true;
+        }
+        T *sp = Sin + (lj - y0 + 1) * WX + (li + 1);
+#pragma unroll
+        for (int cp = 0; cp < ncp; ++cp) sp[cp * WSZ] = v[cp];
+    }
+    if (!waited) ok = mbar_wait(bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicAdd(&g_wait_timeouts, 1u);
+            mbar_wait(bar, 0);  // bounded: give the copies in flight a second chance to land
+        }
+        return false;
+    }
+    return true;
+}
 
 // One tile per CTA.
 template <typename T, int EQ, int NT, int TMX, int TMY, int NN = 0>
@@ -435,14 +584,20 @@ __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel(const
     using Gm = Geo<TMX, TMY>;
     constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Sin = reinterpret_cast<T *>(smem_raw);
-    T *ST = Sin + ncomp * kPlanes * Gm::WSZ;
+    T *const Sbase = reinterpret_cast<T *>(smem_raw);
+    T *const Sin = Sbase + win_off<T, Gm::WX>();
+    T *ST = Sbase + ncomp * kPlanes * Gm::WSZ;
     const af_work wk = A.work[blockIdx.x];  // by value: read once
     if (wk.x1 - wk.x0 > TMX || wk.y1 - wk.y0 > TMY) return;  // built for another tiling
-    stage_issue<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, wk, Sin);
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
+    if (bulk_tile<T, Gm::WX>(A, wk)) {
+        __shared__ __align__(8) uint64_t bar;
+        if (!stage_bulk<T, NT, Gm::WX, Gm::WSZ, ncomp>(A, wk, Sin, &bar)) return;  // counted in g_wait_timeouts
+    } else {
+        stage_issue<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, wk, Sin);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+    }
     if (wk.flags & 1) {
         stage_copy_out<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, wk, Sin);
         __syncthreads();  // copies land before the computed values overwrite them
@@ -573,5 +728,36 @@ af_status launch_step(int k, const StepArgs<T> &A, const typename WeightsOf<T, E
     }
     return launch_step_nn<T, EQ, 0>(k, A, W, nwork, stream);
 }
+
+// Reads (and, if reset, clears) this translation unit's g_wait_timeouts;
+// each translation unit that instantiates step kernels exports it under its
+// own name (af_step_f32.cu, af_step_f64.cu, af_step_f32_n16.cu).
+static inline af_status wait_timeouts_here(unsigned int *count, bool reset) {
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, dev::g_wait_timeouts, sizeof(v)) != cudaSuccess) return AF_ERR_CUDA;
+    *count = v;
+    if (reset && v != 0) {
+        const unsigned int zero = 0;
+        if (cudaMemcpyToSymbol(dev::g_wait_timeouts, &zero, sizeof(zero)) != cudaSuccess) return AF_ERR_CUDA;
+    }
+    return AF_OK;
+}
+af_status wait_timeouts_f32(unsigned int *count, bool reset);
+af_status wait_timeouts_f64(unsigned int *count, bool reset);
+af_status wait_timeouts_f32_n16(unsigned int *count, bool reset);
+
+// Instantiated once each, in af_step_f32.cu and af_step_f64.cu.
+extern template af_status launch_step<float, AF_ACOUSTICS>(int, const StepArgs<float> &,
+                                                           const WeightsOf<float, AF_ACOUSTICS>::type &, int,
+                                                           cudaStream_t);
+extern template af_status launch_step<float, AF_ADVECTION>(int, const StepArgs<float> &,
+                                                           const WeightsOf<float, AF_ADVECTION>::type &, int,
+                                                           cudaStream_t);
+extern template af_status launch_step<double, AF_ACOUSTICS>(int, const StepArgs<double> &,
+                                                            const WeightsOf<double, AF_ACOUSTICS>::type &, int,
+                                                            cudaStream_t);
+extern template af_status launch_step<double, AF_ADVECTION>(int, const StepArgs<double> &,
+                                                            const WeightsOf<double, AF_ADVECTION>::type &, int,
+                                                            cudaStream_t);
 
 }  // namespace af

@@ -367,3 +367,30 @@ def test_planned_fill_equals_direct_fill_bitwise(af, eq, prec):
         assert torch.equal(got, one), levels
     with pytest.raises(af.AFError):
         af.fill_ghosts_planned(cfg, F.c, 0b01100, 0, plan, n_a, n_b, af.state_pair(one, None, 0))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_amr_run_with_bulk_staged_tiles_matches_oracle(af, prec):
+    """16 x 16-cell patches in one 16 x 16 tile each: patches surrounded by
+    same-level neighbours are staged by bulk (TMA) copies, patches that
+    advance their ghost layer element by element; two subcycled coarse
+    steps of acoustics agree with the oracle."""
+    from paper_2205_07572_gb300.amr import AMRRun
+    n, lmax = 16, 3
+    leaves = _sorted(S.balanced_forest(1, 2, lmax, lambda l, x, y: x == y and x < 2))
+    st = S.forest_state(n, 3, 1, lmax, leaves, S.pulse_plus_vortex(), nq=3)
+    if prec:
+        st = st.astype(np.float32).astype(np.float64)
+    dx0 = 1.0 / n
+    dt0 = 0.4 * dx0
+    Fo = OracleForest(1, n, 1, lmax, leaves, (0, 0), (1, 1), dt0, 1.0, 0.5, 1.0, state=st)
+    Fo.sync_fill((1 << (lmax + 1)) - 1)
+    k = [t[:2] for t in af.step_tilings()].index((16, 16))
+    run = AMRRun(af.config(1, prec, n, 1.0, 0.5, 1.0), 1, lmax, leaves, st, (0, 0), (1, 1), dt0, tiling=k)
+    af.step_wait_timeouts(reset=True)
+    for _ in range(2):
+        Fo.coarse_step()
+        run.coarse_step()
+    torch.cuda.synchronize()
+    _compare(Fo, run, n, 3, TOL[prec] * (10 if prec else 1))
+    assert af.step_wait_timeouts() == 0

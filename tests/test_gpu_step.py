@@ -272,3 +272,60 @@ def test_host_state_step_matches_device_step(af, bands):
     got = host.numpy().reshape(st.shape)
     ref = dev.state.cpu().numpy().reshape(st.shape)
     assert np.array_equal(S.unpack_owned(grid, got), S.unpack_owned(grid, ref))
+
+
+def _resplit(work, n, cuts):
+    """Work items of one full-width tile per row band: each patch's items
+    replaced by tiles [cuts[k], cuts[k + 1]) x [0, n)."""
+    w = np.frombuffer(work.tobytes(), dtype=np.int32).reshape(-1, 16).copy()
+    first = w[np.unique(w[:, 0], return_index=True)[1]]
+    out = []
+    for item in first:
+        for y0, y1 in zip(cuts[:-1], cuts[1:]):
+            it = item.copy()
+            h = it.view(np.int16)
+            h[20:24] = [0, n, y0, y1]
+            out.append(it)
+    return np.ascontiguousarray(np.stack(out)).view(np.uint8).reshape(-1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("eq,n,k", [(1, 32, 3), (0, 32, 3), (1, 32, 0), (1, 16, 4), (0, 16, 4)])
+def test_bulk_staging_equals_elementwise_staging(af, prec, eq, n, k):
+    """Full-width tiles whose window is staged by bulk (TMA) copies plus the
+    neighbours' halo, and tiles staged element by element, give the same
+    step bit for bit in one kernel: the row bands of the second and third
+    work lists start on rows whose 16-byte phase differs from row 0's (the
+    element-wise path) or equals it (bulk), and all three agree with the
+    oracle.  No bounded wait gives up."""
+    from paper_2205_07572_gb300.uniform import UniformRun
+    nc = 1 if eq == 0 else 3
+    tdt = torch.float64 if prec == 0 else torch.float32
+    grid = S.UniformGrid(S.Layout(n, nc), 3, 3)
+    own = S.random_owned(grid, seed=90 + n + eq)
+    if prec:
+        own = own.astype(np.float32).astype(np.float64)
+    pst = S.pack_owned(grid, own)
+    dt = _dt(eq, 0.45, grid.dx, grid.dy, 0.9, -0.4, 1.0)
+    pref = S.unpack_owned(grid, O.run_uniform(O.cfg(eq, n, grid.dx, grid.dy, dt, 0.9, -0.4, 1.0), 3, 3, 1, pst))
+    cfg = af.config(eq, prec, n, 0.9, -0.4, 1.0)
+    run = UniformRun(cfg, 3, 3, grid.dx, grid.dy, dt, state=np.nan_to_num(pst), tiling=k)
+    tmy = af.step_tilings()[k][1]
+    odd = [0] + list(range(tmy - 3, n, tmy)) + [n]            # starts 0 (bulk), tmy-3, ... (element-wise)
+    four = [0] + list(range(4, n, tmy)) + [n]                 # every start a multiple of 4: all bulk
+    af.step_wait_timeouts(reset=True)
+    outs = []
+    for work in (run.work.cpu().numpy(), _resplit(run.work.cpu().numpy(), n, odd),
+                 _resplit(run.work.cpu().numpy(), n, four)):
+        din = run.a.clone()
+        dout = din.clone()
+        af.patch_step(cfg, torch.from_numpy(work).cuda(), len(work) // 64, din, dout, dt, grid.dx, grid.dy,
+                      tiling=k)
+        torch.cuda.synchronize()
+        outs.append(np.nan_to_num(dout.cpu().numpy()))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    g = S.unpack_owned(grid, outs[0].astype(np.float64).reshape(pst.shape))
+    for comp in range(nc):
+        err = np.abs(g[comp] - pref[comp]).max() / np.abs(pref[comp]).max()
+        assert err < TOL[prec] * (10 if prec else 1), (comp, err)
+    assert af.step_wait_timeouts() == 0
