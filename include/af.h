@@ -73,7 +73,10 @@ typedef struct {
     int32_t nbr[8];     /* same-level neighbour patch of W, E, S, N, SW, SE, NW, NE, or -1 */
     int16_t x0, x1;     /* cells [x0, x1) of the patch, in [-1, N+1] */
     int16_t y0, y1;
-    int32_t flags;      /* bit 0: the patch advances its first ghost layer too */
+    int32_t flags;      /* bit 0: the patch advances its first ghost layer too;
+                           bit 1 (AF_WORK_SKIP_BULK_COPY): failure injection --
+                           a bulk-staged tile does not issue its copies, so its
+                           bounded wait runs out (af_step_wait_timeouts) */
     int32_t ix, iy;     /* column and row of the patch among the patches of its level
                            (af_build_step_work_at; used only by af_patch_step_var) */
     int32_t pad_;
@@ -207,13 +210,16 @@ af_status af_patch_step_pair(const af_config *cfg, int32_t tiling, int32_t nwork
                              double *d_flux_reg, void *stream);
 
 /* Tiles that span a patch's interior columns are staged by bulk (TMA) copies
- * whose completion the kernel awaits with an iteration limit (seconds).  A
- * tile whose wait gives up leaves its outputs unwritten and increments a
- * device counter.  This call synchronises with the device, writes the
+ * whose completion the kernel awaits for at most about a second (2^31 SM
+ * cycles).  A tile whose wait gives up waits once more with the same limit
+ * for its copies in flight, leaves its outputs unwritten and increments a
+ * device counter.  Setting AF_WORK_SKIP_BULK_COPY in a work item's flags
+ * makes that happen without any fault: its copies are never issued.  This call synchronises with the device, writes the
  * counter to *count and, if reset != 0, sets it to zero.  AF_ERR_ARG if count
  * is NULL, AF_ERR_CUDA if the copy fails.  The counter is armed from the
  * first af_patch_step* call made outside CUDA stream capture. */
 af_status af_step_wait_timeouts(uint32_t *count, int32_t reset);
+#define AF_WORK_SKIP_BULK_COPY 2
 
 
 /* Variable-velocity advection q_t + (a q)_x + (b q)_y = 0 (one component),

@@ -452,6 +452,9 @@ if _lib is not None:
     _register_more(_lib)
 
 
+WORK_SKIP_BULK_COPY = 2  # af_work.flags bit: failure injection, the tile's bulk copies are not issued
+
+
 def step_wait_timeouts(reset: bool = False) -> int:
     """Tiles whose bounded wait on a bulk copy gave up (synchronises)."""
     v = C.c_uint32(0)

@@ -442,9 +442,10 @@ struct Geo {
 // fused same-level ghost copy of Section 3.1), exactly the entries the
 // element-wise staging takes from the neighbour; the staged window is the same.
 
-// Iteration limit of a wait on a bulk copy (each try_wait suspends for at
-// most a few microseconds, so this is seconds, far beyond any real copy).
-constexpr unsigned kWaitLimit = 1u << 22;
+// Limit of a wait on a bulk copy: 2^31 SM cycles (about a second), far
+// beyond any real copy, and an iteration cap behind it.
+constexpr long long kWaitCycles = 1ll << 31;
+constexpr unsigned kWaitIters = 1u << 26;
 
 // Tiles whose wait gave up, one counter per translation unit that
 // instantiates step kernels (read by wait_timeouts_here).
@@ -472,7 +473,8 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsign
 // Wait for phase `parity` of `bar`; false if the iteration limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     const unsigned a = smem_addr(bar);
-    for (unsigned it = 0; it < kWaitLimit; ++it) {
+    const long long t0 = clock64();
+    for (unsigned it = 0; it < kWaitIters; ++it) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -480,6 +482,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if (clock64() - t0 > kWaitCycles) break;
     }
     return false;
 }
@@ -520,7 +523,7 @@ __device__ __forceinline__ bool stage_bulk(const StepArgs<T> &A, const af_work &
     const int g_hi = (g_org - 1 + wh * WX + E - 1) / E * E;    // end of the last row, rounded up
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !(wk.flags & AF_WORK_SKIP_BULK_COPY)) {
         const unsigned bytes = (unsigned)((g_hi - g_lo) * (int)sizeof(T));
         mbar_expect_tx(bar, bytes * ncp);
         const T *src = in + (int64_t)wk.patch * pw + g_lo;

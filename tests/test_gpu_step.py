@@ -329,3 +329,43 @@ def test_bulk_staging_equals_elementwise_staging(af, prec, eq, n, k):
         err = np.abs(g[comp] - pref[comp]).max() / np.abs(pref[comp]).max()
         assert err < TOL[prec] * (10 if prec else 1), (comp, err)
     assert af.step_wait_timeouts() == 0
+
+
+def test_bulk_wait_timeout_is_reported(af):
+    """Failure injection from the host: one work item carries
+    AF_WORK_SKIP_BULK_COPY, so its bulk copies are never issued and its
+    bounded wait (about a second) runs out.  Nothing faults: the tile's
+    outputs stay unwritten, every other tile is exact,
+    af_step_wait_timeouts reports one timeout, and the next step is normal."""
+    from paper_2205_07572_gb300.uniform import UniformRun
+    n = 32
+    grid = S.UniformGrid(S.Layout(n, 3), 3, 3)
+    pst = S.pack_owned(grid, S.random_owned(grid, seed=5).astype(np.float32).astype(np.float64))
+    cfg = af.config(af.ACOUSTICS, af.F32, n, c=1.0)
+    k = [t[:3] for t in af.step_tilings()].index((32, 8, 128))
+    run = UniformRun(cfg, 3, 3, grid.dx, grid.dy, 0.4 * grid.dx, state=np.nan_to_num(pst), tiling=k)
+    work = run.work.cpu().numpy()
+    items = np.frombuffer(work.tobytes(), dtype=np.int32).reshape(-1, 16).copy()
+    victim = 4
+    items[victim, 12] |= af.WORK_SKIP_BULK_COPY
+    bad = np.ascontiguousarray(items).view(np.uint8).reshape(-1)
+
+    def step(w):
+        out = torch.full_like(run.a, 7.0)
+        af.patch_step(cfg, torch.from_numpy(w).cuda(), len(w) // 64, run.a, out, run.dt, grid.dx, grid.dy, tiling=k)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    ref = step(work)
+    af.step_wait_timeouts(reset=True)
+    got = step(bad)
+    assert af.step_wait_timeouts(reset=True) == 1
+    p = items[victim, 0]
+    y0, y1 = items[victim].view(np.int16)[22:24]
+    diff = np.nonzero((got != ref).any(axis=1))[0]
+    assert diff.tolist() == [p]
+    lay = S.Layout(n, 3)
+    avg = lay.lattice(got[p].reshape(1, 3, 4, -1))[0, :, 0]          # [comp, J, I]
+    assert (avg[:, S.G + y0:S.G + y1, S.G:S.G + n] == 7.0).all()
+    assert np.array_equal(step(work), ref)
+    assert af.step_wait_timeouts() == 0
