@@ -273,13 +273,14 @@ __device__ __forceinline__ T adv_eval(const T *w, const T *Sin, int cq, int cr) 
     return v;
 }
 
-// Point values (Eq. advection-update / Eq. ERFormula), then fluxes (Eq.
-// Simpson-2d) and the update (Eq. 2dfv) of one staged tile.  Sin: window
-// (pitch WX, plane size WSZ); ST: T arrays (pitch TX, size TSZ).
+// Point values of one staged tile (Eq. advection-update / Eq. ERFormula):
+// Q^{n+1} of every node the tile owns to the output, T = Q^n + 4 Q^{n+1/2}
+// + Q^{n+1} to ST.  Sin: window (pitch WX, plane size WSZ); ST: T arrays
+// (pitch TX, size TSZ).  The caller synchronises before tile_fluxes.
 template <typename T, int EQ, int NT, int WX, int WSZ, int TX, int TSZ, int TMX = TX - 1, int NN = 0>
-__device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W,
-                                             const T *Sin, T *ST, int patch, int level, int x0, int x1, int y0,
-                                             int y1) {
+__device__ __forceinline__ void tile_nodes(const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W,
+                                           const T *Sin, T *ST, int patch, int level, int x0, int x1, int y0,
+                                           int y1) {
     constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
     const int tw = x1 - x0, th = y1 - y0;
     const int n = NN > 0 ? NN : A.n, W_ = n + 2 * kGhost + 1;
@@ -356,9 +357,20 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
             }
         }
     }
-    __syncthreads();
+}
 
-    // ---- fluxes and update
+// Fluxes (Eq. Simpson-2d) and the update (Eq. 2dfv) of one tile whose T
+// arrays tile_nodes has written; reads the cell averages from the window.
+template <typename T, int EQ, int NT, int WX, int WSZ, int TX, int TSZ, int TMX = TX - 1, int NN = 0>
+__device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, const T *ST, int patch, int level,
+                                            int x0, int x1, int y0, int y1) {
+    constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
+    const int tw = x1 - x0, th = y1 - y0;
+    const int n = NN > 0 ? NN : A.n, W_ = n + 2 * kGhost + 1;
+    const int plane = NN > 0 ? (int)plane_stride(NN) : (int)A.plane;
+    const int64_t pw = (int64_t)ncomp * kPlanes * plane;
+    T *outp = dst_buf(A, level) + (int64_t)patch * pw;
+    const bool full = (tw == TMX);
     const double dtl = ldexp(A.dt0, -level);
     for (int it = threadIdx.x; it < tw * th; it += NT) {
         int jj, ii;
@@ -411,6 +423,16 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
             }
         }
     }
+}
+
+// Point values, then fluxes and update, of one staged tile.
+template <typename T, int EQ, int NT, int WX, int WSZ, int TX, int TSZ, int TMX = TX - 1, int NN = 0>
+__device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W,
+                                             const T *Sin, T *ST, int patch, int level, int x0, int x1, int y0,
+                                             int y1) {
+    tile_nodes<T, EQ, NT, WX, WSZ, TX, TSZ, TMX, NN>(A, W, Sin, ST, patch, level, x0, x1, y0, y1);
+    __syncthreads();
+    tile_fluxes<T, EQ, NT, WX, WSZ, TX, TSZ, TMX, NN>(A, Sin, ST, patch, level, x0, x1, y0, y1);
 }
 
 // Resident CTAs per SM the register allocation must allow: FP32 acoustics
@@ -506,41 +528,45 @@ __device__ __forceinline__ bool bulk_tile(const StepArgs<T> &A, const af_work &w
            (wk.y0 * WX) % E == 0;
 }
 
-// Stage work item wk (bulk_tile true) into the window at Sin (= window
-// buffer + win_off), so that every plane's copy starts on a 16-byte
-// boundary.  Returns false (in every thread) if a wait gave up;
-// g_wait_timeouts is then incremented.  Ends with a CTA barrier.
-template <typename T, int NT, int WX, int WSZ, int NC>
-__device__ __forceinline__ bool stage_bulk(const StepArgs<T> &A, const af_work &wk, T *Sin, uint64_t *bar) {
+// Issue (thread 0) the bulk copies of work item wk (bulk_tile true) into the
+// window at Sin (= window buffer + win_off, so that every plane's copy
+// starts on a 16-byte boundary), completing on bar.  Nothing is issued for
+// an item carrying AF_WORK_SKIP_BULK_COPY, so a wait on bar runs out.
+template <typename T, int WX, int WSZ, int NC>
+__device__ __forceinline__ void bulk_issue(const StepArgs<T> &A, const af_work &wk, T *Sin, uint64_t *bar) {
     constexpr int n = WX - 2 * kGhost - 1;
     constexpr int E = 16 / (int)sizeof(T);
     constexpr int ncp = NC * kPlanes;
     constexpr int64_t plane = plane_stride(n), pw = ncp * plane;
-    const T *const in = src_buf(A, wk.level);
-    const int y0 = wk.y0, y1 = wk.y1, wh = y1 - y0 + 3;
+    if (wk.flags & AF_WORK_SKIP_BULK_COPY) return;
+    const int y0 = wk.y0, wh = wk.y1 - y0 + 3;
     const int g_org = (y0 - 1 + kGhost) * WX + (kGhost - 1);  // lattice offset of window entry (0, 0)
     const int g_lo = (g_org - 1) / E * E;                     // row start (lattice column 0), rounded down
     const int g_hi = (g_org - 1 + wh * WX + E - 1) / E * E;    // end of the last row, rounded up
-    if (threadIdx.x == 0) mbar_init(bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0 && !(wk.flags & AF_WORK_SKIP_BULK_COPY)) {
-        const unsigned bytes = (unsigned)((g_hi - g_lo) * (int)sizeof(T));
-        mbar_expect_tx(bar, bytes * ncp);
-        const T *src = in + (int64_t)wk.patch * pw + g_lo;
-        T *dst = Sin + (g_lo - g_org);
+    const unsigned bytes = (unsigned)((g_hi - g_lo) * (int)sizeof(T));
+    mbar_expect_tx(bar, bytes * ncp);
+    const T *src = src_buf(A, wk.level) + (int64_t)wk.patch * pw + g_lo;
+    T *dst = Sin + (g_lo - g_org);
 #pragma unroll
-        for (int cp = 0; cp < ncp; ++cp) bulk_copy_g2s(dst + cp * WSZ, src + cp * plane, bytes, bar);
+    for (int cp = 0; cp < ncp; ++cp) bulk_copy_g2s(dst + cp * WSZ, src + cp * plane, bytes, bar);
+}
+
+// Halo list of a bulk-staged tile of n-cell patches: the window entries
+// outside the patch interior -- columns -1, n, n+1 of every window row, and
+// rows -1 (y0 = 0) and n .. y1+1 of columns 0 .. n-1.  Entry t gets its node
+// (li, lj) and returns the same-level neighbour it is read from (*src: the
+// lattice offset there), or -1: no such neighbour, the patch's own ghost
+// value (staged by the bulk copy) stays.
+template <int n>
+struct HaloList {
+    int y0, wh, nlo, ncol, count;
+    __device__ __forceinline__ HaloList(int y0_, int y1) : y0(y0_), wh(y1 - y0_ + 3) {
+        nlo = y0 == 0 ? 1 : 0;
+        const int nhi = y1 + 2 > n ? y1 + 2 - n : 0;
+        ncol = 3 * wh;
+        count = ncol + (nlo + nhi) * n;
     }
-    // Window entries outside the patch interior: columns -1, n, n+1 of every
-    // window row, and rows -1 (y0 = 0) and n .. y1+1 of columns 0 .. n-1.
-    int nb[8];
-#pragma unroll
-    for (int d = 0; d < 8; ++d) nb[d] = wk.nbr[d];
-    const int nlo = y0 == 0 ? 1 : 0, nhi = y1 + 2 > n ? y1 + 2 - n : 0;
-    const int ncol = 3 * wh, nh = ncol + (nlo + nhi) * n;
-    bool waited = false, ok = true;
-    for (int t = threadIdx.x; t < nh; t += NT) {
-        int li, lj;
+    __device__ __forceinline__ int entry(const int nb[8], int t, int &li, int &lj, int &src) const {
         if (t < ncol) {
             const int c = t / wh;
             li = c == 0 ? -1 : n - 1 + c;
@@ -556,8 +582,35 @@ __device__ __forceinline__ bool stage_bulk(const StepArgs<T> &A, const af_work &
         int q = nb[0];
 #pragma unroll
         for (int e = 1; e < 8; ++e) q = (d == e) ? nb[e] : q;
-        if (q < 0) continue;  // no same-level neighbour: the patch's own ghost entry, already staged
-        const T *g = in + (int64_t)q * pw + ((lj - sy * n + kGhost) * WX + (li - sx * n + kGhost));
+        src = (lj - sy * n + kGhost) * (n + 2 * kGhost + 1) + (li - sx * n + kGhost);
+        return q;
+    }
+};
+
+// Stage work item wk (bulk_tile true) into the window at Sin: bulk copies,
+// then the halo entries read with plain loads (issued before the wait) and
+// stored once the copies have landed.  Returns false (in every thread) if a
+// wait gave up; g_wait_timeouts is then incremented.  Ends with a CTA
+// barrier.
+template <typename T, int NT, int WX, int WSZ, int NC>
+__device__ __forceinline__ bool stage_bulk(const StepArgs<T> &A, const af_work &wk, T *Sin, uint64_t *bar) {
+    constexpr int n = WX - 2 * kGhost - 1;
+    constexpr int ncp = NC * kPlanes;
+    constexpr int64_t plane = plane_stride(n), pw = ncp * plane;
+    const T *const in = src_buf(A, wk.level);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) bulk_issue<T, WX, WSZ, NC>(A, wk, Sin, bar);
+    int nb[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) nb[d] = wk.nbr[d];
+    const HaloList<n> H(wk.y0, wk.y1);
+    bool waited = false, ok = true;
+    for (int t = threadIdx.x; t < H.count; t += NT) {
+        int li, lj, so;
+        const int q = H.entry(nb, t, li, lj, so);
+        if (q < 0) continue;
+        const T *g = in + (int64_t)q * pw + so;
         T v[ncp];
 #pragma unroll
         for (int cp = 0; cp < ncp; ++cp) v[cp] = __ldg(g + cp * plane);
@@ -565,7 +618,7 @@ __device__ __forceinline__ bool stage_bulk(const StepArgs<T> &A, const af_work &
             ok = mbar_wait(bar, 0);
             waited = true;
         }
-        T *sp = Sin + (lj - y0 + 1) * WX + (li + 1);
+        T *sp = Sin + (lj - H.y0 + 1) * WX + (li + 1);
 #pragma unroll
         for (int cp = 0; cp < ncp; ++cp) sp[cp * WSZ] = v[cp];
     }
@@ -579,6 +632,33 @@ __device__ __forceinline__ bool stage_bulk(const StepArgs<T> &A, const af_work &
     }
     return true;
 }
+
+// Issue (every thread, without waiting) the halo copies of a bulk-staged
+// tile whose bulk copies have landed.
+template <typename T, int NT, int WX, int WSZ, int NC>
+__device__ __forceinline__ void halo_async(const StepArgs<T> &A, const af_work &wk, T *Sin) {
+    constexpr int n = WX - 2 * kGhost - 1;
+    constexpr int ncp = NC * kPlanes;
+    constexpr int64_t plane = plane_stride(n), pw = ncp * plane;
+    const T *const in = src_buf(A, wk.level);
+    int nb[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) nb[d] = wk.nbr[d];
+    const HaloList<n> H(wk.y0, wk.y1);
+    for (int t = threadIdx.x; t < H.count; t += NT) {
+        int li, lj, so;
+        const int q = H.entry(nb, t, li, lj, so);
+        if (q < 0) continue;
+        const T *g = in + (int64_t)q * pw + so;
+        T *sp = Sin + (lj - H.y0 + 1) * WX + (li + 1);
+#pragma unroll
+        for (int cp = 0; cp < ncp; ++cp) cp_async(sp + cp * WSZ, g + cp * plane);
+    }
+}
+
+// Order this thread's generic-proxy accesses to shared memory before later
+// bulk (async-proxy) writes to the same buffer.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 // One tile per CTA.
 template <typename T, int EQ, int NT, int TMX, int TMY, int NN = 0>
@@ -609,9 +689,21 @@ __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel(const
                                                                       wk.x1, wk.y0, wk.y1);
 }
 
-// Persistent variant: one CTA loops over work items, double-buffering the
-// staged windows: while tile t is computed, the copies of the next tile are
-// already in flight.
+// How a persistent CTA stages a work item: 0 not at all (built for another
+// tiling), 1 element by element, 2 in bulk.
+template <typename T, int WX, int TMX, int TMY>
+__device__ __forceinline__ int stage_kind(const StepArgs<T> &A, const af_work &w) {
+    if (w.x1 - w.x0 > TMX || w.y1 - w.y0 > TMY) return 0;
+    return bulk_tile<T, WX>(A, w) ? 2 : 1;
+}
+
+// Persistent variant: one CTA loops over work items t, t + gridDim.x, ...
+// with two windows, so staging overlaps compute.  The copies of the next
+// tile are issued before the node phase of the current one: its bulk copies
+// (thread 0), or its element-wise copies.  A bulk-staged next tile's halo
+// copies follow between the current tile's node and flux phases, once its
+// bulk copies have landed.  A wait that gives up ends the CTA (its remaining
+// tiles stay unwritten) after counting it in g_wait_timeouts.
 template <typename T, int EQ, int NT, int TMX, int TMY, int NN = 0>
 __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel_pipe(const __grid_constant__ StepArgs<T> A,
                                                        const __grid_constant__ typename WeightsOf<T, EQ>::type W,
@@ -620,33 +712,85 @@ __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel_pipe(
     constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
     constexpr int wbuf = ncomp * kPlanes * Gm::WSZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *S0 = reinterpret_cast<T *>(smem_raw);
-    T *ST = S0 + 2 * wbuf;
+    T *const S0 = reinterpret_cast<T *>(smem_raw) + win_off<T, Gm::WX>();
+    T *const ST = reinterpret_cast<T *>(smem_raw) + 2 * wbuf;
+    __shared__ __align__(8) uint64_t bar[2];
     int t = blockIdx.x;
     if (t >= nwork) return;
-    auto fits = [](const af_work &w) { return w.x1 - w.x0 <= TMX && w.y1 - w.y0 <= TMY; };
-    if (fits(A.work[t])) stage_issue<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, A.work[t], S0);
-    cp_async_commit();
-    int buf = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    unsigned phase = 0;  // bit b: parity of the next phase of bar[b]
+    bool ok = true;
+    {  // the first tile, staged completely
+        const int kind = stage_kind<T, Gm::WX, TMX, TMY>(A, A.work[t]);
+        if (kind == 2) {
+            if (threadIdx.x == 0) bulk_issue<T, Gm::WX, Gm::WSZ, ncomp>(A, A.work[t], S0, &bar[0]);
+            ok = mbar_wait(&bar[0], 0);
+            phase = 1;
+            halo_async<T, NT, Gm::WX, Gm::WSZ, ncomp>(A, A.work[t], S0);
+        } else if (kind == 1) {
+            stage_issue<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, A.work[t], S0);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicAdd(&g_wait_timeouts, 1u);
+                mbar_wait(&bar[0], 0);
+            }
+            return;
+        }
+    }
+    int b = 0;
     for (; t < nwork; t += gridDim.x) {
         const int tn = t + gridDim.x;
-        if (tn < nwork && fits(A.work[tn]))
-            stage_issue<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, A.work[tn], S0 + (buf ^ 1) * wbuf);
-        cp_async_commit();
-        cp_async_wait_one();
-        __syncthreads();
-        const af_work wk = A.work[t];
-        if (fits(wk)) {
-            const T *Sin = S0 + buf * wbuf;
-            if (wk.flags & 1) {
-                stage_copy_out<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, wk, Sin);
-                __syncthreads();
+        T *const Sc = S0 + b * wbuf;
+        T *const Sn = S0 + (b ^ 1) * wbuf;
+        int nkind = 0;
+        if (tn < nwork) {
+            nkind = stage_kind<T, Gm::WX, TMX, TMY>(A, A.work[tn]);
+            if (nkind == 2) {
+                if (threadIdx.x == 0) bulk_issue<T, Gm::WX, Gm::WSZ, ncomp>(A, A.work[tn], Sn, &bar[b ^ 1]);
+            } else if (nkind == 1) {
+                stage_issue<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, A.work[tn], Sn);
+                cp_async_commit();
             }
-            tile_compute<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ, TMX, NN>(A, W, Sin, ST, wk.patch, wk.level,
-                                                                              wk.x0, wk.x1, wk.y0, wk.y1);
+        }
+        const af_work wk = A.work[t];
+        const bool fits = wk.x1 - wk.x0 <= TMX && wk.y1 - wk.y0 <= TMY;
+        if (fits) {
+            if (wk.flags & 1) {
+                stage_copy_out<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, wk, Sc);
+                __syncthreads();  // copies land before the computed values overwrite them
+            }
+            tile_nodes<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ, TMX, NN>(A, W, Sc, ST, wk.patch, wk.level,
+                                                                            wk.x0, wk.x1, wk.y0, wk.y1);
         }
         __syncthreads();
-        buf ^= 1;
+        unsigned par = 0;
+        if (nkind == 2) {
+            par = (phase >> (b ^ 1)) & 1u;
+            ok = mbar_wait(&bar[b ^ 1], par);
+            phase ^= 1u << (b ^ 1);
+            halo_async<T, NT, Gm::WX, Gm::WSZ, ncomp>(A, A.work[tn], Sn);
+            cp_async_commit();
+        }
+        if (fits)
+            tile_fluxes<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ, TMX, NN>(A, Sc, ST, wk.patch, wk.level, wk.x0,
+                                                                             wk.x1, wk.y0, wk.y1);
+        cp_async_wait_all();
+        fence_proxy_async();  // this window is refilled by bulk copies after the barrier
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicAdd(&g_wait_timeouts, 1u);
+                mbar_wait(&bar[b ^ 1], par);  // bounded: the copies in flight
+            }
+            return;
+        }
+        b ^= 1;
     }
 }
 
