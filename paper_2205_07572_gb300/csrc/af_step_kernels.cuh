@@ -371,7 +371,6 @@ __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, 
     const int64_t pw = (int64_t)ncomp * kPlanes * plane;
     T *outp = dst_buf(A, level) + (int64_t)patch * pw;
     const bool full = (tw == TMX);
-    const double dtl = ldexp(A.dt0, -level);
     for (int it = threadIdx.x; it < tw * th; it += NT) {
         int jj, ii;
         if (full) {
@@ -412,6 +411,9 @@ __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, 
             ob[c * kPlanes * plane] = q - A.dtdx * (fr[c] - fl[c]) - A.dtdy * (gt[c] - gb[c]);
         }
         if (A.freg != nullptr) {
+            // dt_l = dt0 / 2^level, scaled exactly by the power of two (no FP64
+            // library call outside this branch)
+            const double dtl = A.dt0 * __longlong_as_double((long long)(1023 - level) << 52);
             double *fr_p = A.freg + (int64_t)patch * 4 * ncomp * n;
             const bool iny = (j >= 0 && j < n), inx = (i >= 0 && i < n);
 #pragma unroll
@@ -855,15 +857,20 @@ af_status launch_step_nn(int k, const StepArgs<T> &A, const typename WeightsOf<T
 }
 
 // FP32 kernels are also compiled for 16 x 16-cell patches (the adaptive
-// workloads), with plane offsets as constants: 13 % faster on the adaptive
-// advection step.  The same specialisation for 32 x 32 patches measured
-// slower than the run-time size (0.73 against 0.60 ms per 16.8M-cell
-// acoustics step), so those use the general kernels.  The instantiations
-// live in their own translation unit.
+// workloads) and 32 x 32-cell patches, with lattice widths and plane offsets
+// as constants: 13 % faster on the adaptive advection step, 3 % on the
+// 16.8M-cell acoustics step.  The instantiations live in translation units
+// of their own (af_step_f32_n16.cu, af_step_f32_n32.cu).
 extern template af_status launch_step_nn<float, AF_ACOUSTICS, 16>(int, const StepArgs<float> &,
                                                                   const WeightsOf<float, AF_ACOUSTICS>::type &, int,
                                                                   cudaStream_t);
 extern template af_status launch_step_nn<float, AF_ADVECTION, 16>(int, const StepArgs<float> &,
+                                                                  const WeightsOf<float, AF_ADVECTION>::type &, int,
+                                                                  cudaStream_t);
+extern template af_status launch_step_nn<float, AF_ACOUSTICS, 32>(int, const StepArgs<float> &,
+                                                                  const WeightsOf<float, AF_ACOUSTICS>::type &, int,
+                                                                  cudaStream_t);
+extern template af_status launch_step_nn<float, AF_ADVECTION, 32>(int, const StepArgs<float> &,
                                                                   const WeightsOf<float, AF_ADVECTION>::type &, int,
                                                                   cudaStream_t);
 
@@ -872,13 +879,15 @@ af_status launch_step(int k, const StepArgs<T> &A, const typename WeightsOf<T, E
                       cudaStream_t stream) {
     if constexpr (sizeof(T) == 4) {
         if (A.n == 16) return launch_step_nn<T, EQ, 16>(k, A, W, nwork, stream);
+        if (A.n == 32) return launch_step_nn<T, EQ, 32>(k, A, W, nwork, stream);
     }
     return launch_step_nn<T, EQ, 0>(k, A, W, nwork, stream);
 }
 
 // Reads (and, if reset, clears) this translation unit's g_wait_timeouts;
 // each translation unit that instantiates step kernels exports it under its
-// own name (af_step_f32.cu, af_step_f64.cu, af_step_f32_n16.cu).
+// own name (af_step_f32.cu, af_step_f64.cu, af_step_f32_n16.cu,
+// af_step_f32_n32.cu).
 static inline af_status wait_timeouts_here(unsigned int *count, bool reset) {
     unsigned int v = 0;
     if (cudaMemcpyFromSymbol(&v, dev::g_wait_timeouts, sizeof(v)) != cudaSuccess) return AF_ERR_CUDA;
@@ -892,6 +901,7 @@ static inline af_status wait_timeouts_here(unsigned int *count, bool reset) {
 af_status wait_timeouts_f32(unsigned int *count, bool reset);
 af_status wait_timeouts_f64(unsigned int *count, bool reset);
 af_status wait_timeouts_f32_n16(unsigned int *count, bool reset);
+af_status wait_timeouts_f32_n32(unsigned int *count, bool reset);
 
 // Instantiated once each, in af_step_f32.cu and af_step_f64.cu.
 extern template af_status launch_step<float, AF_ACOUSTICS>(int, const StepArgs<float> &,
