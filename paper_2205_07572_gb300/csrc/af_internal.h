@@ -71,6 +71,15 @@ struct AcousticSymWeights {
     T yA[2][6], yDx[2][3], yDy[2][4];
 };
 
+// FP32 acoustic weights with the two time combinations of each weight side
+// by side (x: T, y: Q^{n+1}), so one packed FP32x2 multiply-add advances
+// both accumulators of a node value.
+struct AcousticPairWeights {
+    float cA[9][2], cDx[6][2], cDy[6][2];
+    float xA[6][2], xDx[4][2], xDy[3][2];
+    float yA[6][2], yDx[3][2], yDy[4][2];
+};
+
 // Advection weights (Eq. advection-update): for node type t (0 corner,
 // 1 left-edge mid, 2 bottom-edge mid) and time s (0: dt/2, 1: dt) the foot of
 // the characteristic lies in cell (line + off[t][s][0], line + off[t][s][1]);

@@ -59,6 +59,15 @@ void get_advection(double nx, double ny, AdvectionWeights<T> &out) {
         }
 }
 
+// Interleave the two time combinations (T, Q^{n+1}) of every FP32 weight.
+void pair_weights(const AcousticSymWeights<float> &s, AcousticPairWeights &p) {
+    for (int k = 0; k < 9; ++k) for (int t = 0; t < 2; ++t) p.cA[k][t] = s.cA[t][k];
+    for (int k = 0; k < 6; ++k) for (int t = 0; t < 2; ++t) p.cDx[k][t] = s.cDx[t][k], p.cDy[k][t] = s.cDy[t][k];
+    for (int k = 0; k < 6; ++k) for (int t = 0; t < 2; ++t) p.xA[k][t] = s.xA[t][k], p.yA[k][t] = s.yA[t][k];
+    for (int k = 0; k < 4; ++k) for (int t = 0; t < 2; ++t) p.xDx[k][t] = s.xDx[t][k], p.yDy[k][t] = s.yDy[t][k];
+    for (int k = 0; k < 3; ++k) for (int t = 0; t < 2; ++t) p.xDy[k][t] = s.xDy[t][k], p.yDx[k][t] = s.yDx[t][k];
+}
+
 template <typename T, int EQ>
 af_status launch(int k, const af_config &cfg, int nwork, const af_work *d_work, const void *d_in, void *d_out,
                  uint32_t swap, double dt0, double dx0, double dy0, double *d_freg, cudaStream_t stream) {
@@ -77,7 +86,13 @@ af_status launch(int k, const af_config &cfg, int nwork, const af_work *d_work, 
     typename WeightsOf<T, EQ>::type W;
     if constexpr (EQ == AF_ACOUSTICS) {
         A.fx = A.fy = (T)(cfg.c / 36.0);
-        if (!get_acoustic<T>(cfg.c * dt0 / dx0, cfg.c * dt0 / dy0, W)) return AF_ERR_UNIMPLEMENTED;
+        if constexpr (sizeof(T) == 4) {
+            AcousticSymWeights<float> sw;
+            if (!get_acoustic<float>(cfg.c * dt0 / dx0, cfg.c * dt0 / dy0, sw)) return AF_ERR_UNIMPLEMENTED;
+            pair_weights(sw, W);
+        } else {
+            if (!get_acoustic<T>(cfg.c * dt0 / dx0, cfg.c * dt0 / dy0, W)) return AF_ERR_UNIMPLEMENTED;
+        }
     } else {
         A.fx = (T)(cfg.a / 36.0);
         A.fy = (T)(cfg.b / 36.0);

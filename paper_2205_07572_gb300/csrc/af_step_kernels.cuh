@@ -13,7 +13,8 @@
 //            and bottom-edge midpoint of its cell to t^{n+1/2} and t^{n+1}
 //            (Eq. advection-update / Eq. ERFormula) as constant-weight
 //            stencils, keeps T = Q^n + 4 Q^{n+1/2} + Q^{n+1} in shared memory
-//            and writes Q^{n+1} to the output;
+//            and writes Q^{n+1} to the output (FP32 acoustics: T and Q^{n+1}
+//            accumulated together by packed FP32x2 multiply-adds);
 //   update - one thread per cell forms the four face fluxes by the space-time
 //            Simpson rule (Eq. Simpson-2d: f is linear, so the 3 x 3 sum is
 //            f((T_lo + 4 T_mid + T_hi) / 36)) and applies Eq. 2dfv.
@@ -54,6 +55,8 @@ template <typename T, int EQ>
 struct WeightsOf;
 template <typename T>
 struct WeightsOf<T, AF_ACOUSTICS> { using type = AcousticSymWeights<T>; };
+template <>
+struct WeightsOf<float, AF_ACOUSTICS> { using type = AcousticPairWeights; };
 template <typename T>
 struct WeightsOf<T, AF_ADVECTION> { using type = AdvectionWeights<T>; };
 
@@ -253,6 +256,73 @@ __device__ __forceinline__ void acoustic_item(const AcousticSymWeights<T> &W, co
             dot<3>(tx[0], W.xDy[0], xsa); dot<3>(nx[0], W.xDy[1], xsa);
             dot<4>(ty[0], W.yDy[0], ysa); dot<4>(ny[0], W.yDy[1], ysa);
         }
+    }
+}
+
+// acc += (w[k][0], w[k][1]) * v[k] over k, both lanes at once (packed FP32x2
+// multiply-add; each lane rounds like the scalar fma chain).
+template <int N>
+__device__ __forceinline__ void dot2(float2 &acc, const float (*w)[2], const float *v) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc = __ffma2_rn(make_float2(w[k][0], w[k][1]), make_float2(v[k], v[k]), acc);
+}
+
+// FP32 acoustic node evaluation: as acoustic_item, with the T and Q^{n+1}
+// accumulators of every node value packed in one float2.
+template <typename T, int WX, int WSZ>
+__device__ __forceinline__ void acoustic_item(const AcousticPairWeights &W, const float *Sin, int qi, int rj,
+                                              float tc[3], float nc[3], float tx[3], float nx[3], float ty[3],
+                                              float ny[3]) {
+    float2 c2[3], x2[3], y2[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) c2[o] = x2[o] = y2[o] = make_float2(0.f, 0.f);
+    const float *base = Sin + (rj - 1) * WX + (qi - 1);
+#pragma unroll
+    for (int ci = 0; ci < 3; ++ci) {
+        float b[25];
+#pragma unroll
+        for (int k = 0; k < 25; ++k) b[k] = base[(ci * kPlanes + blk_plane(k)) * WSZ + blk_b(k) * WX + blk_a(k)];
+        float css[9], cas[6], csa[6];
+        quad(b[3], b[1], b[2], b[0], css[0], cas[0], csa[0]);
+        quad(b[12], b[6], b[10], b[4], css[1], cas[1], csa[1]);
+        quad(b[18], b[15], b[16], b[13], css[2], cas[2], csa[2]);
+        quad(b[24], b[20], b[23], b[19], css[3], cas[3], csa[3]);
+        css[4] = b[9] + b[7];   cas[4] = b[9] - b[7];
+        css[5] = b[22] + b[21]; cas[5] = b[22] - b[21];
+        css[6] = b[11] + b[5];  csa[4] = b[11] - b[5];
+        css[7] = b[17] + b[14]; csa[5] = b[17] - b[14];
+        css[8] = b[8];
+        float xss[6], xas[4], xsa[3];
+        quad(b[12], b[9], b[10], b[7], xss[0], xas[0], xsa[0]);
+        quad(b[24], b[22], b[23], b[21], xss[1], xas[1], xsa[1]);
+        xss[2] = b[3] + b[2];   xas[2] = b[3] - b[2];
+        xss[3] = b[18] + b[16]; xas[3] = b[18] - b[16];
+        xss[4] = b[11] + b[8];  xsa[2] = b[11] - b[8];
+        xss[5] = b[17];
+        float yss[6], yas[3], ysa[4];
+        quad(b[12], b[6], b[11], b[5], yss[0], yas[0], ysa[0]);
+        quad(b[18], b[15], b[17], b[14], yss[1], yas[1], ysa[1]);
+        yss[2] = b[9] + b[8];   yas[2] = b[9] - b[8];
+        yss[3] = b[3] + b[1];   ysa[2] = b[3] - b[1];
+        yss[4] = b[24] + b[20]; ysa[3] = b[24] - b[20];
+        yss[5] = b[22];
+        if (ci == 0) {
+            dot2<9>(c2[0], W.cA, css);  dot2<6>(x2[0], W.xA, xss);  dot2<6>(y2[0], W.yA, yss);
+            dot2<6>(c2[1], W.cDx, cas); dot2<4>(x2[1], W.xDx, xas); dot2<3>(y2[1], W.yDx, yas);
+            dot2<6>(c2[2], W.cDy, csa); dot2<3>(x2[2], W.xDy, xsa); dot2<4>(y2[2], W.yDy, ysa);
+        } else if (ci == 1) {
+            dot2<9>(c2[1], W.cA, css);  dot2<6>(x2[1], W.xA, xss);  dot2<6>(y2[1], W.yA, yss);
+            dot2<6>(c2[0], W.cDx, cas); dot2<4>(x2[0], W.xDx, xas); dot2<3>(y2[0], W.yDx, yas);
+        } else {
+            dot2<9>(c2[2], W.cA, css);  dot2<6>(x2[2], W.xA, xss);  dot2<6>(y2[2], W.yA, yss);
+            dot2<6>(c2[0], W.cDy, csa); dot2<3>(x2[0], W.xDy, xsa); dot2<4>(y2[0], W.yDy, ysa);
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        tc[o] = c2[o].x; nc[o] = c2[o].y;
+        tx[o] = x2[o].x; nx[o] = x2[o].y;
+        ty[o] = y2[o].x; ny[o] = y2[o].y;
     }
 }
 
