@@ -161,7 +161,10 @@ af_status af_build_step_work_at(const af_config *cfg, int32_t tiling, int32_t np
  *            cell.  A patch that advances its first ghost layer (one with a
  *            non-same-level neighbour) is written whole: its other entries
  *            are copied from d_in (same-level directions: from the
- *            neighbours).  For other patches entries not advanced are left
+ *            neighbours).  For other patches the ghost ring is not kept:
+ *            its entries in the rows of advanced cells may receive the
+ *            values read at t^n (a patch's own or its neighbours'), so that
+ *            whole lattice rows are written; other ghost entries are left
  *            untouched.  Must not be the same buffer as d_in (AF_ERR_ARG).
  * dt0, dx0, dy0   time step and mesh widths of level 0 (level l uses /2^l).
  *            AF_ERR_CFL if max(|a| dt/dx, |b| dt/dy) > 1 (Eq. cfl-adv) or

@@ -728,6 +728,31 @@ __device__ __forceinline__ void halo_async(const StepArgs<T> &A, const af_work &
     }
 }
 
+// For a bulk-staged tile: write the ghost columns (-2, -1, n, n+1, n+2) of
+// the lattice rows y0 .. y1-1 the tile writes, in every plane, with the
+// staged t^n values.  The tile's rows then go out whole, so consecutive rows
+// fill their shared 32-byte sectors and no partial sector needs a
+// read-modify-write in DRAM.  No other entry of a patch without a
+// non-same-level neighbour is read, so these values are never used.
+template <typename T, int NT, int WX, int WSZ, int NC>
+__device__ __forceinline__ void write_ghost_columns(const StepArgs<T> &A, const af_work &wk, const T *Sin) {
+    constexpr int n = WX - 2 * kGhost - 1;
+    constexpr int ncp = NC * kPlanes;
+    constexpr int64_t plane = plane_stride(n), pw = ncp * plane;
+    static_assert(NT % 8 == 0, "threads in groups of eight: five ghost columns each");
+    T *const out = dst_buf(A, wk.level) + (int64_t)wk.patch * pw;
+    const int y0 = wk.y0, rows = wk.y1 - y0;
+    const int k = threadIdx.x & 7;  // ghost column -2, -1, n, n+1, n+2 (k < 5)
+    if (k >= 5) return;
+    const int li = k < 2 ? k - kGhost : n + (k - 2);
+    for (int row = threadIdx.x >> 3; row < rows; row += NT / 8) {
+        T *o = out + (int64_t)(y0 + row + kGhost) * WX + (li + kGhost);
+        const T *sp = Sin + (row + 1) * WX + (li + 1);
+#pragma unroll
+        for (int cp = 0; cp < ncp; ++cp) o[cp * plane] = sp[cp * WSZ];
+    }
+}
+
 // Order this thread's generic-proxy accesses to shared memory before later
 // bulk (async-proxy) writes to the same buffer.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -759,6 +784,7 @@ __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel(const
     }
     tile_compute<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ, TMX, NN>(A, W, Sin, ST, wk.patch, wk.level, wk.x0,
                                                                       wk.x1, wk.y0, wk.y1);
+    if (bulk_tile<T, Gm::WX>(A, wk)) write_ghost_columns<T, NT, Gm::WX, Gm::WSZ, ncomp>(A, wk, Sin);
 }
 
 // How a persistent CTA stages a work item: 0 not at all (built for another
@@ -850,9 +876,11 @@ __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel_pipe(
             halo_async<T, NT, Gm::WX, Gm::WSZ, ncomp>(A, A.work[tn], Sn);
             cp_async_commit();
         }
-        if (fits)
+        if (fits) {
             tile_fluxes<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ, TMX, NN>(A, Sc, ST, wk.patch, wk.level, wk.x0,
                                                                              wk.x1, wk.y0, wk.y1);
+            if (bulk_tile<T, Gm::WX>(A, wk)) write_ghost_columns<T, NT, Gm::WX, Gm::WSZ, ncomp>(A, wk, Sc);
+        }
         cp_async_wait_all();
         fence_proxy_async();  // this window is refilled by bulk copies after the barrier
         if (__syncthreads_or(!ok)) {
