@@ -414,3 +414,56 @@ def test_persistent_pipeline_equals_one_tile_kernel(af, prec, eq):
             outs.append(dout.cpu().numpy())
         assert np.array_equal(outs[0], outs[1])
     assert af.step_wait_timeouts() == 0
+
+
+def _pack_periodic(grid, owned):
+    """pack_owned with the ghost ring filled from the periodic neighbours."""
+    lay = grid.layout
+    n, g = lay.n, S.G
+    st = lay.empty(grid.npatch)
+    lat = lay.lattice(st)
+    loc = np.arange(lay.w) - g
+    X, Y = grid.px * n, grid.py * n
+    for p in range(grid.npatch):
+        ix, iy = p % grid.px, p // grid.px
+        gx, gy = (ix * n + loc) % X, (iy * n + loc) % Y
+        lat[p] = owned[:, :, gy[:, None], gx[None, :]]
+    return np.nan_to_num(st)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bulk_tiles_read_own_ghosts_where_no_neighbour_is_listed(af, prec):
+    """A bulk-staged tile whose work item lists no neighbour on a side takes
+    that side's halo -- ghost rows included -- from the patch's own ghost
+    ring.  With the ring filled periodically the step equals the one with all
+    eight neighbours listed, bit for bit."""
+    from paper_2205_07572_gb300.uniform import UniformRun
+    n, px = 32, 3
+    grid = S.UniformGrid(S.Layout(n, 3), px, px)
+    own = S.random_owned(grid, seed=21)
+    if prec:
+        own = own.astype(np.float32).astype(np.float64)
+    st = _pack_periodic(grid, own)
+    cfg = af.config(af.ACOUSTICS, prec, n, c=1.0)
+    k = af.step_tilings().index((32, 8, 128, 0))
+    run = UniformRun(cfg, px, px, grid.dx, grid.dy, 0.4 * grid.dx, state=st, tiling=k)
+    base = run.work.cpu().numpy()
+    items = np.frombuffer(base.tobytes(), dtype=np.int32).reshape(-1, 16).copy()
+    h = items.view(np.int16)
+    for it, hh in zip(items, h):
+        p = it[0]
+        if hh[22] == 0 and p % 2 == 0:
+            it[4] = -1                        # no S neighbour listed
+        if hh[23] == n and p % 3 == 0:
+            it[9] = -1                        # no NE neighbour listed
+        if p % 4 == 1:
+            it[2] = -1                        # no W neighbour listed
+    cut = np.ascontiguousarray(items).view(np.uint8).reshape(-1)
+    outs = []
+    for w in (base, cut):
+        dout = torch.zeros_like(run.a)
+        af.patch_step(cfg, torch.from_numpy(w).cuda(), len(w) // 64, run.a, dout, run.dt, grid.dx, grid.dy, tiling=k)
+        torch.cuda.synchronize()
+        outs.append(S.unpack_owned(grid, dout.double().cpu().numpy().reshape(st.shape)))
+    assert np.array_equal(outs[0], outs[1])
+    assert af.step_wait_timeouts() == 0
