@@ -201,40 +201,53 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
                        "tuned_ms": {str(tilings[k]): round(v, 4) for k, v in table.items()}}}
 
 
-def run_e2e(prec: str, steps: int, warmup: int, tiling=None, bands: int = 16):
+def run_e2e(prec: str, steps: int, warmup: int, tiling=None, bands: int = 16, layout: str = "owned"):
     """Same step through the public API with the state kept in pinned HOST
     memory: every step copies it host->device, runs af_patch_step, and copies
     the result back (host<->device copies inside the timed region), in bands
-    of patch rows so that the copies in, the step and the copies out overlap
-    (UniformRun.step_host; bands=1 is the plain sequence)."""
+    of patch rows so that the copies in, the step and the copies out overlap.
+    layout "owned": the host holds only the patches' own degrees of freedom
+    ([patch][comp][plane][n][n], UniformRun.step_host_owned: unpacked into and
+    packed out of the device state by af_unpack_owned / af_pack_owned);
+    "lattice": the host holds the device layout, ghost rings and padding
+    included (UniformRun.step_host)."""
     import torch
+    import synth as S
     from paper_2205_07572_gb300 import af
     grid, st = initial_state(prec)
     dt = CFL * grid.dx
     cfg = af.config(af.ACOUSTICS, af.F32 if prec == "f32" else af.F64, N_CELLS, c=1.0)
     from paper_2205_07572_gb300.uniform import UniformRun
     run = UniformRun(cfg, P_SIDE, P_SIDE, grid.dx, grid.dy, dt, state=None, tiling=tiling)
-    host = torch.from_numpy(st.reshape(run.a.shape)).pin_memory()
+    lat = st.reshape(run.a.shape)
+    if layout == "owned":
+        g, n = S.G, N_CELLS
+        own = S.Layout(n, 3).lattice(lat.reshape(grid.npatch, 3, 4, -1))[..., g:g + n, g:g + n]
+        host = torch.from_numpy(np.ascontiguousarray(own).reshape(grid.npatch, -1)).pin_memory()
+        step = run.step_host_owned
+    else:
+        host = torch.from_numpy(lat).pin_memory()
+        step = run.step_host
     stream = torch.cuda.current_stream()
 
     def one():
-        run.step_host(host, bands)
+        step(host, bands)
 
     for _ in range(warmup):
         one()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(steps):
         one()
     ev1.record(stream)
     torch.cuda.synchronize()
+    assert torch.isfinite(host).all().item()
     ms = ev0.elapsed_time(ev1) / steps
     nbytes = host.numel() * host.element_size()
     cells = grid.npatch * N_CELLS * N_CELLS
     return {"value": cells / (ms * 1e-3), "unit": "cell updates/s", "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "ms_per_step": ms, "bands": bands,
+            "d2h_bytes_per_step": nbytes, "ms_per_step": ms, "bands": bands, "host_layout": layout,
             "link_gbs": 2 * nbytes / (ms * 1e-3) / 1e9}
 
 
@@ -818,6 +831,10 @@ def main():
     if rank == 0:
         extras = not args.no_extras
         e2e = run_e2e("f32", max(3, args.steps // 4), 2, r32["tiling"]["index"]) if extras else None
+        if e2e is not None:  # context: the host holding the device layout, ghost rings included
+            lat = run_e2e("f32", max(3, args.steps // 4), 2, r32["tiling"]["index"], layout="lattice")
+            e2e["lattice_layout"] = {k: lat[k] for k in ("value", "ms_per_step", "h2d_bytes_per_step",
+                                                         "d2h_bytes_per_step", "link_gbs")}
         lit32 = literal_config2("f32", 50) if extras else None
         lit64 = literal_config2("f64", 10) if extras else None
         cpu = None if (args.no_cpu_baseline or not extras) else oracle_sample(20)

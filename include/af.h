@@ -212,6 +212,24 @@ af_status af_patch_step_pair(const af_config *cfg, int32_t tiling, int32_t nwork
                              const af_state_pair *state, double dt0, double dx0, double dy0,
                              double *d_flux_reg, void *stream);
 
+/* The owned degrees of freedom of npatch patches (entries with i, j in
+ * [0, N) of every plane: the cell averages and the corner, left-edge and
+ * bottom-edge point values of the patch's own cells, Section 2, Fig. 1)
+ * between the state layout above and a compact array
+ * owned[patch][comp][plane][j][i], N x N per plane, elements as cfg->prec,
+ * no padding.  For a state kept in host memory this is all that crosses the
+ * host link: a patch with same-level neighbours on all sides reads its halo
+ * from them, so its ghost ring need not travel.
+ * af_pack_owned    d_state -> d_owned
+ * af_unpack_owned  d_owned -> d_state; the ghost ring and the plane padding of
+ *                  d_state are left untouched
+ * Both asynchronous on `stream`, device pointers owned by the caller.
+ * AF_ERR_ARG on a bad cfg, npatch < 0, a NULL pointer (npatch > 0) or the same
+ * pointer twice; AF_ERR_LAYOUT if d_state is not 32-byte aligned or d_owned
+ * not aligned to its element size. */
+af_status af_pack_owned(const af_config *cfg, int32_t npatch, const void *d_state, void *d_owned, void *stream);
+af_status af_unpack_owned(const af_config *cfg, int32_t npatch, const void *d_owned, void *d_state, void *stream);
+
 /* Tiles that span a patch's interior columns are staged by bulk (TMA) copies
  * whose completion the kernel awaits for at most about a second (2^31 SM
  * cycles).  A tile whose wait gives up waits once more with the same limit

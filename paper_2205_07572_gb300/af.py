@@ -460,3 +460,26 @@ def step_wait_timeouts(reset: bool = False) -> int:
     v = C.c_uint32(0)
     _check(lib().af_step_wait_timeouts(C.byref(v), 1 if reset else 0), "af_step_wait_timeouts")
     return int(v.value)
+
+
+_EXTRA += [("af_pack_owned", C.c_int, [C.POINTER(Config), C.c_int32, _VP, _VP, _VP]),
+           ("af_unpack_owned", C.c_int, [C.POINTER(Config), C.c_int32, _VP, _VP, _VP])]
+if _lib is not None:
+    _register_more(_lib)
+
+
+def owned_words(n: int, ncomp: int) -> int:
+    """Elements of one patch in the compact owned layout: ncomp * 4 * n * n."""
+    return ncomp * 4 * n * n
+
+
+def pack_owned(cfg: Config, npatch: int, state, owned, stream=None) -> None:
+    """af_pack_owned: lattice state -> compact [patch][comp][plane][n][n]."""
+    _check(lib().af_pack_owned(C.byref(cfg), int(npatch), ptr(state), ptr(owned), stream_handle(stream)),
+           "af_pack_owned")
+
+
+def unpack_owned(cfg: Config, npatch: int, owned, state, stream=None) -> None:
+    """af_unpack_owned: compact owned entries -> lattice state (ghosts untouched)."""
+    _check(lib().af_unpack_owned(C.byref(cfg), int(npatch), ptr(owned), ptr(state), stream_handle(stream)),
+           "af_unpack_owned")

@@ -70,6 +70,20 @@ class UniformRun:
         self.t += self.dt
         self.a, self.b = self.b, self.a
 
+    def _band_setup(self, bands: int):
+        """Work lists of `bands` bands of patch rows, and three streams."""
+        import torch
+        key = (self.tiling, bands)
+        if getattr(self, "_bands_key", None) != key:
+            edges = [round(k * self.py / bands) for k in range(bands + 1)]
+            self._bands = []
+            for b in range(bands):
+                p = np.arange(edges[b] * self.px, edges[b + 1] * self.px)
+                w = af.build_step_work(self.cfg, p, nbr=self.nbr[p], tiling=self.tiling)
+                self._bands.append((int(p[0]), int(p[-1]) + 1, torch.from_numpy(w).to(self.device), len(w) // 64))
+            self._streams = [torch.cuda.Stream() for _ in range(3)]
+            self._bands_key = key
+
     def step_host(self, host, bands: int = 16):
         """One step of a state kept in (pinned) host memory, updated in place:
         [npatch, words] like the device arrays.  The grid is split into bands
@@ -82,16 +96,7 @@ class UniformRun:
         if self.field is not None:
             raise ValueError("step_host runs constant-velocity steps")
         bands = max(1, min(int(bands), self.py))
-        key = (self.tiling, bands)
-        if getattr(self, "_bands_key", None) != key:
-            edges = [round(k * self.py / bands) for k in range(bands + 1)]
-            self._bands = []
-            for b in range(bands):
-                p = np.arange(edges[b] * self.px, edges[b + 1] * self.px)
-                w = af.build_step_work(self.cfg, p, nbr=self.nbr[p], tiling=self.tiling)
-                self._bands.append((int(p[0]), int(p[-1]) + 1, torch.from_numpy(w).to(self.device), len(w) // 64))
-            self._streams = [torch.cuda.Stream() for _ in range(3)]
-            self._bands_key = key
+        self._band_setup(bands)
         s_in, s_cmp, s_out = self._streams
         cur = torch.cuda.current_stream()
         for st in self._streams:
@@ -115,6 +120,53 @@ class UniformRun:
             s_out.wait_event(done)
             with torch.cuda.stream(s_out):
                 host[p0:p1].copy_(self.b[p0:p1], non_blocking=True)
+        cur.wait_stream(s_out)
+        cur.wait_stream(s_cmp)
+        self.t += self.dt
+
+    def step_host_owned(self, host, bands: int = 16):
+        """step_host for a state kept in host memory in the compact owned
+        layout ([npatch, ncomp * 4 * n * n], af_pack_owned's): only the
+        patches' own degrees of freedom cross the host link, 74 % of the
+        lattice words for 32 x 32 patches.  A band is copied in and unpacked
+        into the device state, advanced once it and its neighbouring bands
+        are there, packed and copied back; ghost rings stay on the device and
+        are never needed (every patch reads its halo from its neighbours)."""
+        import torch
+        if self.field is not None:
+            raise ValueError("step_host_owned runs constant-velocity steps")
+        bands = max(1, min(int(bands), self.py))
+        self._band_setup(bands)
+        words = af.owned_words(self.cfg.n, self.cfg.ncomp)
+        if getattr(self, "_own_bufs", None) is None or self._own_bufs[0].shape != (self.npatch, words):
+            self._own_bufs = (torch.empty((self.npatch, words), dtype=self.a.dtype, device=self.device),
+                              torch.empty((self.npatch, words), dtype=self.a.dtype, device=self.device))
+        own_in, own_out = self._own_bufs
+        s_in, s_cmp, s_out = self._streams
+        cur = torch.cuda.current_stream()
+        for st in self._streams:
+            st.wait_stream(cur)
+        uploaded = []
+        for p0, p1, _, _ in self._bands:
+            with torch.cuda.stream(s_in):
+                own_in[p0:p1].copy_(host[p0:p1], non_blocking=True)
+            af.unpack_owned(self.cfg, p1 - p0, own_in[p0:p1], self.a[p0:p1], s_in)
+            ev = torch.cuda.Event()
+            ev.record(s_in)
+            uploaded.append(ev)
+        order = list(range(1, bands)) + [0]
+        for b in order:
+            for nb in {(b - 1) % bands, b, (b + 1) % bands}:
+                s_cmp.wait_event(uploaded[nb])
+            p0, p1, work, nwork = self._bands[b]
+            af.patch_step(self.cfg, work, nwork, self.a, self.b, self.dt, self.dx, self.dy, self.freg, s_cmp,
+                          tiling=self.tiling)
+            af.pack_owned(self.cfg, p1 - p0, self.b[p0:p1], own_out[p0:p1], s_cmp)
+            done = torch.cuda.Event()
+            done.record(s_cmp)
+            s_out.wait_event(done)
+            with torch.cuda.stream(s_out):
+                host[p0:p1].copy_(own_out[p0:p1], non_blocking=True)
         cur.wait_stream(s_out)
         cur.wait_stream(s_cmp)
         self.t += self.dt

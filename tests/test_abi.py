@@ -118,3 +118,27 @@ def test_variable_velocity_host_side_errors(af):
     with pytest.raises(af.AFError):
         af.patch_step_var(acu, 0, work, 1, pair, swirl, 0.2 * dx, dx, dx, stream=0)
     af.patch_step_var(cfg, 0, work, 0, pair, swirl, 0.2 * dx, dx, dx, stream=0)   # nothing to do: OK
+
+
+def test_owned_layout_host_side_errors(af):
+    """af_pack_owned / af_unpack_owned refuse bad arguments on the host."""
+    cfg = af.config(af.ACOUSTICS, af.F32, 32, c=1.0)
+    state, owned = 1 << 20, 2 << 20                   # fake, aligned, never dereferenced
+    af.pack_owned(cfg, 0, state, owned, stream=0)     # nothing to do: OK
+    with pytest.raises(af.AFError) as e:
+        af.pack_owned(cfg, 1, state, state, stream=0)
+    assert e.value.status == 1                        # same array twice
+    with pytest.raises(af.AFError) as e:
+        af.unpack_owned(cfg, 1, None, state, stream=0)
+    assert e.value.status == 1
+    with pytest.raises(af.AFError) as e:
+        af.pack_owned(cfg, 1, state + 8, owned, stream=0)
+    assert e.value.status == 3                        # state not 32-byte aligned
+    with pytest.raises(af.AFError) as e:
+        af.unpack_owned(cfg, 1, owned + 2, state, stream=0)
+    assert e.value.status == 3                        # owned not aligned to float
+    bad = af.config(af.ACOUSTICS, af.F32, 32, c=1.0)
+    bad.ncomp = 1
+    with pytest.raises(af.AFError):
+        af.pack_owned(bad, 1, state, owned, stream=0)
+    assert af.owned_words(32, 3) == 12 * 32 * 32

@@ -467,3 +467,56 @@ def test_bulk_tiles_read_own_ghosts_where_no_neighbour_is_listed(af, prec):
         outs.append(S.unpack_owned(grid, dout.double().cpu().numpy().reshape(st.shape)))
     assert np.array_equal(outs[0], outs[1])
     assert af.step_wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [8, 32])
+def test_pack_and_unpack_owned_match_the_layout(af, prec, n):
+    """af_pack_owned gathers exactly the owned entries (i, j in [0, n) of every
+    plane) into [patch][comp][plane][n][n]; af_unpack_owned scatters them back
+    and leaves the ghost ring and padding untouched.  Bit for bit."""
+    nc, npatch = 3, 5
+    cfg = af.config(af.ACOUSTICS, prec, n, c=1.0)
+    tdt = torch.float64 if prec == 0 else torch.float32
+    lay = S.Layout(n, nc)
+    rng = np.random.default_rng(n)
+    st = torch.from_numpy(rng.normal(size=(npatch, af.patch_words(n, nc)))).to(tdt).cuda()
+    own = torch.empty((npatch, af.owned_words(n, nc)), dtype=tdt, device="cuda")
+    af.pack_owned(cfg, npatch, st, own)
+    torch.cuda.synchronize()
+    lat = lay.lattice(st.cpu().numpy().reshape(npatch, nc, 4, -1))
+    ref = lat[..., S.G:S.G + n, S.G:S.G + n].reshape(npatch, -1)
+    assert np.array_equal(own.cpu().numpy(), ref)
+    back = torch.full_like(st, 3.0)
+    af.unpack_owned(cfg, npatch, own, back)
+    torch.cuda.synchronize()
+    b = back.cpu().numpy().reshape(npatch, nc, 4, -1)
+    blat = lay.lattice(b)
+    assert np.array_equal(blat[..., S.G:S.G + n, S.G:S.G + n], lat[..., S.G:S.G + n, S.G:S.G + n])
+    mask = np.ones(b.shape, bool)
+    lay.lattice(mask)[..., S.G:S.G + n, S.G:S.G + n] = False
+    assert (b[mask] == 3.0).all()
+
+
+@pytest.mark.parametrize("bands", [1, 5, 16])
+def test_host_owned_step_matches_device_step(af, bands):
+    """UniformRun.step_host_owned (compact owned state in pinned host memory,
+    banded copies, unpack / step / pack on the device) gives the device step's
+    owned entries bit for bit, three steps running."""
+    from paper_2205_07572_gb300.uniform import UniformRun
+    n, px = 16, 8
+    grid = S.UniformGrid(S.Layout(n, 3), px, px)
+    st = S.periodic_state(grid, S.pulse_plus_vortex(), nq=2)
+    cfg = af.config(af.ACOUSTICS, af.F32, n, c=1.0)
+    dev = UniformRun(cfg, px, px, grid.dx, grid.dy, 0.4 * grid.dx, state=st)
+    hrun = UniformRun(cfg, px, px, grid.dx, grid.dy, 0.4 * grid.dx, state=None)
+    own = torch.empty((grid.npatch, af.owned_words(n, 3)), dtype=torch.float32, device="cuda")
+    af.pack_owned(cfg, grid.npatch, dev.a, own)
+    host = own.cpu().pin_memory()
+    for _ in range(3):
+        dev.step()
+        hrun.step_host_owned(host, bands)
+    torch.cuda.synchronize()
+    af.pack_owned(cfg, grid.npatch, dev.a, own)
+    torch.cuda.synchronize()
+    assert np.array_equal(host.numpy(), own.cpu().numpy())
