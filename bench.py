@@ -682,10 +682,25 @@ def var_velocity_bench(steps: int = 20):
         for prec in ("f32", "f64"):
             cfg = af.config(af.ADVECTION, af.F32 if prec == "f32" else af.F64, n)
             run = UniformRun(cfg, px, px, grid.dx, grid.dy, 0.45 * grid.dx / vmax, state=st, field=field, lo=lo)
+            stream = torch.cuda.current_stream()
+            # the default tiling or one n x n tile per patch (bulk-staged): the faster
+            cands = sorted({af.default_tiling(cfg), [t[:2] for t in af.step_tilings()].index((n, n))})
+            tmeas = {}
+            for kt in cands:
+                run.set_tiling(kt)
+                for _ in range(2):
+                    run.step()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(3):
+                    run.step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tmeas[kt] = e0.elapsed_time(e1) / 3
+            run.set_tiling(min(tmeas, key=tmeas.get))
             for _ in range(3):
                 run.step()
             torch.cuda.synchronize()
-            stream = torch.cuda.current_stream()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             k = steps if prec == "f32" else max(3, steps // 4)
             e0.record(stream)
@@ -697,7 +712,9 @@ def var_velocity_bench(steps: int = 20):
             cells = px * px * n * n
             bpc = 8 * (4 if prec == "f32" else 8)
             rates[f"{name}_{prec}"] = {"value": cells / (ms * 1e-3), "unit": "cell updates/s", "ms_per_step": ms,
-                                       "achieved_gbs": cells * bpc / (ms * 1e-3) / 1e9, "cells": cells}
+                                       "achieved_gbs": cells * bpc / (ms * 1e-3) / 1e9, "cells": cells,
+                                       "tiling": af.step_tilings()[run.tiling],
+                                       "tried_ms": {str(af.step_tilings()[k]): round(v, 4) for k, v in tmeas.items()}}
     out["rates_4096x4096"] = rates
     return out
 

@@ -985,7 +985,7 @@ af_status launch_step(int k, const StepArgs<T> &A, const typename WeightsOf<T, E
 // Reads (and, if reset, clears) this translation unit's g_wait_timeouts;
 // each translation unit that instantiates step kernels exports it under its
 // own name (af_step_f32.cu, af_step_f64.cu, af_step_f32_n16.cu,
-// af_step_f32_n32.cu).
+// af_step_f32_n32.cu, af_step_var.cu).
 static inline af_status wait_timeouts_here(unsigned int *count, bool reset) {
     unsigned int v = 0;
     if (cudaMemcpyFromSymbol(&v, dev::g_wait_timeouts, sizeof(v)) != cudaSuccess) return AF_ERR_CUDA;
@@ -1000,6 +1000,7 @@ af_status wait_timeouts_f32(unsigned int *count, bool reset);
 af_status wait_timeouts_f64(unsigned int *count, bool reset);
 af_status wait_timeouts_f32_n16(unsigned int *count, bool reset);
 af_status wait_timeouts_f32_n32(unsigned int *count, bool reset);
+af_status wait_timeouts_var(unsigned int *count, bool reset);
 
 // Instantiated once each, in af_step_f32.cu and af_step_f64.cu.
 extern template af_status launch_step<float, AF_ACOUSTICS>(int, const StepArgs<float> &,

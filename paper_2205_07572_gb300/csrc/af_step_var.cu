@@ -128,15 +128,22 @@ __global__ void __launch_bounds__(NT) step_var_kernel(const __grid_constant__ Va
     using Gm = Geo<TMX, TMY>;
     constexpr int WX = Gm::WX, WSZ = Gm::WSZ, TX = Gm::TX, TSZ = Gm::TSZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Sin = reinterpret_cast<T *>(smem_raw);
-    T *ST = Sin + kPlanes * WSZ;  // [node type][half, full][TSZ]
+    T *const Sbase = reinterpret_cast<T *>(smem_raw);
+    T *const Sin = Sbase + win_off<T, WX>();
+    T *ST = Sbase + kPlanes * WSZ;  // [node type][half, full][TSZ]
     const StepArgs<T> &A = V.s;
     const af_work wk = A.work[blockIdx.x];
     if (wk.x1 - wk.x0 > TMX || wk.y1 - wk.y0 > TMY) return;
-    stage_issue<T, NT, WX, WSZ>(A, wk, Sin);
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
+    const bool bulk = bulk_tile<T, WX>(A, wk);
+    if (bulk) {  // bulk (TMA) copies of the window rows, as in the constant-velocity step
+        __shared__ __align__(8) uint64_t bar;
+        if (!stage_bulk<T, NT, WX, WSZ, 1>(A, wk, Sin, &bar)) return;  // counted in g_wait_timeouts
+    } else {
+        stage_issue<T, NT, WX, WSZ>(A, wk, Sin);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+    }
     if (wk.flags & 1) {
         stage_copy_out<T, NT, WX, WSZ>(A, wk, Sin);
         __syncthreads();
@@ -255,6 +262,7 @@ __global__ void __launch_bounds__(NT) step_var_kernel(const __grid_constant__ Va
             if (inx && j == n - 1) fr_p[3 * n + i] += dtl * (double)gt;
         }
     }
+    if (bulk) write_ghost_columns<T, NT, WX, WSZ, 1>(A, wk, Sin);
 }
 
 template <typename T, int FIELD, int NT, int TMX, int TMY>
@@ -361,3 +369,7 @@ extern "C" af_status af_patch_step_var(const af_config *cfg, int32_t tiling_inde
     return vel->field == AF_FIELD_SOLID_BODY ? dev::launch_var<float, AF_FIELD_SOLID_BODY>(k, V, nwork, s)
                                              : dev::launch_var<float, AF_FIELD_SWIRL>(k, V, nwork, s);
 }
+
+namespace af {
+af_status wait_timeouts_var(unsigned int *count, bool reset) { return wait_timeouts_here(count, reset); }
+}  // namespace af
