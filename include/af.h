@@ -230,6 +230,17 @@ af_status af_patch_step_pair(const af_config *cfg, int32_t tiling, int32_t nwork
 af_status af_pack_owned(const af_config *cfg, int32_t npatch, const void *d_state, void *d_owned, void *stream);
 af_status af_unpack_owned(const af_config *cfg, int32_t npatch, const void *d_owned, void *d_state, void *stream);
 
+/* Measurement probe (no counterpart in the paper): `blocks` CTAs of
+ * af_fma_probe_threads() / 8 threads each run 8 independent fused
+ * multiply-add chains of `iters` steps in precision `prec` (af_precision) and
+ * store one value per thread to d_sink (device, blocks * 256 elements of that
+ * precision, aligned to its size).  Flops per call:
+ * 2 * 8 * iters * blocks * 256; timing the call on `stream` gives the GPU's
+ * FMA rate, the ALU roof of the step kernels.  AF_ERR_ARG on a bad precision,
+ * blocks < 1, iters < 1 or NULL d_sink; AF_ERR_LAYOUT if d_sink is misaligned. */
+int32_t af_fma_probe_threads(void);
+af_status af_fma_throughput(int32_t prec, int32_t blocks, int32_t iters, void *d_sink, void *stream);
+
 /* Tiles that span a patch's interior columns are staged by bulk (TMA) copies
  * whose completion the kernel awaits for at most about a second (2^31 SM
  * cycles).  A tile whose wait gives up waits once more with the same limit

@@ -483,3 +483,15 @@ def unpack_owned(cfg: Config, npatch: int, owned, state, stream=None) -> None:
     """af_unpack_owned: compact owned entries -> lattice state (ghosts untouched)."""
     _check(lib().af_unpack_owned(C.byref(cfg), int(npatch), ptr(owned), ptr(state), stream_handle(stream)),
            "af_unpack_owned")
+
+
+_EXTRA += [("af_fma_probe_threads", C.c_int32, []),
+           ("af_fma_throughput", C.c_int, [C.c_int32, C.c_int32, C.c_int32, _VP, _VP])]
+if _lib is not None:
+    _register_more(_lib)
+
+
+def fma_throughput(prec: int, blocks: int, iters: int, sink, stream=None) -> None:
+    """af_fma_throughput: 2 * 8 * iters * blocks * 256 flops of FMA chains."""
+    _check(lib().af_fma_throughput(int(prec), int(blocks), int(iters), ptr(sink), stream_handle(stream)),
+           "af_fma_throughput")

@@ -520,3 +520,26 @@ def test_host_owned_step_matches_device_step(af, bands):
     af.pack_owned(cfg, grid.npatch, dev.a, own)
     torch.cuda.synchronize()
     assert np.array_equal(host.numpy(), own.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fma_probe_computes_its_chains(af, prec):
+    """af_fma_throughput (the ALU-roof probe) runs the chains it claims: every
+    thread's stored sum equals the eight recurrences a <- a * m + c."""
+    blocks, iters = 3, 50
+    tdt, ndt = (torch.float64, np.float64) if prec == 0 else (torch.float32, np.float32)
+    sink = torch.zeros(blocks * 256, dtype=tdt, device="cuda")
+    af.fma_throughput(prec, blocks, iters, sink)
+    torch.cuda.synchronize()
+    got = sink.cpu().numpy().reshape(blocks, 256)
+    t = np.arange(256)
+    m, c = ndt(0.9999999), ndt(1e-7)
+    ref = np.zeros(256, np.float64)
+    for k in range(8):
+        a = (ndt(1) + (t + k).astype(ndt) * ndt(1e-7)).astype(np.float64)
+        for _ in range(iters):
+            a = a * float(m) + float(c)
+        ref += a
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert np.allclose(got, ref[None, :], rtol=tol, atol=0)
+    assert af.lib().af_fma_probe_threads() == 256 * 8
