@@ -394,3 +394,31 @@ def test_amr_run_with_bulk_staged_tiles_matches_oracle(af, prec):
     torch.cuda.synchronize()
     _compare(Fo, run, n, 3, TOL[prec] * (10 if prec else 1))
     assert af.step_wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("graphs", [False, True])
+def test_amr_run_with_a_second_tiling_for_extended_leaves(af, prec, graphs):
+    """Leaves with eight same-level neighbours in one 16 x 16 tile each
+    (bulk-staged), leaves that advance their ghost layer in one 18 x 18 tile
+    (ext_tiling: a second work list, a second launch per substep); eager and
+    graph-replayed subcycled coarse steps agree with the oracle."""
+    from paper_2205_07572_gb300.amr import AMRRun
+    n, lmax = 16, 3
+    leaves = _sorted(S.balanced_forest(1, 2, lmax, lambda l, x, y: x == y and x < 2))
+    st = S.forest_state(n, 3, 1, lmax, leaves, S.pulse_plus_vortex(), nq=3)
+    if prec:
+        st = st.astype(np.float32).astype(np.float64)
+    dx0 = 1.0 / n
+    dt0 = 0.4 * dx0
+    Fo = OracleForest(1, n, 1, lmax, leaves, (0, 0), (1, 1), dt0, 1.0, 0.5, 1.0, state=st)
+    Fo.sync_fill((1 << (lmax + 1)) - 1)
+    tl = [t[:2] for t in af.step_tilings()]
+    run = AMRRun(af.config(1, prec, n, 1.0, 0.5, 1.0), 1, lmax, leaves, st, (0, 0), (1, 1), dt0,
+                 tiling=tl.index((16, 16)), ext_tiling=tl.index((18, 18)), graphs=graphs)
+    assert len(run.work_groups) == 2 and all(nw > 0 for _, nw, _, _ in run.work_groups)
+    for _ in range(4):
+        Fo.coarse_step()
+        run.coarse_step()
+    torch.cuda.synchronize()
+    _compare(Fo, run, n, 3, TOL[prec] * (10 if prec else 1))
