@@ -204,7 +204,7 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
                        "tuned_ms": {str(tilings[k]): round(v, 4) for k, v in table.items()}}}
 
 
-def run_e2e(prec: str, steps: int, warmup: int, tiling=None, bands: int = 16, layout: str = "owned"):
+def run_e2e(prec: str, steps: int, warmup: int, tiling=None, bands: int = 32, layout: str = "owned"):
     """Same step through the public API with the state kept in pinned HOST
     memory: every step copies it host->device, runs af_patch_step, and copies
     the result back (host<->device copies inside the timed region), in bands

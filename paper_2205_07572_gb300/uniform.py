@@ -128,10 +128,12 @@ class UniformRun:
         """step_host for a state kept in host memory in the compact owned
         layout ([npatch, ncomp * 4 * n * n], af_pack_owned's): only the
         patches' own degrees of freedom cross the host link, 74 % of the
-        lattice words for 32 x 32 patches.  A band is copied in and unpacked
-        into the device state, advanced once it and its neighbouring bands
-        are there, packed and copied back; ghost rings stay on the device and
-        are never needed (every patch reads its halo from its neighbours)."""
+        lattice words for 32 x 32 patches.  The bands are copied in back to
+        back on one stream; on the compute stream each is unpacked into the
+        device state once it has arrived, advanced once it and its
+        neighbouring bands are unpacked, and packed; a third stream copies it
+        back.  Ghost rings stay on the device and are never needed (every
+        patch reads its halo from its neighbours)."""
         import torch
         if self.field is not None:
             raise ValueError("step_host_owned runs constant-velocity steps")
@@ -147,17 +149,20 @@ class UniformRun:
         for st in self._streams:
             st.wait_stream(cur)
         uploaded = []
-        for p0, p1, _, _ in self._bands:
+        for p0, p1, _, _ in self._bands:  # copies only: the link stays busy
             with torch.cuda.stream(s_in):
                 own_in[p0:p1].copy_(host[p0:p1], non_blocking=True)
-            af.unpack_owned(self.cfg, p1 - p0, own_in[p0:p1], self.a[p0:p1], s_in)
-            ev = torch.cuda.Event()
-            ev.record(s_in)
+                ev = torch.cuda.Event()
+                ev.record(s_in)
             uploaded.append(ev)
         order = list(range(1, bands)) + [0]
+        unpacked = set()
         for b in order:
-            for nb in {(b - 1) % bands, b, (b + 1) % bands}:
+            for nb in sorted({(b - 1) % bands, b, (b + 1) % bands} - unpacked):
+                q0, q1 = self._bands[nb][:2]
                 s_cmp.wait_event(uploaded[nb])
+                af.unpack_owned(self.cfg, q1 - q0, own_in[q0:q1], self.a[q0:q1], s_cmp)
+                unpacked.add(nb)
             p0, p1, work, nwork = self._bands[b]
             af.patch_step(self.cfg, work, nwork, self.a, self.b, self.dt, self.dx, self.dy, self.freg, s_cmp,
                           tiling=self.tiling)
