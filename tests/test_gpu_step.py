@@ -168,9 +168,10 @@ def test_config1_full_run_matches_oracle_and_exact(af):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_config2_full_size_two_steps_match_oracle(af, prec):
     """2-D acoustics, 512 x 512 cells as 16 x 16 patches of 32 x 32 with two
-    ghost layers, Gaussian pulse + stationary vortex, CFL 0.4: two steps at
-    full size, in the launch configuration the benchmark times, match the
-    oracle on every interior DOF."""
+    ghost layers, Gaussian pulse + stationary vortex, CFL 0.4 (the literal
+    configuration; the benchmark's 4096^2 scale-up is checked on sampled
+    patches below): two steps in the default tiling match the oracle on every
+    interior DOF."""
     from paper_2205_07572_gb300.uniform import UniformRun
     n, P = 32, 16
     grid = S.UniformGrid(S.Layout(n, 3), P, P)
@@ -543,3 +544,58 @@ def test_fma_probe_computes_its_chains(af, prec):
     tol = 1e-12 if prec == 0 else 1e-5
     assert np.allclose(got, ref[None, :], rtol=tol, atol=0)
     assert af.lib().af_fma_probe_threads() == 256 * 8
+
+
+@pytest.fixture(scope="module")
+def bench_workload():
+    """The benchmark's workload: 4096 x 4096 cells as 128 x 128 periodic
+    patches of 32 x 32, Gaussian pulse + stationary vortex (FP64 state)."""
+    grid = S.UniformGrid(S.Layout(32, 3), 128, 128)
+    return grid, S.periodic_state(grid, S.pulse_plus_vortex(), nq=2, dtype=np.float64)
+
+
+def _patch_with_neighbour_halo(grid, lat, p):
+    """Lattice of patch p with every ghost entry taken from the owned entry of
+    the same global node or cell (periodic), as the step's halo reads it."""
+    n, g, w = grid.layout.n, S.G, grid.layout.w
+    ix, iy = p % grid.px, p // grid.px
+    gx = (ix * n + np.arange(w) - g) % (grid.px * n)
+    gy = (iy * n + np.arange(w) - g) % (grid.py * n)
+    q = (gy[:, None] // n) * grid.px + gx[None, :] // n
+    return lat[q, :, :, (gy % n)[:, None] + g, (gx % n)[None, :] + g].transpose(2, 3, 0, 1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bench_workload_full_size_sampled_patches_match_oracle(af, bench_workload, prec):
+    """The benchmark's workload at full size, one step in the launch
+    configuration it times (the 32 x 8-cell, 128-thread tiling: bulk-staged
+    tiles, packed FP32x2 node evaluation, whole-row writes): sampled patches
+    -- corners, edges, the pulse, the vortex -- match the oracle's single-patch
+    step on the same input, every owned DOF, normwise against each
+    component's largest value on the grid."""
+    from paper_2205_07572_gb300.uniform import UniformRun
+    grid, st64 = bench_workload
+    n, P, nc = 32, 128, 3
+    st = st64 if prec == 0 else st64.astype(np.float32)
+    dt = 0.4 * grid.dx
+    cfg = af.config(af.ACOUSTICS, prec, n, c=1.0)
+    k = af.step_tilings().index((32, 8, 128, 0))
+    run = UniformRun(cfg, P, P, grid.dx, grid.dy, dt, state=st, tiling=k)
+    af.step_wait_timeouts(reset=True)
+    run.step()
+    torch.cuda.synchronize()
+    samples = [0, P - 1, P * (P - 1), P * P - 1, P * 64 + 64, P * 64 + 20, P * 30 + 97, 12345]
+    got = run.state[torch.tensor(samples, device="cuda")].double().cpu().numpy().reshape(len(samples), nc, 4, -1)
+    lay = S.Layout(n, nc)
+    lat = lay.lattice(st.reshape(P * P, nc, 4, -1).astype(np.float64))
+    scale = [np.abs(lat[:, c, :, S.G:S.G + n, S.G:S.G + n]).max() for c in range(nc)]
+    cf = O.cfg(1, n, grid.dx, grid.dy, dt, c=1.0)
+    for i, p in enumerate(samples):
+        patch = np.zeros((nc, 4, lay.plane))
+        lay.lattice(patch)[...] = _patch_with_neighbour_halo(grid, lat, p)
+        ref = lay.lattice(O.step_patch(cf, patch))[..., S.G:S.G + n, S.G:S.G + n]
+        g = lay.lattice(got[i])[..., S.G:S.G + n, S.G:S.G + n]
+        for c in range(nc):
+            err = np.abs(g[c] - ref[c]).max() / scale[c]
+            assert err < TOL[prec], (p, c, err)
+    assert af.step_wait_timeouts() == 0
