@@ -422,3 +422,31 @@ def test_amr_run_with_a_second_tiling_for_extended_leaves(af, prec, graphs):
         run.coarse_step()
     torch.cuda.synchronize()
     _compare(Fo, run, n, 3, TOL[prec] * (10 if prec else 1))
+
+
+@pytest.mark.parametrize("case", ["advection_levels2-6", "acoustics_levels3-7"])
+def test_bench_amr_workloads_conserve_mass_at_full_size(af, case):
+    """The benchmark's adaptive workloads at full size (736 and 4944 leaves of
+    16 x 16 cells, forests from the method's own tagging and regridding), in
+    the launch configuration it times (batched, graph-replayed, 16 x 16
+    tiles): FP64 mass is conserved to round-off over four coarse steps with
+    subcycling, the conservative fix and the planned ghost exchange, on
+    these periodic domains (Section 3.2)."""
+    import bench
+    from paper_2205_07572_gb300.amr import AMRRun
+    leaves, st = bench.amr_initial(case)
+    c = bench.AMR_CASES[case]
+    n = bench.AMR_N
+    dx0 = (c["hi"][0] - c["lo"][0]) / (c["B"] * n)
+    dt0 = bench.CFL * dx0 / (max(abs(c["a"]), abs(c["b"])) if c["eq"] == 0 else 1.0)
+    k = [t[:3] for t in af.step_tilings()].index((16, 16, 128))
+    run = AMRRun(af.config(c["eq"], af.F64, n, c["a"], c["b"], 1.0), c["B"], c["lmax"], leaves, st, c["lo"],
+                 c["hi"], dt0, graphs=True, tiling=k)
+    assert run.forest.nleaf == len(leaves) and len(run.forest.levels) >= 3
+    m0 = run.mass()
+    for _ in range(4):
+        run.coarse_step()
+    torch.cuda.synchronize()
+    m1 = run.mass()
+    assert np.abs(m1 - m0).max() < 1e-12 * max(1.0, np.abs(m0).max()), (m0, m1)
+    assert af.step_wait_timeouts() == 0
