@@ -1,14 +1,17 @@
 // Device side of af_patch_step: one Active Flux time step (Section 2 of
-// arXiv 2205.07572) on GB300 (sm_103a).  Included by af_step_f32.cu and
-// af_step_f64.cu, which instantiate the launchers for one precision each.
+// arXiv 2205.07572) on GB300 (sm_103a).  Included by af_step_f32.cu,
+// af_step_f64.cu, af_step_f32_n16.cu and af_step_f32_n32.cu, which
+// instantiate the launchers (per precision; FP32 also per patch size).
 //
 // One CTA advances one tile (<= TMX x TMY cells) of one patch:
 //   stage  - the tile's degrees of freedom plus a one-cell halo are copied to
-//            shared memory with asynchronous copies; halo entries in a
-//            direction with a same-level neighbour are read straight from that
-//            neighbour's interior (the same-level ghost copy of Section 3.1
-//            fused into the load), other directions from the patch's own
-//            ghost ring;
+//            shared memory: a tile spanning the patch's interior columns by
+//            one bulk (TMA) copy of its window rows per plane completing on
+//            an mbarrier, other tiles element by element with cp.async; halo
+//            entries in a direction with a same-level neighbour are read
+//            straight from that neighbour's interior (the same-level ghost
+//            copy of Section 3.1 fused into the load), other directions from
+//            the patch's own ghost ring;
 //   nodes  - one thread per node-cell evolves the corner, left-edge midpoint
 //            and bottom-edge midpoint of its cell to t^{n+1/2} and t^{n+1}
 //            (Eq. advection-update / Eq. ERFormula) as constant-weight
@@ -17,7 +20,9 @@
 //            accumulated together by packed FP32x2 multiply-adds);
 //   update - one thread per cell forms the four face fluxes by the space-time
 //            Simpson rule (Eq. Simpson-2d: f is linear, so the 3 x 3 sum is
-//            f((T_lo + 4 T_mid + T_hi) / 36)) and applies Eq. 2dfv.
+//            f((T_lo + 4 T_mid + T_hi) / 36)) and applies Eq. 2dfv; a
+//            bulk-staged tile also writes its rows' ghost columns, so whole
+//            lattice rows go out.
 // No tensor cores: the stencil is not a dense contraction.
 #pragma once
 
