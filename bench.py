@@ -832,9 +832,12 @@ def main():
             return
         import oracle as O
         O.build()
+        # under torchrun (OMP_NUM_THREADS=1 per rank) rank 0 runs alone: it
+        # takes the host's cores, as the single-process run does
+        nt = max(O.max_threads(), os.cpu_count() or 1) if world > 1 else None
         per = []
         for k in range(warm + args.steps):
-            r = oracle_sample(1, budget_s=60.0)
+            r = oracle_sample(1, budget_s=60.0, nthreads=nt)
             if k >= warm:
                 per.append(r)
         v = statistics.median(x["value"] for x in per)
