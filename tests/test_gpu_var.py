@@ -159,3 +159,56 @@ def test_subcycled_swirl_constant_state_paper_configuration(af):
     g = lay.lattice(run.current().double().cpu().numpy().reshape(run.forest.nleaf, 1, 4, -1))
     err = np.abs(g[:, 0, 0, 2:2 + n, 2:2 + n] - 1.0).max()
     assert err < 2e-11, err
+
+
+def _patch_with_neighbour_halo(grid, lat, p):
+    """Lattice of patch p with every ghost entry taken from the owned entry of
+    the same global node or cell (periodic), as the step's halo reads it."""
+    n, g, w = grid.layout.n, S.G, grid.layout.w
+    ix, iy = p % grid.px, p // grid.px
+    gx = (ix * n + np.arange(w) - g) % (grid.px * n)
+    gy = (iy * n + np.arange(w) - g) % (grid.py * n)
+    q = (gy[:, None] // n) * grid.px + gx[None, :] // n
+    return lat[q, :, :, (gy % n)[:, None] + g, (gx % n)[None, :] + g].transpose(2, 3, 0, 1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("field", [0, 1])
+def test_bench_workload_full_size_sampled_patches_match_oracle(af, field, prec):
+    """The benchmark's variable-velocity workloads at full size (4096^2 cells
+    as 256 x 256 patches of 16 x 16; swirl on the unit square, solid body on
+    [-1, 1]^2; dt = 0.45 dx / max speed), one step from t = 0 in both tilings
+    the benchmark chooses between (18 x 18 element-wise staged, 16 x 16 bulk
+    staged): sampled patches match the oracle's single-patch step, every
+    owned DOF."""
+    from paper_2205_07572_gb300.uniform import UniformRun
+    n, P = 16, 256
+    lo, hi = ((0.0, 0.0), (1.0, 1.0)) if field == 1 else ((-1.0, -1.0), (1.0, 1.0))
+    f = S.swirl_gaussians if field == 1 else S.gaussian(0.3, 0.2, 0.1)
+    vmax = 1.0 if field == 1 else np.pi * 1.01
+    grid = S.UniformGrid(S.Layout(n, 1), P, P, lo, hi)
+    st = S.periodic_state(grid, [f], nq=2, dtype=np.float32 if prec else np.float64)
+    dt = 0.45 * grid.dx / vmax
+    cfg = af.config(af.ADVECTION, prec, n)
+    lay = S.Layout(n, 1)
+    lat = lay.lattice(st.reshape(P * P, 1, 4, -1).astype(np.float64))
+    scale = np.abs(lat[:, 0, :, S.G:S.G + n, S.G:S.G + n]).max()
+    samples = [0, P - 1, P * (P - 1), P * P - 1, P * 128 + 128, P * 77 + 200, 40000]
+    tl = [t[:3] for t in af.step_tilings()]
+    for k in (tl.index((18, 18, 256)), tl.index((16, 16, 128))):
+        run = UniformRun(cfg, P, P, grid.dx, grid.dy, dt, state=st, tiling=k, field=field, lo=lo)
+        af.step_wait_timeouts(reset=True)
+        run.step()
+        torch.cuda.synchronize()
+        got = run.state[torch.tensor(samples, device="cuda")].double().cpu().numpy().reshape(len(samples), 1, 4, -1)
+        for i, p in enumerate(samples):
+            ix, iy = p % P, p // P
+            vc = O.VarCfg(n, field, grid.dx, grid.dy, dt, lo[0] + ix * n * grid.dx, lo[1] + iy * n * grid.dy, 0.0)
+            patch = np.zeros((1, 4, lay.plane))
+            lay.lattice(patch)[...] = _patch_with_neighbour_halo(grid, lat, p)
+            ref = lay.lattice(O.step_patch_var(vc, patch))[..., S.G:S.G + n, S.G:S.G + n]
+            g = lay.lattice(got[i])[..., S.G:S.G + n, S.G:S.G + n]
+            err = np.abs(g - ref).max() / scale
+            assert err < TOL[prec], (k, p, err)
+        assert af.step_wait_timeouts() == 0
+        del run
