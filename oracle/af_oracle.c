@@ -1005,7 +1005,10 @@ void orc_reflux_amr(int n, int ncomp, int nleaf, const int32_t *level, const int
  * centred difference quotient |Q_{i+1,j} - Q_{i-1,j}| / (2 dx) or
  * |Q_{i,j+1} - Q_{i,j-1}| / (2 dy) over cells whose two neighbours are both
  * interior (Section 4.4).  tag = 1 if indicator >= refine_thr, -1 if
- * indicator < coarsen_thr, else 0.                                           */
+ * indicator < coarsen_thr, else 0.
+ * Pinned by: the indicators of linear data (range and slope) and the exact
+ * centred quotient 2x of quadratic data; the threshold rule at its boundaries
+ * (test_oracle_tag_regrid.py).                                                */
 void orc_tag(int n, int ncomp, int nleaf, const int32_t *level, const double *state, int comp, int kind,
              double dx0, double dy0, double refine_thr, double coarsen_thr, int8_t *tags, double *ind) {
     lay_t L = lay_make(n, ncomp);

@@ -145,7 +145,9 @@ class OracleForest:
 def new_leaves(leaves, tags, B: int, lmin: int, lmax: int):
     """Refine leaves tagged 1 (below lmax), coarsen complete families of four
     leaves tagged -1 (above lmin) unless that breaks the 2:1 balance, then
-    split leaves until the forest is 2:1 balanced across faces and corners."""
+    split leaves until the forest is 2:1 balanced across faces and corners.
+    Pinned by brute-force invariants on random forests (tiling, balance,
+    refinement and coarsening rules; test_oracle_tag_regrid.py)."""
     cur = set(leaves)
     tag = {leaf: int(t) for leaf, t in zip(leaves, tags)}
     refine = {leaf for leaf in leaves if tag[leaf] == 1 and leaf[0] < lmax}
