@@ -329,7 +329,10 @@ static void phys_flux(const orc_cfg *cf, int dir, const double *q, double *f) {
  * `out` receives a copy of `in` with the updated entries replaced.  If freg is
  * not NULL, dt * F (resp. dt * G) on the four patch faces is ADDED to it:
  * freg[side][comp][k], side 0 = x-line 0, 1 = x-line N, 2 = y-line 0,
- * 3 = y-line N, k in [0, N) (Section 3.2, conservative fix).                */
+ * 3 = y-line N, k in [0, N) (Section 3.2, conservative fix).
+ * Pinned by: the full step exact for Q2 data without x^2 y^2 (P3); constant
+ * states and the rotating state u = w(-y, x) preserved (P6); mass conserved
+ * (P7); third-order convergence and the paper's Table 1 (P10, P11).        */
 void orc_step_patch(const orc_cfg *cf, const double *in, double *out, double *freg) {
     lay_t L = lay_make(cf->n, cf->ncomp);
     const int n = cf->n, nc = cf->ncomp;
@@ -656,7 +659,9 @@ void orc_run_uniform_var(orc_var *v, int px, int py, double lo_x, double lo_y, i
 /* --------------------------------------------------------- Section 3.1 (3.)
  * Same-level ghost fill on a px x py array of patches tiling a periodic box:
  * every ghost entry (lattice entries outside [g, g+N)^2 of every plane) is a
- * copy of the entry owned by the neighbouring patch at the same position.   */
+ * copy of the entry owned by the neighbouring patch at the same position.
+ * Pinned by: ghost entries equal the analytic values at the wrapped
+ * positions; one patch equals many (P9).                                   */
 void orc_fill_periodic(int n, int ncomp, int px, int py, double *state) {
     lay_t L = lay_make(n, ncomp);
     long pw = lay_patch_words(&L);
@@ -681,7 +686,9 @@ void orc_fill_periodic(int n, int ncomp, int px, int py, double *state) {
 }
 
 /* Uniform periodic run: nsteps x (fill ghosts, step every patch).  `tmp` has
- * the size of `state`.  OpenMP over patches with `nthreads` threads.        */
+ * the size of `state`.  OpenMP over patches with `nthreads` threads.
+ * Pinned by: one patch equals many (P9); mass conserved (P7); convergence
+ * and the paper's Table 1 (P10, P11).                                      */
 void orc_run_uniform(const orc_cfg *cf, int px, int py, int nsteps, double *state, double *tmp, int nthreads) {
     lay_t L = lay_make(cf->n, cf->ncomp);
     long pw = lay_patch_words(&L);
@@ -893,7 +900,9 @@ static int entry_owner(const forest_t *F, int plane, long x, long y) {
  * before: entries owned by finer leaves, then by same-level leaves, then by
  * coarser leaves; so a coarse reconstruction used for interpolation already
  * carries the fine values on its coarse-fine faces.  Results are written to
- * `out` (a copy of `in` on entry).                                          */
+ * `out` (a copy of `in` on entry).
+ * Pinned by: coarse-to-fine interpolation exact for biquadratic data and
+ * conservative (P8); a same-level forest equals the uniform run (P9).      */
 void orc_fill_amr(int n, int ncomp, int nleaf, const int32_t *level, const int32_t *ix, const int32_t *iy,
                   int B, int lmax, uint32_t dst_levels, uint32_t src_levels, int same_only, const double *in,
                   double *out) {
@@ -941,7 +950,9 @@ void orc_fill_amr(int n, int ncomp, int nleaf, const int32_t *level, const int32
  * where R = sum over the steps since the last synchronisation of dt * F
  * (registers filled by orc_step_patch; the fine one spans two fine steps and
  * two fine faces), h_C the coarse mesh width normal to the face.  Consumed
- * register entries (both sides) are reset to zero.                        */
+ * register entries (both sides) are reset to zero.
+ * Pinned by: mass conserved to round-off across coarse-fine faces with
+ * subcycling, and not without the fix (P7).                                */
 void orc_reflux_amr(int n, int ncomp, int nleaf, const int32_t *level, const int32_t *ix, const int32_t *iy,
                     int B, int lmax, uint32_t sync_levels, double dx0, double dy0, double *freg, double *state) {
     forest_t F;
@@ -1042,7 +1053,8 @@ void orc_tag(int n, int ncomp, int nleaf, const int32_t *level, const double *st
 }
 
 /* Total of every component: sum over patches and interior cells of
- * Q_{i,j} dx_l dy_l (the conserved quantity of Eq. 2dfv). */
+ * Q_{i,j} dx_l dy_l (the conserved quantity of Eq. 2dfv).
+ * Pinned by: its definition, used by the P7 conservation pins.            */
 void orc_mass(int n, int ncomp, int nleaf, const int32_t *level, const double *state, double dx0, double dy0,
               double *out) {
     lay_t L = lay_make(n, ncomp);
@@ -1063,7 +1075,9 @@ void orc_mass(int n, int ncomp, int nleaf, const int32_t *level, const double *s
  * that is also a leaf of the old one is copied; every other new leaf gets its
  * interior-owned entries from the old leaf covering each entry (coarse ->
  * fine interpolation if that leaf is coarser, fine -> coarse averaging if it
- * is finer).  Ghost entries of new leaves are left for the next exchange.  */
+ * is finer).  Ghost entries of new leaves are left for the next exchange.
+ * Pinned by: refine-then-coarsen returns the original averages, and the
+ * nodes shared with the old leaf are copied exactly (P8).                  */
 void orc_transfer(int n, int ncomp, int B, int lmax, int nold, const int32_t *olevel, const int32_t *oix,
                   const int32_t *oiy, const double *old_state, int nnew, const int32_t *nlevel, const int32_t *nix,
                   const int32_t *niy, double *new_state) {
