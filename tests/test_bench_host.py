@@ -1,0 +1,60 @@
+"""CPU checks of the benchmark's host logic: the clock sampler's parsing of
+nvidia-smi output (median clock, throttle reasons), the roofline peak's
+source (the measured HBM bandwidth, else the stated fallback), and the flop
+count per acoustic cell update."""
+import json
+import os
+import stat
+import time
+
+import pytest
+
+import bench
+
+
+def _fake_smi(tmp_path, lines):
+    """An executable `nvidia-smi` that prints `lines` once, then idles."""
+    script = tmp_path / "nvidia-smi"
+    body = "\n".join(f"echo '{ln}'" for ln in lines)
+    script.write_text(f"#!/bin/sh\n{body}\nexec sleep 30\n")
+    script.chmod(script.stat().st_mode | stat.S_IEXEC)
+    return str(tmp_path)
+
+
+def test_clock_sampler_parses_clocks_and_reasons(tmp_path, monkeypatch):
+    lines = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1950, 2070, 1350.2, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2070, 1200.0, 0x8, Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, lines) + os.pathsep + os.environ["PATH"])
+    ck = bench.ClockSampler(0)
+    time.sleep(0.5)
+    out = ck.stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2010.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    out = bench.ClockSampler(0).stop()
+    assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_roofline_peak_source(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6788.3, "bf16_tflops": 1886.0}))
+    assert bench.measured_peaks() == (6788.3, "measured")
+    (tmp_path / "MEASURED_PEAKS.json").write_text("not json")
+    assert bench.measured_peaks() == (6800.0, "fallback")
+
+
+def test_flop_count_per_acoustic_cell_update():
+    """3 components x 76 orbit-sum adds, 230 multiply-adds of the three nodes'
+    two time combinations (2 flops each), 4 Simpson face sums x 3 components
+    (a multiply-add and an add), 8 flux scalings, and per component two
+    differences and two multiply-adds in the update."""
+    assert bench.ACOUSTIC_FLOP_PER_CELL == 3 * 76 + 230 * 2 + 4 * 3 * 3 + 8 + 3 * (2 + 2 * 2) == 750
