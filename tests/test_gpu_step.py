@@ -291,7 +291,8 @@ def _resplit(work, n, cuts):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("eq,n,k", [(1, 32, 3), (0, 32, 3), (1, 32, 0), (1, 16, 4), (0, 16, 4), (1, 32, 5), (0, 32, 5)])
+@pytest.mark.parametrize("eq,n,k", [(1, 32, 3), (0, 32, 3), (1, 32, 0), (1, 16, 4), (0, 16, 4), (1, 32, 5), (0, 32, 5),
+                                    (1, 18, 6), (0, 18, 7), (1, 10, 8)])
 # tiling 5 is the persistent (pipelined) one
 def test_bulk_staging_equals_elementwise_staging(af, prec, eq, n, k):
     """Full-width tiles whose window is staged by bulk (TMA) copies plus the
