@@ -142,3 +142,18 @@ def test_owned_layout_host_side_errors(af):
     with pytest.raises(af.AFError):
         af.pack_owned(bad, 1, state, owned, stream=0)
     assert af.owned_words(32, 3) == 12 * 32 * 32
+
+
+def test_probe_and_counter_host_side_errors(af):
+    """af_fma_throughput and af_step_wait_timeouts refuse bad arguments on
+    the host, before any device call."""
+    import ctypes
+    L = af.lib()
+    sink = 1 << 20                                     # fake, aligned, never dereferenced
+    assert L.af_fma_throughput(7, 1, 1, ctypes.c_void_p(sink), None) == 1       # unknown precision
+    assert L.af_fma_throughput(af.F32, 0, 1, ctypes.c_void_p(sink), None) == 1  # no blocks
+    assert L.af_fma_throughput(af.F32, 1, 0, ctypes.c_void_p(sink), None) == 1  # no iterations
+    assert L.af_fma_throughput(af.F32, 1, 1, None, None) == 1                   # no sink
+    assert L.af_fma_throughput(af.F64, 1, 1, ctypes.c_void_p(sink + 4), None) == 3  # misaligned FP64 sink
+    assert L.af_step_wait_timeouts(None, 0) == 1
+    assert L.af_fma_probe_threads() == 256 * 8
