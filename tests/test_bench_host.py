@@ -30,7 +30,9 @@ def test_clock_sampler_parses_clocks_and_reasons(tmp_path, monkeypatch):
     ]
     monkeypatch.setenv("PATH", _fake_smi(tmp_path, lines) + os.pathsep + os.environ["PATH"])
     ck = bench.ClockSampler(0)
-    time.sleep(0.5)
+    t0 = time.time()
+    while time.time() - t0 < 10 and open(ck.f.name).read().count("\n") < len(lines):
+        time.sleep(0.05)
     out = ck.stop()
     assert out["samples"] == 3
     assert out["sm_mhz"] == 2010.0 and out["sm_max_mhz"] == 2070.0
