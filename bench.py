@@ -76,15 +76,75 @@ def measured_peaks():
     return hbm, src
 
 
+# ------------------------------------------------------------------- traffic
+PROFILE = os.path.join(ROOT, "profiles", "step_kernel_f32_acoustics_4096x4096.md")
+KERNEL_SOURCES = ["paper_2205_07572_gb300/csrc/af_step_kernels.cuh", "paper_2205_07572_gb300/csrc/af_internal.h",
+                  "paper_2205_07572_gb300/csrc/af_step_f32_n32.cu"]
+
+
+def kernel_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the step kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(tiling: dict, path: str = PROFILE):
+    """DRAM bytes (read + write) per launch of the timed tiling, from the
+    committed ncu summary's `traffic:` record, or None when the summary
+    covers another tiling or the kernel's sources changed since the capture
+    (their hash differs).  Returns (bytes or None, description)."""
+    import re
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None, "no ncu summary"
+    m = re.search(r"traffic: tiling=(\d+)x(\d+)x(\d+) bytes_per_launch=(\d+) source_hash=([0-9a-f]+)", txt)
+    if not m:
+        return None, "no traffic record in the ncu summary"
+    tmx, tmy, nt, nbytes, hsh = int(m[1]), int(m[2]), int(m[3]), int(m[4]), m[5]
+    rel = os.path.relpath(path, ROOT)
+    if (tuple(tiling["tile"]) != (tmx, tmy) or tiling["threads"] != nt or tiling["persistent"]):
+        return None, f"{rel} covers the {tmx}x{tmy}/{nt} tiling, not the timed one"
+    if hsh != kernel_source_hash():
+        return None, f"stale: the kernel sources changed since the capture in {rel}"
+    return float(nbytes), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {rel}"
+
+
 # -------------------------------------------------------------------- clocks
+def smi_device(dev: int) -> str:
+    """nvidia-smi's selector (-i) for CUDA device `dev` of this process.
+    CUDA numbers the devices it can see, so under CUDA_VISIBLE_DEVICES its
+    index is not nvidia-smi's: select by the device's UUID, else by the
+    CUDA_VISIBLE_DEVICES entry the index maps to."""
+    try:
+        import torch
+        u = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    except Exception:
+        u = None
+    if u is not None and str(u):
+        s = str(u)
+        return s if s.startswith(("GPU-", "MIG-")) else "GPU-" + s
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ent = [e.strip() for e in vis.split(",") if e.strip()]
+        if 0 <= dev < len(ent):
+            return ent[dev]
+    return str(dev)
+
+
 class ClockSampler:
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu: str):
+        """gpu: nvidia-smi's selector of the timed device (smi_device)."""
         self.f = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={q}",
                                        "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
@@ -170,7 +230,8 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
     # The timed region is far shorter than nvidia-smi's sampling interval, so
     # the clocks are sampled over a window of the same step loop around it
     # (about 0.3 s of untimed steps before the warm-up and after the timed steps).
-    clocks = ClockSampler(torch.cuda.current_device())
+    smi_sel = smi_device(torch.cuda.current_device())
+    clocks = ClockSampler(smi_sel)
     _busy(run, 0.3)
     for _ in range(warmup):
         run.step()
@@ -192,6 +253,7 @@ def run_ours(prec: str, steps: int, warmup: int, rank: int, world: int, dist):
     _busy(run, 0.3)
     ck = clocks.stop()
     ck["window"] = "same step loop, ~0.3 s before the warm-up to ~0.3 s after the timed steps"
+    ck["device"] = smi_sel
     ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, dist, "cuda")
     cells = grid.npatch * N_CELLS * N_CELLS
     # sanity: the state stays finite
@@ -252,6 +314,38 @@ def run_e2e(prec: str, steps: int, warmup: int, tiling=None, bands: int = 32, la
     return {"value": cells / (ms * 1e-3), "unit": "cell updates/s", "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes, "ms_per_step": ms, "bands": bands, "host_layout": layout,
             "link_gbs": 2 * nbytes / (ms * 1e-3) / 1e9}
+
+
+def link_peak(nbytes: int, reps: int = 5):
+    """Host-link copy rates for a state of `nbytes` in pinned host memory:
+    host->device alone, device->host alone, and both at once on two streams
+    (the pattern of the end-to-end step).  Best of `reps`, GB/s."""
+    import torch
+    h_in = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(up: bool, dn: bool) -> float:
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if up:
+                with torch.cuda.stream(s_up):
+                    d_a.copy_(h_in, non_blocking=True)
+            if dn:
+                with torch.cuda.stream(s_dn):
+                    h_out.copy_(d_b, non_blocking=True)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        return (int(up) + int(dn)) * nbytes / best / 1e9
+
+    out = {"h2d_gbs": timed(True, False), "d2h_gbs": timed(False, True), "both_gbs": timed(True, True),
+           "bytes_each_way": nbytes, "how": "pinned host <-> device copies (torch copy_), best of %d" % reps}
+    del h_in, h_out, d_a, d_b
+    return out
 
 
 def literal_config2(prec: str, steps: int):
@@ -418,13 +512,14 @@ def amr_tune(case: str, leaves, st, prec: str):
     the fastest second tiling for the leaves that advance their ghost layer
     (AMRRun ext_tiling; None: the same tiling).  Returns (tiling, ext_tiling,
     times in ms keyed "k" or "k+e")."""
-    ntil = len(__import__("paper_2205_07572_gb300.af", fromlist=["af"]).step_tilings())
+    from paper_2205_07572_gb300 import tune
+    cands = tune.default_candidates()
     times = {}
-    for k in range(ntil):
+    for k in cands:
         r, _ = amr_time(case, leaves, st, prec, "batched", False, 2, 1, tiling=k)
         times[(k, None)] = r["ms_per_coarse_step"]
     best = min(times, key=times.get)[0]
-    for e in range(ntil):
+    for e in cands:
         if e != best:
             r, _ = amr_time(case, leaves, st, prec, "batched", False, 2, 1, tiling=best, ext_tiling=e)
             times[(best, e)] = r["ms_per_coarse_step"]
@@ -894,11 +989,7 @@ def main():
     r64 = run_ours("f64", max(3, args.steps // 4), warm, rank, world, dist)
     hbm, src = measured_peaks()
     cells = r32["cells"]
-    # DRAM bytes (read + write) of one launch of the 32 x 8 FP32 tiling on this
-    # workload, from an ncu capture of the current kernel; other tilings were
-    # not captured
-    t = r32["tiling"]
-    traffic = 1.951e9 if (tuple(t["tile"]) == (32, 8) and t["threads"] == 128 and not t["persistent"]) else None
+    traffic, traffic_src = profiled_traffic(r32["tiling"])
     value = job_rate(cells, world, r32["ms"])
     achieved = cells * BYTES_PER_CELL["f32"] / (r32["ms"] * 1e-3) / 1e9
     line = None
@@ -909,6 +1000,8 @@ def main():
             lat = run_e2e("f32", max(3, args.steps // 4), 2, r32["tiling"]["index"], layout="lattice")
             e2e["lattice_layout"] = {k: lat[k] for k in ("value", "ms_per_step", "h2d_bytes_per_step",
                                                          "d2h_bytes_per_step", "link_gbs")}
+            e2e["link_peak"] = link_peak(e2e["h2d_bytes_per_step"])
+            e2e["link_frac"] = e2e["link_gbs"] / e2e["link_peak"]["both_gbs"]
         lit32 = literal_config2("f32", 50) if extras else None
         lit64 = literal_config2("f64", 10) if extras else None
         cpu = None if (args.no_cpu_baseline or not extras) else oracle_sample(20)
@@ -941,7 +1034,7 @@ def main():
                      "bound": "alu", "clocks": r64["clocks"]},
             "alu": alu,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic,
+                         "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_src,
                          "kernel": "step_kernel<float, acoustics>",
                          "peak_source": f"{src} HBM copy bandwidth",
                          "algorithmic_bytes_per_launch": cells * BYTES_PER_CELL["f32"]},

@@ -477,15 +477,19 @@ af_status af_mass_pair(const af_config *cfg, const af_forest *forest, const af_s
  * The partial sums live in one fixed array inside the library, 1024 doubles
  * (8 KB, room for 256 partial sums of up to 4 components), which every GPU
  * that loads the library keeps until the process exits; AF_ERR_ARG if a
- * call would need more (it never does for ncomp <= 3).  The first call on a
- * device, with that device current, looks up the array's device address (a
- * runtime query that enqueues no work); make that first call before any
- * stream capture.  All calls on one device share that device's copy of the
- * array, which keeps the last call's partial sums: calls that overlap on the
- * GPU (for example on two streams with no ordering between them) race and
- * give wrong totals; calls on different devices use different copies.
- * Nothing needs clearing between calls: every partial sum is written before
- * it is read. */
+ * call would need more (it never does: af_mass uses at most 256 partial sums
+ * per component and ncomp <= 3).  The state must be 32-byte aligned, as for
+ * af_mass (else AF_ERR_LAYOUT).  Every call looks up the array's device
+ * address (cudaGetSymbolAddress, a runtime query that enqueues no work and
+ * allocates nothing) with the caller's device current, so the address always
+ * belongs to the current context, also after a device reset.  The first call
+ * on a device may load the library's device code; make it before any stream
+ * capture.  All calls on one device share that device's copy of the array,
+ * which keeps the last call's partial sums: calls that overlap on the GPU
+ * (for example on two streams with no ordering between them) race and give
+ * wrong totals; calls on different devices use different copies.  Nothing
+ * needs clearing between calls: every partial sum is written before it is
+ * read. */
 af_status af_mass_noalloc(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0,
                           double dy0, double *d_mass, void *stream);
 

@@ -8,7 +8,6 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "af_internal.h"
 
@@ -896,38 +895,27 @@ extern "C" af_status af_mass(const af_config *cfg, const af_forest *forest, cons
 // loads the library keeps this array (8 KB) until the process exits.
 static __device__ __align__(256) double g_mass_partials[256 * 4];  // kMassBlocks partial sums x up to 4 components
 
-namespace {
-std::mutex g_partials_mu;
-constexpr int kMaxDevices = 64;
-double *g_partials_addr[kMaxDevices] = {nullptr};
-}  // namespace
-
 extern "C" af_status af_mass_noalloc(const af_config *cfg, const af_forest *forest, const void *d_state, double dx0,
                                      double dy0, double *d_mass, void *stream) {
     if (!check_cfg(cfg) || !check_forest(forest)) return AF_ERR_ARG;
     if (!(dx0 > 0.0) || !(dy0 > 0.0) || !d_mass) return AF_ERR_ARG;
     if (forest->nleaf > 0 && !d_state) return AF_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(d_mass) & 7u) return AF_ERR_LAYOUT;
+    const af_state_pair st = single(d_state);
+    if (forest->nleaf > 0)
+        if (const af_status e = check_pair(&st)) return e;  // the alignment af_mass requires
     const int nb = mass_blocks(forest->nleaf);
     // capacity check: partial sums needed vs. the fixed array
     if ((int64_t)nb * cfg->ncomp > (int64_t)(sizeof(g_mass_partials) / sizeof(double))) return AF_ERR_ARG;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return AF_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return AF_ERR_ARG;
-    double *part = nullptr;
-    {
-        // In host code g_mass_partials names a host-side stand-in, not device
-        // memory: resolve the device address once per device, with that
-        // device current.
-        std::lock_guard<std::mutex> lk(g_partials_mu);
-        if (g_partials_addr[dev] == nullptr) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_mass_partials) != cudaSuccess || p == nullptr) return AF_ERR_CUDA;
-            g_partials_addr[dev] = static_cast<double *>(p);
-        }
-        part = g_partials_addr[dev];
-    }
+    // In host code g_mass_partials names a host-side stand-in, not device
+    // memory.  Its device address is looked up on every call, with the
+    // caller's device current, so that it always belongs to the current
+    // context (a cached address would go stale after a device reset).  The
+    // lookup enqueues no work and allocates nothing.
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_mass_partials) != cudaSuccess || p == nullptr) return AF_ERR_CUDA;
     // every partial sum read by mass_final is written by mass_partial first,
     // so nothing left in the array by an earlier call is used
-    return launch_mass(*cfg, *forest, single(d_state), dx0, dy0, part, d_mass, static_cast<cudaStream_t>(stream));
+    return launch_mass(*cfg, *forest, st, dx0, dy0, static_cast<double *>(p), d_mass,
+                       static_cast<cudaStream_t>(stream));
 }

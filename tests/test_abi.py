@@ -157,3 +157,28 @@ def test_probe_and_counter_host_side_errors(af):
     assert L.af_fma_throughput(af.F64, 1, 1, ctypes.c_void_p(sink + 4), None) == 3  # misaligned FP64 sink
     assert L.af_step_wait_timeouts(None, 0) == 1
     assert L.af_fma_probe_threads() == 256 * 8
+
+
+def test_mass_noalloc_host_side_errors_and_capacity(af):
+    """af_mass_noalloc refuses, on the host, what af_mass refuses: a missing
+    state or result, a misaligned state (AF_ERR_LAYOUT, as af_mass's
+    check), a misaligned result.  Its fixed array holds 1024 partial sums
+    (af.h): af_mass needs at most 256 per component for any leaf count, so
+    three components always fit."""
+    import ctypes
+    cfg = af.config(af.ACOUSTICS, af.F64, 16, c=1.0)
+    fake = 1 << 20                                     # fake, aligned, never dereferenced
+    F = af.forest_struct(300, 1, 5, fake, fake, fake, fake)
+    L = af.lib()
+
+    def call(state, out):
+        return L.af_mass_noalloc(ctypes.byref(cfg), ctypes.byref(F), ctypes.c_void_p(state), 1 / 16, 1 / 16,
+                                 ctypes.c_void_p(out), None)
+
+    assert call(0, fake) == 1                          # no state
+    assert call(fake, 0) == 1                          # no result
+    assert call(fake + 8, fake) == 3                   # state not 32-byte aligned
+    assert call(fake, fake + 4) == 3                   # result not 8-byte aligned
+    for nleaf in (1, 255, 256, 300, 1 << 20, (1 << 31) - 1):
+        assert af.mass_scratch_bytes(nleaf, 3) <= 1024 * 8
+    assert af.mass_scratch_bytes(1 << 20, 3) == 256 * 3 * 8

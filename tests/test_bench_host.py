@@ -13,10 +13,11 @@ import bench
 
 
 def _fake_smi(tmp_path, lines):
-    """An executable `nvidia-smi` that prints `lines` once, then idles."""
+    """An executable `nvidia-smi` that records its arguments in args.txt,
+    prints `lines` once, then idles."""
     script = tmp_path / "nvidia-smi"
     body = "\n".join(f"echo '{ln}'" for ln in lines)
-    script.write_text(f"#!/bin/sh\n{body}\nexec sleep 30\n")
+    script.write_text(f"#!/bin/sh\necho \"$@\" > {tmp_path}/args.txt\n{body}\nexec sleep 30\n")
     script.chmod(script.stat().st_mode | stat.S_IEXEC)
     return str(tmp_path)
 
@@ -29,7 +30,7 @@ def test_clock_sampler_parses_clocks_and_reasons(tmp_path, monkeypatch):
         "garbage line",
     ]
     monkeypatch.setenv("PATH", _fake_smi(tmp_path, lines) + os.pathsep + os.environ["PATH"])
-    ck = bench.ClockSampler(0)
+    ck = bench.ClockSampler("0")
     t0 = time.time()
     while time.time() - t0 < 10 and open(ck.f.name).read().count("\n") < len(lines):
         time.sleep(0.05)
@@ -41,7 +42,7 @@ def test_clock_sampler_parses_clocks_and_reasons(tmp_path, monkeypatch):
 
 def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
     monkeypatch.setenv("PATH", str(tmp_path))
-    out = bench.ClockSampler(0).stop()
+    out = bench.ClockSampler("0").stop()
     assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
 
 
@@ -60,3 +61,26 @@ def test_flop_count_per_acoustic_cell_update():
     (a multiply-add and an add), 8 flux scalings, and per component two
     differences and two multiply-adds in the update."""
     assert bench.ACOUSTIC_FLOP_PER_CELL == 3 * 76 + 230 * 2 + 4 * 3 * 3 + 8 + 3 * (2 + 2 * 2) == 750
+
+
+def test_clock_sampler_follows_a_remapped_device(tmp_path, monkeypatch):
+    """Under CUDA_VISIBLE_DEVICES the process's CUDA device 1 is the host's
+    GPU 5: without a UUID the sampler selects GPU 5, and with one it selects
+    by UUID -- never the process-local index."""
+    import types
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "3,5")
+    fake = types.SimpleNamespace(cuda=types.SimpleNamespace(
+        get_device_properties=lambda d: types.SimpleNamespace(name="gpu")))
+    monkeypatch.setitem(__import__("sys").modules, "torch", fake)
+    assert bench.smi_device(1) == "5"
+    fake.cuda.get_device_properties = lambda d: types.SimpleNamespace(uuid="1234abcd-0000-1111-2222-333344445555")
+    assert bench.smi_device(1) == "GPU-1234abcd-0000-1111-2222-333344445555"
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, ["5, 2070, 2070, 900.0, 0x0, Not Active, Not Active, "
+                                                    "Not Active, Not Active"]) + os.pathsep + os.environ["PATH"])
+    ck = bench.ClockSampler(bench.smi_device(1))
+    t0 = time.time()
+    while time.time() - t0 < 10 and not (tmp_path / "args.txt").exists():
+        time.sleep(0.05)
+    ck.stop()
+    args = (tmp_path / "args.txt").read_text().split()
+    assert args[:2] == ["-i", "GPU-1234abcd-0000-1111-2222-333344445555"]
