@@ -409,9 +409,14 @@ af_status af_fill_ghosts_planned(const af_config *cfg, const af_forest *forest, 
 
 /* Regrid transfer (Section 3.1 cases 1 and 2): every leaf of new_forest that
  * is a leaf of old_forest is copied whole from d_old; every other new leaf
- * gets its interior-owned entries from the owners in old_forest (coarse ->
- * fine interpolation, fine -> coarse averaging, one level of coarsening at
- * most) and zeros in its ghost ring.  d_old and d_new must not overlap. */
+ * gets, from the owners in old_forest (coarse -> fine interpolation, fine ->
+ * coarse averaging over one level, the coinciding vertex of a finer owner),
+ * its cell averages and the point values on its cells' boundaries -- node
+ * lines 0 .. n, the right and top lines included, which the leaf owns where
+ * its neighbour across is coarser (Section 3.2 uses the finer grid's values
+ * at coarse-fine faces) -- and zeros in the rest of its ghost ring.  Entries
+ * another leaf owns are replaced by the exchange (af_fill_ghosts over all
+ * levels) that must follow.  d_old and d_new must not overlap. */
 af_status af_transfer(const af_config *cfg, const af_forest *old_forest, const void *d_old,
                       const af_forest *new_forest, void *d_new, void *stream);
 

@@ -97,6 +97,8 @@ def lib():
         L.orc_step_patch_var.argtypes = [vp, dp, dp, dp]
         L.orc_run_uniform_var.restype = None
         L.orc_run_uniform_var.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, dp, dp, C.c_int]
+        L.orc_step_patches.restype = None
+        L.orc_step_patches.argtypes = [C.POINTER(Cfg), vp, dp, dp, C.c_int, ip, C.c_long, dp, dp, C.c_long, C.c_int]
         _lib = L
     return _lib
 

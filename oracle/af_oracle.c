@@ -702,6 +702,32 @@ void orc_run_uniform(const orc_cfg *cf, int px, int py, int nsteps, double *stat
     }
 }
 
+/* One step of the patches idx[0..np) of a state of `words`-word patches,
+ * each patch independent of the others (its ghost ring already filled):
+ * the loop of the adaptive driver over the leaves of one level, with OpenMP
+ * over patches.  freg: flux registers of `rwords` words per patch, or NULL.
+ * var: NULL for constant coefficients (cf), else the variable-velocity
+ * configuration, with x0[k], y0[k] the position of patch idx[k]. */
+void orc_step_patches(const orc_cfg *cf, const orc_var *var, const double *x0, const double *y0, int np,
+                      const int32_t *idx, long words, double *state, double *freg, long rwords, int nthreads) {
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)words * (size_t)(np > 0 ? np : 1));
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1)
+    for (int k = 0; k < np; ++k) {
+        const long p = idx[k];
+        double *fr = freg ? freg + p * rwords : NULL;
+        if (var) {
+            orc_var vp = *var;
+            vp.x0 = x0[k];
+            vp.y0 = y0[k];
+            orc_step_patch_var(&vp, state + p * words, tmp + (long)k * words, fr);
+        } else {
+            orc_step_patch(cf, state + p * words, tmp + (long)k * words, fr);
+        }
+    }
+    for (int k = 0; k < np; ++k) memcpy(state + (long)idx[k] * words, tmp + (long)k * words, sizeof(double) * words);
+    free(tmp);
+}
+
 int orc_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();
@@ -914,6 +940,8 @@ void orc_fill_amr(int n, int ncomp, int nleaf, const int32_t *level, const int32
     double *prev = (double *)malloc(sizeof(double) * pw * nleaf);
     for (int pass = 0; pass < 3; ++pass) { /* 0: finer owner, 1: same level, 2: coarser */
         memcpy(prev, out, sizeof(double) * pw * nleaf);
+        /* every leaf writes only its own ghost entries, read from prev */
+#pragma omp parallel for schedule(dynamic, 4)
         for (int p = 0; p < nleaf; ++p) {
             int lp = level[p];
             if (!((dst_levels >> lp) & 1u)) continue;
@@ -1072,12 +1100,17 @@ void orc_mass(int n, int ncomp, int nleaf, const int32_t *level, const double *s
 }
 
 /* Regrid transfer (Section 3.1, cases 1 and 2): every leaf of the new forest
- * that is also a leaf of the old one is copied; every other new leaf gets its
- * interior-owned entries from the old leaf covering each entry (coarse ->
- * fine interpolation if that leaf is coarser, fine -> coarse averaging if it
- * is finer).  Ghost entries of new leaves are left for the next exchange.
+ * that is also a leaf of the old one is copied; every other new leaf gets,
+ * from the old leaf owning each entry (coarse -> fine interpolation if that
+ * leaf is coarser, fine -> coarse averaging or the coinciding vertex if it is
+ * finer), its cell averages and the point values of its cells' boundaries:
+ * node lines 0 .. n, the far lines i = n and j = n included, because a leaf
+ * finer than its right or top neighbour owns the nodes on that face (the more
+ * resolved grid's values are used at coarse-fine faces, Section 3.2).  Entries
+ * another leaf owns, and the ghost ring, are replaced by the next exchange.
  * Pinned by: refine-then-coarsen returns the original averages, and the
- * nodes shared with the old leaf are copied exactly (P8).                  */
+ * nodes shared with the old leaf are copied exactly (P8); after any regrid
+ * and exchange of biquadratic data every entry of every leaf is exact.     */
 void orc_transfer(int n, int ncomp, int B, int lmax, int nold, const int32_t *olevel, const int32_t *oix,
                   const int32_t *oiy, const double *old_state, int nnew, const int32_t *nlevel, const int32_t *nix,
                   const int32_t *niy, double *new_state) {
@@ -1093,9 +1126,14 @@ void orc_transfer(int n, int ncomp, int B, int lmax, int nold, const int32_t *ol
         for (long e = 0; e < pw; ++e) dst[e] = 0.0;
         long hw = hw_of(&F, nlevel[p]);
         long x0 = (long)nix[p] * n * hw, y0 = (long)niy[p] * n * hw;
-        for (int k = 0; k < 4; ++k)
-            for (int j = 0; j < n; ++j)
-                for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < 4; ++k) {
+            /* lattice lines of the plane on the leaf's cells and their
+             * boundaries: averages [0,n)^2, corners [0,n]^2, left-edge
+             * midpoints [0,n] x [0,n), bottom-edge midpoints [0,n) x [0,n] */
+            const int ni = (k == PL_CORNER || k == PL_XMID) ? n + 1 : n;
+            const int nj = (k == PL_CORNER || k == PL_YMID) ? n + 1 : n;
+            for (int j = 0; j < nj; ++j)
+                for (int i = 0; i < ni; ++i) {
                     long x = x0 + (long)i * hw + ((k == PL_AVG || k == PL_YMID) ? hw / 2 : 0);
                     long y = y0 + (long)j * hw + ((k == PL_AVG || k == PL_XMID) ? hw / 2 : 0);
                     int q = entry_owner(&F, k, x, y);
@@ -1103,6 +1141,7 @@ void orc_transfer(int n, int ncomp, int B, int lmax, int nold, const int32_t *ol
                     for (int c = 0; c < ncomp; ++c)
                         PL(&L, dst, c, k)[IX(&L, i, j)] = transfer_value(&F, old_state, nlevel[p], q, c, k, x, y);
                 }
+        }
     }
     forest_free(&F);
 }

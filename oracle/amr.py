@@ -20,7 +20,7 @@ import ctypes as C
 
 import numpy as np
 
-from . import ADVECTION, VarCfg, _dp, cfg, lib
+from . import ADVECTION, VarCfg, _dp, cfg, lib, max_threads
 
 
 def _ip(a):
@@ -54,9 +54,10 @@ class OracleForest:
     def levels(self):
         return sorted(set(self.level.tolist()))
 
-    def cfg_level(self, l):
+    def cfg_level(self, l, dt=None):
         s = 2.0 ** -l
-        return cfg(self.eq, self.n, self.dx0 * s, self.dy0 * s, self.dt0 * s, self.a, self.b, self.c)
+        return cfg(self.eq, self.n, self.dx0 * s, self.dy0 * s, self.dt0 * s if dt is None else dt, self.a,
+                   self.b, self.c)
 
     # ---------------------------------------------------------------- pieces
     def fill(self, dst_mask: int, src_mask: int, same_only: bool):
@@ -66,21 +67,20 @@ class OracleForest:
                            _dp(self.state), _dp(out))
         self.state = out
 
-    def advance(self, l: int, t: float = 0.0):
-        """One step of dt_l from time t on every leaf of level l (same-level
-        copy first)."""
+    def advance(self, l: int, t: float = 0.0, dt=None):
+        """One step of dt (default dt_l) from time t on every leaf of level l
+        (same-level copy first); each leaf's step is orc_step_patch (or
+        orc_step_patch_var) on its own lattice, the leaves in parallel."""
         self.fill(1 << l, 1 << l, True)
-        cf = self.cfg_level(l)
-        for p in np.nonzero(self.level == l)[0]:
-            fr = self.freg[p]
-            out = np.empty_like(self.state[p])
-            if self.field is None:
-                lib().orc_step_patch(C.byref(cf), _dp(self.state[p]), _dp(out), _dp(fr))
-            else:
-                vc = VarCfg(self.n, self.field, cf.dx, cf.dy, cf.dt, self.lo[0] + self.ix[p] * self.n * cf.dx,
-                            self.lo[1] + self.iy[p] * self.n * cf.dy, t)
-                lib().orc_step_patch_var(C.byref(vc), _dp(self.state[p]), _dp(out), _dp(fr))
-            self.state[p] = out
+        cf = self.cfg_level(l, dt)
+        idx = np.ascontiguousarray(np.nonzero(self.level == l)[0], dtype=np.int32)
+        if len(idx) == 0:
+            return
+        x0 = np.ascontiguousarray(self.lo[0] + self.ix[idx] * self.n * cf.dx, dtype=np.float64)
+        y0 = np.ascontiguousarray(self.lo[1] + self.iy[idx] * self.n * cf.dy, dtype=np.float64)
+        var = None if self.field is None else C.byref(VarCfg(self.n, self.field, cf.dx, cf.dy, cf.dt, 0.0, 0.0, t))
+        lib().orc_step_patches(C.byref(cf), var, _dp(x0), _dp(y0), len(idx), _ip(idx), self.state.shape[1],
+                               _dp(self.state), _dp(self.freg), self.freg.shape[1], max_threads())
 
     def reflux(self, sync_mask: int):
         lib().orc_reflux_amr(self.n, self.ncomp, len(self.leaves), _ip(self.level), _ip(self.ix), _ip(self.iy),
@@ -89,13 +89,27 @@ class OracleForest:
     def sync_fill(self, sync_mask: int):
         self.fill(sync_mask, sync_mask, False)
 
-    def coarse_step(self):
+    def coarse_step(self, subcycle: bool = True):
         """Advance every level by dt of the coarsest level present (Section
-        3.2, 'Subcycling'), finest level first."""
+        3.2, 'Subcycling'), finest level first.  subcycle=False: global time
+        stepping, every level takes the finest level's dt, and all levels are
+        synchronised (conservative fix, ghost exchange) after every step --
+        the runs 'without subcycling' of Section 4.3."""
         levels = self.levels
         lmin, lmx = levels[0], levels[-1]
         S = 1 << (lmx - lmin)
         t0, dtf = self.time, self.dt0 / (1 << lmx)
+        if not subcycle:
+            every = sum(1 << l for l in levels)
+            for s in range(S):
+                for l in range(lmx, lmin - 1, -1):
+                    if l in levels:
+                        self.advance(l, t0 + s * dtf, dt=dtf)
+                if len(levels) > 1:
+                    self.reflux(every)
+                    self.sync_fill(every)
+            self.time = t0 + self.dt0 / (1 << lmin)
+            return
         for s in range(S):
             for l in range(lmx, lmin - 1, -1):
                 if l in levels and s % (1 << (lmx - l)) == 0:

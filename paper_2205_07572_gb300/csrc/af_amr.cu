@@ -457,16 +457,25 @@ __global__ void transfer_kernel(DevForest Fo, StateView<T> So, DevForest Fn, Sta
     }
     for (int64_t e = threadIdx.x; e < words; e += blockDim.x) dst[e] = T(0);
     __syncthreads();
-    const int n = Fn.n;
+    const int n = Fn.n, m = n + 1;
     const long long hwn = 2LL << (Fn.lmax - l);
     const long long x0 = (long long)px * n * hwn, y0 = (long long)py * n * hwn;
-    for (int e = threadIdx.x; e < kPlanes * n * n; e += blockDim.x) {
-        const int k = e / (n * n), r = e - k * n * n, j = r / n, i = r % n;
+    // The cells' averages and the point values on their boundaries: node
+    // lines 0 .. n, the right (i = n) and top (j = n) lines included -- a leaf
+    // finer than its neighbour across that face owns those nodes (the finer
+    // grid's values are used at coarse-fine faces), and nothing else writes
+    // them.  Entries owned by another leaf are overwritten by the exchange
+    // that follows a regrid.
+    for (int e = threadIdx.x; e < kPlanes * m * m; e += blockDim.x) {
+        const int k = e / (m * m), r = e - k * m * m, j = r / m, i = r - j * m;
+        if ((i == n && (k == kAvg || k == kYmid)) || (j == n && (k == kAvg || k == kXmid))) continue;
         const long long x = x0 + (long long)i * hwn + ((k == kAvg || k == kYmid) ? hwn / 2 : 0);
         const long long y = y0 + (long long)j * hwn + ((k == kAvg || k == kXmid) ? hwn / 2 : 0);
         const int q = entry_owner(Fo, k, x, y);
         if (q < 0) continue;
-        if (__ldg(Fo.level + q) > l + 1) continue;  // at most one level of coarsening
+        // an average comes from at most one level finer (the four children's
+        // mean); a point value is the coinciding vertex of any finer owner
+        if (k == kAvg && __ldg(Fo.level + q) > l + 1) continue;
         for (int c = 0; c < Sn.ncomp; ++c) *Sn.at(p, c, k, i, j) = (T)transfer<T>(Fo, So, l, q, c, k, x, y);
     }
 }

@@ -255,6 +255,54 @@ def test_dynamic_regrid_run_matches_oracle(af, prec):
     _compare(Fo, run, n, 1, TOL[prec])
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_regrid_transfer_matches_oracle_and_is_exact_for_biquadratics(af, seed):
+    """Random refine / coarsen tags on a biquadratic (levels 2-4): after each
+    regrid (af_forest_regrid, af_transfer, exchange) every cell average and
+    every point value on the leaves' left and bottom lines and inside them
+    equals the oracle's regrid, and is exact on the leaves in [1/4, 3/4]^2
+    (the data are not periodic, so cells on the periodic seam are not).  A
+    refined leaf owns the nodes on its right and top faces where the
+    neighbour across is coarser; they reach that neighbour's left and bottom
+    lines through the exchange, so a transfer that left them unset fails
+    here."""
+    from paper_2205_07572_gb300.amr import AMRRun
+    f = lambda x, y: 0.3 + x - 2 * y + 1.5 * x * y + x * x - 0.5 * y * y + x * x * y - 2 * x * y * y \
+        + 3 * x * x * y * y
+    n, lmin, lmax = 8, 2, 4
+    leaves = _sorted(S.balanced_forest(1, lmin, 3, lambda l, x, y: (x + y) % 3 == 0))
+    st = S.forest_state(n, 1, 1, lmax, leaves, [f], nq=3)
+    Fo = OracleForest(0, n, 1, lmax, leaves, (0, 0), (1, 1), 0.01, 1.0, 0.5, state=st)
+    Fo.sync_fill((1 << (lmax + 1)) - 1)
+    run = AMRRun(af.config(0, 0, n, 1.0, 0.5), 1, lmax, leaves, st, (0, 0), (1, 1), 0.01)
+    rng = np.random.default_rng(seed)
+    lay = S.Layout(n, 1)
+    exact_leaves = 0
+    for _ in range(4):
+        tags = rng.choice(np.array([-1, 0, 1], np.int8), size=len(Fo.leaves), p=[0.45, 0.25, 0.3])
+        order = {leaf: k for k, leaf in enumerate(Fo.leaves)}
+        Fo.regrid(tags, lmin)
+        run.regrid(tags[[order[lf] for lf in run.forest.leaves]], lmin)
+        assert Fo.leaves == run.forest.leaves
+        torch.cuda.synchronize()
+        g = lay.lattice(run.state_in_order(Fo.leaves).reshape(len(Fo.leaves), 1, 4, -1))[:, 0, :, G:G + n, G:G + n]
+        r = lay.lattice(Fo.state.reshape(len(Fo.leaves), 1, 4, -1))[:, 0, :, G:G + n, G:G + n]
+        assert np.abs(g - r).max() < 1e-12
+        for p, (l, ix, iy) in enumerate(Fo.leaves):
+            q = 1 << (l - 2)
+            if not (q <= ix < 3 * q and q <= iy < 3 * q):
+                continue
+            w = 1.0 / (1 << l)
+            h = w / n
+            I = np.arange(n)
+            for k in (S.CORNER, S.XMID, S.YMID):
+                X, Y = np.meshgrid(ix * w + I * h + (0.5 * h if k == S.YMID else 0.0),
+                                   iy * w + I * h + (0.5 * h if k == S.XMID else 0.0))
+                assert np.abs(g[p, k] - f(X, Y)).max() < 1e-12, ((l, ix, iy), k)
+            exact_leaves += 1
+    assert exact_leaves > 20
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_graph_replayed_amr_run_matches_oracle(af, prec):
     """Levels 2-4, batched launches captured in CUDA graphs: the first coarse
