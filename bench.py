@@ -383,25 +383,46 @@ def literal_config2(prec: str, steps: int):
 # ghost exchange at every synchronised time.
 AMR_CASES = {
     "advection_levels2-6": dict(
-        eq=0, B=1, lmin=2, lmax=6, lo=(0.0, 0.0), hi=(1.0, 1.0), a=1.0, b=1.0,
+        eq=0, B=1, lmin=2, lmax=6, lo=(0.0, 0.0), hi=(1.0, 1.0), a=1.0, b=1.0, per_patch=True,
         desc=("advection a=(1,1), periodic unit square, wave packet exp(-r^2/0.01) cos(60 pi x), levels 2-6, "
               "16x16-cell patches, gradient tagging (refine >= 4, coarsen < 1), CFL 0.4"),
         tag=(0, 1, 4.0, 1.0)),
     "acoustics_levels3-7": dict(
-        eq=1, B=3, lmin=3, lmax=7, lo=(-1.5, -1.5), hi=(1.5, 1.5), a=0.0, b=0.0,
+        eq=1, B=3, lmin=3, lmax=7, lo=(-1.5, -1.5), hi=(1.5, 1.5), a=0.0, b=0.0, per_patch=True,
         desc=("acoustics c=1, periodic [-1.5,1.5]^2 (3x3 brick), ring wave exp(-(r-0.25)^2/0.001) cos(80 pi r), "
               "u=v=0, levels 3-7, 16x16-cell patches, gradient tagging on p (refine >= 4, coarsen < 1), CFL 0.4"),
+        tag=(0, 1, 4.0, 1.0)),
+    # the configurations' stated patch counts: the same data repeated in every
+    # unit tree of a brick (one packet per tree of a 2x2 brick: 1k-5k leaves;
+    # one ring per tree of the 3x3 brick: tens of thousands of leaves)
+    "advection_levels2-6_2x2_packets": dict(
+        eq=0, B=2, lmin=2, lmax=6, lo=(0.0, 0.0), hi=(2.0, 2.0), a=1.0, b=1.0, per_patch=False,
+        per_tree=(0.0, 0.0),
+        desc=("advection a=(1,1), periodic [0,2]^2 (2x2 brick), the wave packet exp(-r^2/0.01) cos(60 pi x) in "
+              "each unit tree, levels 2-6, 16x16-cell patches, gradient tagging (refine >= 4, coarsen < 1), "
+              "CFL 0.4"),
+        tag=(0, 1, 4.0, 1.0)),
+    "acoustics_levels3-7_3x3_rings": dict(
+        eq=1, B=3, lmin=3, lmax=7, lo=(-1.5, -1.5), hi=(1.5, 1.5), a=0.0, b=0.0, per_patch=False,
+        per_tree=(-0.5, -0.5),
+        desc=("acoustics c=1, periodic [-1.5,1.5]^2 (3x3 brick), the ring wave exp(-(r-0.25)^2/0.001) "
+              "cos(80 pi r) centred in each unit tree, u=v=0, levels 3-7, 16x16-cell patches, gradient tagging "
+              "on p (refine >= 4, coarsen < 1), CFL 0.4"),
         tag=(0, 1, 4.0, 1.0)),
 }
 AMR_N = 16
 
 
-def _amr_funcs(eq):
+def _amr_funcs(case):
     import synth as S
-    if eq == 0:
-        return [S.wave_packet]
+    c = AMR_CASES[case]
+    f = S.wave_packet if c["eq"] == 0 else S.ring_wave
+    if "per_tree" in c:
+        f = S.per_unit_tree(f, c["per_tree"])
+    if c["eq"] == 0:
+        return [f]
     zero = lambda x, y: 0.0 * x
-    return [S.ring_wave, zero, zero]
+    return [f, zero, zero]
 
 
 def amr_initial(case: str, device="cuda"):
@@ -416,7 +437,7 @@ def amr_initial(case: str, device="cuda"):
     side = B << lmin
     leaves = [(lmin, x, y) for y in range(side) for x in range(side)]
     cfg = af.config(c["eq"], af.F64, AMR_N, c["a"], c["b"], 1.0)
-    funcs = _amr_funcs(c["eq"])
+    funcs = _amr_funcs(case)
     for _ in range(lmax - lmin):
         lv = np.array(leaves, dtype=np.int64).reshape(-1, 3)
         st = S.forest_state_fast(AMR_N, cfg.ncomp, B, lv[:, 0], lv[:, 1], lv[:, 2], funcs, c["lo"], c["hi"])
@@ -482,7 +503,7 @@ def amr_l1_exact(case: str, run, t: float):
     the initial data translated by (a, b) t)."""
     import synth as S
     c = AMR_CASES[case]
-    f = S.translated(S.wave_packet, c["a"], c["b"], t, c["lo"], c["hi"])
+    f = S.translated(_amr_funcs(case)[0], c["a"], c["b"], t, c["lo"], c["hi"])
     F = run.forest
     ex = S.forest_state_fast(AMR_N, 1, c["B"], F.level, F.ix, F.iy, [f], c["lo"], c["hi"], nq=4)
     lay = S.Layout(AMR_N, 1)
@@ -568,8 +589,13 @@ def amr_bench(case: str, coarse_steps: int, warmup: int, per_patch: bool = True)
     if out["regrid_same_forest_f32_f64"]:
         out["regrid_l1_f32_vs_f64"] = amr_l1_between(case, g32, g64)
     del g32, g64
-    base = out.get("per_patch_f64", out["per_level_f64"])["value"]
-    out["speedup_batched_f32_vs_per_patch_f64"] = r32["value"] / base
+    out["leaves"] = len(leaves)
+    # precision and batching at equal L1 first: batched FP32 against batched
+    # FP64, then against the per-level and per-patch launches
+    out["speedup_batched_f32_vs_batched_f64"] = r32["value"] / r64["value"]
+    out["speedup_batched_f32_vs_per_level_f64"] = r32["value"] / out["per_level_f64"]["value"]
+    if per_patch:
+        out["speedup_batched_f32_vs_per_patch_f64"] = r32["value"] / out["per_patch_f64"]["value"]
     return out
 
 
@@ -622,19 +648,61 @@ def adapt_initial(cfg, B, lmin, lmax, lo, hi, funcs, tag):
     return leaves, S.forest_state_fast(cfg.n, cfg.ncomp, B, lv[:, 0], lv[:, 1], lv[:, 2], funcs, lo, hi)
 
 
-def learned_tagging(B=3, lmin=3, lmax=6, train_radii=(0.2, 0.3), test_radius=0.25, train_steps=384,
-                    test_steps=160, horizon=4, epochs=4, batch=4096, cmin=0.5, seed=0):
-    """Acoustics ring wave on the 3 x 3 brick [-1.5, 1.5]^2, 16 x 16-cell
-    patches, FP32 stencil.  The tagger is trained on runs of the method
-    (plain criterion, regrid every `horizon` coarse steps) started from rings
-    of other radii, to predict whether the plain criterion will tag a leaf at
-    any of the next `horizon` coarse steps.  From the test ring: its tags are
-    judged against the plain criterion's, and three runs of test_steps coarse
-    steps are compared by the L1 distance of p to a uniform run at the finest
-    level and by cell updates per second (regrids included): the plain
-    criterion regridding every coarse step, the plain criterion regridding
-    every `horizon` steps, and the learned tagger (plain fallback below
-    confidence cmin) regridding every `horizon` steps."""
+def _tiling_index(tmx, tmy, threads):
+    from paper_2205_07572_gb300 import af
+    return [t[:3] for t in af.step_tilings()].index((tmx, tmy, threads))
+
+
+def pareto_front(points):
+    """Points (l1, rate) not beaten by another with lower (or equal) L1 and
+    higher rate, by increasing L1."""
+    front = []
+    for l1, rate in sorted(points):
+        if not front or rate > front[-1][1]:
+            front.append((l1, rate))
+    return front
+
+
+def rate_at(front, l1):
+    """Throughput of a Pareto front at L1 error `l1`, interpolated linearly
+    in log L1 and log rate between its neighbours; None outside its range.
+    A front that reaches lower L1 at an equal or higher rate counts as that
+    rate at every larger L1 (it could be run as is)."""
+    if not front or l1 < front[0][0] * (1 - 1e-12):
+        return None
+    best = None
+    for k, (a, ra) in enumerate(front):
+        if a <= l1:
+            best = ra if best is None else max(best, ra)
+        if k + 1 < len(front):
+            (b, rb) = front[k + 1]
+            if a <= l1 <= b:
+                t = (math.log(l1) - math.log(a)) / (math.log(b) - math.log(a)) if b > a else 0.0
+                v = math.exp(math.log(ra) + t * (math.log(rb) - math.log(ra)))
+                best = v if best is None else max(best, v)
+    return best
+
+
+def learned_tagging(B=3, lmin=3, lmax=7, train_radii=(0.2, 0.3), test_radius=0.25, train_steps=256,
+                    t_end=None, test_steps=128, intervals=(2, 4, 8), plain_intervals=(1, 2, 4),
+                    thresholds=(3.0, 4.0, 6.0), epochs=4, batch=4096, cmin=0.5, seed=0, fp64=True,
+                    per_patch=True):
+    """Acoustics ring wave on the 3 x 3 brick [-1.5, 1.5]^2, levels 3-7 (the
+    configuration-4 forest), 16 x 16-cell patches, FP32 stencil.  For each
+    regrid interval R in `intervals` a tagger is trained on runs of the method
+    (plain criterion, regrid every R coarse steps) started from rings of other
+    radii, to predict whether the plain criterion tags a leaf at any of the
+    next R coarse steps.  On the test ring, runs to the same end time are
+    compared by the L1 distance of p to a uniform run at the finest level and
+    by cell updates per second (regrids and tagging included):
+      plain criterion, regrid every {plain_intervals} steps, refine threshold
+      in {thresholds} (coarsen below a quarter of it);
+      learned tags (plain fallback below confidence cmin), regrid every R.
+    The two Pareto fronts (L1, throughput) are compared at equal L1
+    (interpolated).  Batched FP64 and per-patch FP64 runs of the plain
+    criterion (every step, threshold 4) give the precision baselines; the
+    per-patch run is timed on a few coarse steps (its arithmetic, and so its
+    L1, is the batched FP64 run's)."""
     import torch
     import synth as S
     from paper_2205_07572_gb300 import af
@@ -643,111 +711,241 @@ def learned_tagging(B=3, lmin=3, lmax=6, train_radii=(0.2, 0.3), test_radius=0.2
     lo, hi = (-1.5, -1.5), (1.5, 1.5)
     n = AMR_N
     cfg = af.config(af.ACOUSTICS, af.F32, n, c=1.0)
+    cfg64 = af.config(af.ACOUSTICS, af.F64, n, c=1.0)
     dx0 = (hi[0] - lo[0]) / (B * n)
     dt0 = CFL * dx0
-    tag = (0, 1, 4.0, 1.0)
+    comp, kind = 0, 1
     zero = lambda x, y: 0.0 * x
     out = {"workload": (f"acoustics ring waves exp(-(r-r0)^2/0.001) cos(80 pi r) on the {B}x{B} brick "
                         f"[-1.5,1.5]^2, levels {lmin}-{lmax}, 16x16 patches, FP32; train r0 {list(train_radii)}, "
-                        f"test r0 {test_radius}; regrid horizon {horizon} coarse steps"), "horizon": horizon}
-    t0 = time.perf_counter()
-    parts = []
-    for r0 in train_radii:
-        leaves, st = adapt_initial(cfg, B, lmin, lmax, lo, hi, [S.ring_wave_at(r0), zero, zero], tag)
-        run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
-        parts.append(collect(run, train_steps, tag, lmin, tag[2], horizon=horizon))
-        del run
-    data = {k: torch.cat([p[k] for p in parts]) for k in parts[0]}
-    torch.cuda.synchronize()
-    out["collect_s"] = round(time.perf_counter() - t0, 2)
-    data = prepare(data, batch, seed=seed)
-    out["samples"] = int(data["level"].numel())
-    out["positive_fraction"] = data["positives"] / out["samples"]
-    tg = Tagger(3, n, seed=seed)
-    ev0 = tg.evaluate(data)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    tg.fit(data, epochs=epochs, batch=batch)
-    torch.cuda.synchronize()
-    out["train_s"] = round(time.perf_counter() - t1, 3)
-    out["train_samples_per_s"] = epochs * (out["samples"] // batch) * batch / out["train_s"]
-    out["train_eval"] = {"before": ev0, "after": tg.evaluate(data)}
-    del data, parts
+                        f"test r0 {test_radius}; gradient criterion (refine >= thr, coarsen < thr/4)"),
+           "levels": [lmin, lmax]}
+    tagq = lambda thr: (comp, kind, thr, thr / 4.0)
+    # ---- one tagger per regrid interval
+    taggers, out["training"] = {}, {}
+    for R in intervals:
+        t0 = time.perf_counter()
+        parts = []
+        for r0 in train_radii:
+            leaves, st = adapt_initial(cfg, B, lmin, lmax, lo, hi, [S.ring_wave_at(r0), zero, zero], tagq(4.0))
+            run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
+            parts.append(collect(run, train_steps, tagq(4.0), lmin, 4.0, horizon=R))
+            del run
+        data = {k: torch.cat([p[k] for p in parts]) for k in parts[0]}
+        torch.cuda.synchronize()
+        collect_s = time.perf_counter() - t0
+        data = prepare(data, batch, seed=seed)
+        tg = Tagger(3, n, seed=seed)
+        ev0 = tg.evaluate(data)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        tg.fit(data, epochs=epochs, batch=batch)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t1
+        taggers[R] = tg
+        out["training"][str(R)] = {"samples": int(data["level"].numel()),
+                                   "positive_fraction": data["positives"] / int(data["level"].numel()),
+                                   "collect_s": round(collect_s, 2), "train_s": round(train_s, 3),
+                                   "train_samples_per_s": epochs * (int(data["level"].numel()) // batch) * batch
+                                   / train_s, "before": ev0, "after": tg.evaluate(data)}
+        del data, parts
     funcs = [S.ring_wave_at(test_radius), zero, zero]
-    leaves, st = adapt_initial(cfg, B, lmin, lmax, lo, hi, funcs, tag)
-    run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
-    test = prepare(collect(run, test_steps, tag, lmin, tag[2], horizon=horizon), batch, seed=seed + 1)
-    out["test_eval"] = tg.evaluate(test)
-    del run, test
-
-    def tagged_run(learned: bool, every: int):
+    leaves, st = adapt_initial(cfg, B, lmin, lmax, lo, hi, funcs, tagq(4.0))
+    out["initial_leaves"] = len(leaves)
+    T = t_end if t_end is not None else test_steps * dt0 / (1 << lmin)
+    # how well each tagger predicts the plain criterion on the test ring
+    out["test_eval"] = {}
+    for R, tg in taggers.items():
         run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
-        leaves_sum = cu = falls = regrids = 0
+        test = prepare(collect(run, min(test_steps, 64), tagq(4.0), lmin, 4.0, horizon=R), batch, seed=seed + 1)
+        out["test_eval"][str(R)] = tg.evaluate(test)
+        del run, test
+
+    def tagged_run(c, tagger, every, thr, mode="batched"):
+        run = AMRRun(c, B, lmax, leaves, st, lo, hi, dt0, mode=mode)
+        leaves_sum = cu = falls = regrids = steps = 0
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        for k in range(test_steps):
-            if k % every == 0:
-                if learned:
-                    tags, nf = run.tags_learned(tg, *tag, cmin)
+        while run.time < T - 1e-12:
+            if steps % every == 0:
+                if tagger is not None:
+                    tags, nf = run.tags_learned(tagger, *tagq(thr), cmin)
                     falls += nf
                 else:
-                    tags, _ = run.tags(*tag)
+                    tags, _ = run.tags(*tagq(thr))
                 regrids += 1
                 run.regrid(tags, lmin)
             leaves_sum += run.forest.nleaf
             cu += run.cell_updates_per_coarse_step()
             run.coarse_step()
+            steps += 1
         torch.cuda.synchronize()
         el = time.perf_counter() - t2
-        r = {"regrids": regrids, "mean_leaves": leaves_sum / test_steps, "cell_updates": cu,
+        r = {"regrids": regrids, "coarse_steps": steps, "mean_leaves": leaves_sum / steps, "cell_updates": cu,
              "cell_updates_per_s": cu / el, "wall_s": round(el, 4), "t": run.time}
-        if learned:
+        if tagger is not None:
             r["fallback_fraction"] = falls / max(1, leaves_sum)
         return r, run
 
-    res, finals = {}, {}
-    for name, learned, every in (("plain_every_step", False, 1), (f"plain_every_{horizon}", False, horizon),
-                                 (f"learned_every_{horizon}", True, horizon)):
-        res[name], finals[name] = tagged_run(learned, every)
-    # reference: uniform finest level, run to the same time
+    # reference: uniform finest level to T
     side = B << lmax
     ref_leaves = [(lmax, x, y) for y in range(side) for x in range(side)]
     lv = np.array(ref_leaves, dtype=np.int64)
     rst = S.forest_state_fast(n, 3, B, lv[:, 0], lv[:, 1], lv[:, 2], funcs, lo, hi)
-    ref = AMRRun(cfg, B, lmax, ref_leaves, rst, lo, hi, dt0)
+    ref = AMRRun(cfg, B, lmax, ref_leaves, rst, lo, hi, dt0, graphs=True, tiling=_tiling_index(16, 16, 128))
     del rst
-    T = res["plain_every_step"]["t"]
-    for _ in range(int(round(T / ref.coarse_dt()))):
+    while ref.time < T - 1e-12:
         ref.coarse_step()
-    out["reference"] = {"leaves": len(ref_leaves), "t": ref.time}
+    out["reference"] = {"leaves": len(ref_leaves), "t": ref.time, "precision": "f32"}
     g = uniform_global(ref, 0)
     del ref
-    for name, run in finals.items():
-        res[name]["l1_p_vs_uniform"] = l1_vs_uniform(run, g, 0)
-    del finals
-    out["runs"] = res
-    pe, pr, lr_ = res["plain_every_step"], res[f"plain_every_{horizon}"], res[f"learned_every_{horizon}"]
-    out["l1_learned_over_plain_same_regrids"] = lr_["l1_p_vs_uniform"] / pr["l1_p_vs_uniform"]
-    out["l1_learned_over_plain_every_step"] = lr_["l1_p_vs_uniform"] / pe["l1_p_vs_uniform"]
-    out["throughput_learned_over_plain_every_step"] = lr_["cell_updates_per_s"] / pe["cell_updates_per_s"]
-    # inference cost on the initial forest of the test ring
+    runs = {}
+    for every in plain_intervals:
+        for thr in thresholds:
+            r, run = tagged_run(cfg, None, every, thr)
+            r["l1_p_vs_uniform"] = l1_vs_uniform(run, g, 0)
+            runs[f"plain_every_{every}_thr_{thr:g}"] = r
+            del run
+    for R, tg in taggers.items():
+        r, run = tagged_run(cfg, tg, R, 4.0)
+        r["l1_p_vs_uniform"] = l1_vs_uniform(run, g, 0)
+        runs[f"learned_every_{R}"] = r
+        del run
+    if fp64:
+        r, run = tagged_run(cfg64, None, 1, 4.0)
+        r["l1_p_vs_uniform"] = l1_vs_uniform(run, g, 0)
+        runs["plain_every_1_thr_4_f64_batched"] = r
+        del run
+    out["runs"] = runs
+    for v in runs.values():
+        assert abs(v["t"] - T) < 1e-9, (v["t"], T)
+    plain_front = pareto_front([(v["l1_p_vs_uniform"], v["cell_updates_per_s"]) for k, v in runs.items()
+                                if k.startswith("plain") and "f64" not in k])
+    learned_front = pareto_front([(v["l1_p_vs_uniform"], v["cell_updates_per_s"]) for k, v in runs.items()
+                                  if k.startswith("learned")])
+    out["pareto"] = {"plain_f32": plain_front, "learned_f32": learned_front}
+    # equal L1: at every point of either front, the other front's rate
+    matched = []
+    for l1, _ in plain_front + learned_front:
+        rp, rl = rate_at(plain_front, l1), rate_at(learned_front, l1)
+        if rp is not None and rl is not None:
+            matched.append({"l1": l1, "learned": rl, "plain": rp, "learned_over_plain": rl / rp})
+    out["equal_l1"] = sorted(matched, key=lambda m: m["l1"])
+    base = runs["plain_every_1_thr_4"]
+    out["equal_l1_at_plain_every_step"] = {
+        "l1": base["l1_p_vs_uniform"], "plain": base["cell_updates_per_s"],
+        "learned": rate_at(learned_front, base["l1_p_vs_uniform"])}
+    if fp64:
+        b64 = runs["plain_every_1_thr_4_f64_batched"]
+        out["fp64_batched_every_step"] = {"l1": b64["l1_p_vs_uniform"], "rate": b64["cell_updates_per_s"],
+                                          "learned_f32_at_that_l1": rate_at(learned_front, b64["l1_p_vs_uniform"]),
+                                          "plain_f32_at_that_l1": rate_at(plain_front, b64["l1_p_vs_uniform"])}
+    if per_patch:
+        run = AMRRun(cfg64, B, lmax, leaves, st, lo, hi, dt0, mode="per_patch")
+        run.coarse_step()
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        cu = 0
+        for _ in range(2):
+            cu += run.cell_updates_per_coarse_step()
+            run.coarse_step()
+        torch.cuda.synchronize()
+        out["fp64_per_patch"] = {"rate": cu / (time.perf_counter() - t3), "coarse_steps_timed": 2,
+                                 "l1": "as fp64_batched_every_step (same arithmetic, one launch per patch)"}
+        del run
+    # inference cost (inputs + forward) on the initial forest of the test ring, and the forward alone on a
+    # large batch, against the measured BF16 tensor peak
+    tg = taggers[intervals[len(intervals) // 2]]
     run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
-    x = run.cnn_inputs(tag[2])
+    x = run.cnn_inputs(4.0)
     fwd = tg.outputs(run.forest.nleaf)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     tg.forward(x, run.forest.d_level, fwd)
     e0.record(stream)
     for _ in range(10):
-        run.cnn_inputs(tag[2])
+        run.cnn_inputs(4.0)
         tg.forward(x, run.forest.d_level, fwd)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 10
-    flops = run.forest.nleaf * 2 * 32 * ((n + 2) ** 2 * 3 * 9 + n * n * 32 * 9)
+    flop = 2 * 32 * ((n + 2) ** 2 * 3 * 9 + n * n * 32 * 9)      # per patch: both convolutions
+    reps = max(1, 65536 // run.forest.nleaf)
+    xb = x.repeat(reps, 1, 1, 1).contiguous()
+    lb = run.forest.d_level.repeat(reps).contiguous()
+    fb = tg.outputs(int(lb.numel()))
+    tg.forward(xb, lb, fb)
+    e0.record(stream)
+    for _ in range(10):
+        tg.forward(xb, lb, fb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    msb = e0.elapsed_time(e1) / 10
+    peak = bf16_peak()
     out["inference"] = {"leaves": run.forest.nleaf, "ms_inputs_and_forward": ms,
-                        "tflops": flops / (ms * 1e-3) / 1e12}
+                        "tflops_inputs_and_forward": run.forest.nleaf * flop / (ms * 1e-3) / 1e12,
+                        "batch": int(lb.numel()), "ms_forward": msb,
+                        "tflops_forward": int(lb.numel()) * flop / (msb * 1e-3) / 1e12,
+                        "peak_tflops": peak[0], "peak_source": peak[1],
+                        "flop_per_patch": flop}
+    out["inference"]["frac_forward"] = out["inference"]["tflops_forward"] / peak[0]
     return out
+
+
+def tagger_kernels(nsample: int = 65536, steps: int = 20, warmup: int = 3, C: int = 3, N: int = 16,
+                   batch: int = 4096):
+    """The tagger's kernels alone on synthetic BF16 inputs (normal, seed 0):
+    af_cnn_forward on nsample patches, and a training step (forward,
+    backward, Adam) on `batch`; TFLOP/s of the two convolutions (forward)
+    against the measured BF16 tensor peak."""
+    import torch
+    from paper_2205_07572_gb300.tagger import Tagger
+    g = torch.Generator(device="cpu").manual_seed(0)
+    xf = torch.randn((nsample, C, N + 4, N + 4), generator=g) * 2.0
+    x = (xf.to(torch.bfloat16).view(torch.int16)).cuda()
+    level = torch.randint(0, 8, (nsample,), generator=g, dtype=torch.int32).cuda()
+    tg = Tagger(C, N, seed=0)
+    out = tg.outputs(nsample)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        tg.forward(x, level, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        tg.forward(x, level, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    flop = 2 * 32 * ((N + 2) ** 2 * C * 9 + N * N * 32 * 9)
+    peak = bf16_peak()
+    label = (torch.rand(batch, generator=g) > 0.5).float().cuda()
+    weight = torch.ones(batch).cuda()
+    xb, lb = x[:batch].contiguous(), level[:batch].contiguous()
+    fb = tg.outputs(batch)
+    for _ in range(warmup):
+        tg.train_step(xb, lb, label, weight, float(batch), 1e-4, fb)
+    e0.record(stream)
+    for _ in range(steps):
+        tg.train_step(xb, lb, label, weight, float(batch), 1e-4, fb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1) / steps
+    tf = nsample * flop / (ms * 1e-3) / 1e12
+    return {"shape": {"ncomp": C, "n": N, "channels": 32}, "forward": {
+                "samples": nsample, "ms": ms, "samples_per_s": nsample / (ms * 1e-3), "flop_per_sample": flop,
+                "tflops": tf, "peak_tflops": peak[0], "peak_source": peak[1], "frac": tf / peak[0]},
+            "train_step": {"batch": batch, "ms": ms_t, "samples_per_s": batch / (ms_t * 1e-3)}}
+
+
+def bf16_peak():
+    """Measured dense BF16 tensor peak (burst), TFLOP/s, and its source."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        if isinstance(d.get("bf16_tflops"), (int, float)):
+            return float(d["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except Exception:
+        pass
+    return 1900.0, "fallback"
 
 
 # ------------------------------------------------ variable-velocity advection
@@ -914,7 +1112,13 @@ def main():
                     help="only the learned-tagging experiment")
     ap.add_argument("--amr-only", action="store_true",
                     help="time only the adaptive-mesh workloads (one JSON object per workload)")
+    ap.add_argument("--tagger-only", action="store_true",
+                    help="only the learned tagger's forward and backward kernels on a synthetic batch")
+    ap.add_argument("--patches", type=int, default=128,
+                    help="patches per side of the uniform workload with --prec f32/f64 (profiling of a smaller case)")
     args = ap.parse_args()
+    if args.prec != "both":
+        globals()["P_SIDE"] = args.patches
     warm = max(3, args.warmup)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -964,7 +1168,8 @@ def main():
     if args.amr_only:
         if rank == 0:
             for case in AMR_CASES:
-                print(json.dumps({"amr": case, **amr_bench(case, 8, 4)}), flush=True)
+                print(json.dumps({"amr": case, **amr_bench(case, 8, 4, per_patch=AMR_CASES[case]["per_patch"])}),
+                      flush=True)
         return
     if args.amr_profile:
         if rank == 0:
@@ -977,6 +1182,10 @@ def main():
     if args.learned_only:
         if rank == 0:
             print(json.dumps({"learned_tagging": learned_tagging()}), flush=True)
+        return
+    if args.tagger_only:
+        if rank == 0:
+            print(json.dumps({"tagger_kernels": tagger_kernels(steps=args.steps, warmup=warm)}), flush=True)
         return
     if args.prec != "both":
         r = run_ours(args.prec, args.steps, warm, rank, world, dist)
@@ -1015,7 +1224,8 @@ def main():
                "fp32": {"achieved": f32_tf, "peak": peaks["fp32"], "unit": "TFLOP/s", "frac": f32_tf / peaks["fp32"]},
                "fp64": {"achieved": f64_tf, "peak": peaks["fp64"], "unit": "TFLOP/s", "frac": f64_tf / peaks["fp64"]},
                "peak_source": "measured: af_fma_throughput (8 independent FMA chains per thread, best of 5)"}
-        amr = {case: amr_bench(case, 8, 4) for case in AMR_CASES} if extras else None
+        amr = {case: amr_bench(case, 8, 4, per_patch=AMR_CASES[case]["per_patch"]) for case in AMR_CASES} \
+            if extras else None
         learned = learned_tagging() if extras else None
         var = var_velocity_bench() if extras else None
         v64 = world * cells / (r64["ms"] * 1e-3)

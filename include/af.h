@@ -246,7 +246,14 @@ af_status af_fma_throughput(int32_t prec, int32_t blocks, int32_t iters, void *d
  * cycles).  A tile whose wait gives up waits once more with the same limit
  * for its copies in flight, leaves its outputs unwritten and increments a
  * device counter.  Setting AF_WORK_SKIP_BULK_COPY in a work item's flags
- * makes that happen without any fault: its copies are never issued.  This call synchronises with the device, writes the
+ * makes that happen without any fault: its copies are never issued.  The
+ * learned tagger's kernels (af_cnn_forward, af_cnn_backward) wait the same
+ * bounded way for their tensor-core MMAs and count a wait that gives up in
+ * the same total (that CTA then stops: its remaining samples are left
+ * unwritten).  A CTA whose second wait also gives up (about two seconds in
+ * all, far beyond any copy or MMA of a working GPU) exits with its copies
+ * possibly still in flight; the step's results must then be discarded.
+ * This call synchronises with the device, writes the
  * counter to *count and, if reset != 0, sets it to zero.  AF_ERR_ARG if count
  * is NULL, AF_ERR_CUDA if the copy fails.  The counter is armed from the
  * first af_patch_step* call made outside CUDA stream capture. */
@@ -388,7 +395,9 @@ af_status af_fill_ghosts(const af_config *cfg, const af_forest *forest, uint32_t
  *      (16-byte aligned; zeroed by the call); after the build, scratch[2]
  *      is non-zero if the counts were too small (the plan is then unusable).
  * flags: AF_FILL_ALL_PATCHES includes leaves whose eight neighbours are all
- * same-level (as af_fill_ghosts).  Entries are in no particular order; each
+ * same-level (as af_fill_ghosts).  Each leaf's entries of a pass are
+ * contiguous and in lattice order (plane, row, column), so the exchange's
+ * accesses coalesce; the leaves' ranges are in no particular order.  Each
  * destination entry appears once, so the order does not change the result.
  *
  * af_fill_ghosts_planned runs the exchange for the leaves of `levels` from

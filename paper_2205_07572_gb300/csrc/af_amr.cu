@@ -363,25 +363,73 @@ __global__ void plan_count_kernel(DevForest F, int64_t plane, int flags, unsigne
 }
 
 // Pass-A entries fill [0, na), pass-B entries [na, na + nb); cursor[2] starts at 0.
+// Each leaf reserves one contiguous range per pass and writes its entries
+// there in lattice order (plane, row, column), so the threads of an
+// executing warp touch consecutive destination entries (and, for copies,
+// consecutive source entries): the exchange's accesses coalesce.  The order
+// of the leaves' ranges is whatever order the CTAs reserve them in; each
+// destination entry appears once, so the order does not change the result.
 __global__ void plan_build_kernel(DevForest F, int64_t plane, int flags, GhostEntry *plan, long long na, long long nb,
                                   unsigned long long *cursor, int *overflow) {
     const int p = blockIdx.x;
     __shared__ int s_use;
-    if (threadIdx.x == 0) s_use = plan_leaf(F, p, flags);
+    __shared__ unsigned int s_cnt[2];
+    __shared__ unsigned long long s_base[2];
+    __shared__ unsigned int s_warp[2][32];
+    if (threadIdx.x == 0) {
+        s_use = plan_leaf(F, p, flags);
+        s_cnt[0] = s_cnt[1] = 0;
+    }
     __syncthreads();
     if (!s_use) return;
     const int lp = __ldg(F.level + p), W = F.n + 2 * kGhost + 1;
-    for (int e = threadIdx.x; e < kPlanes * W * W; e += blockDim.x) {
+    const int total = kPlanes * W * W;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int k = e / (W * W), r = e - k * W * W;
         GhostEntry g;
-        if (!ghost_entry(F, plane, p, lp, k, r % W - kGhost, r / W - kGhost, g)) continue;
-        const int b = g.kind >= kGPoint;
-        const unsigned long long slot = atomicAdd(cursor + b, 1ull);
-        if ((long long)slot >= (b ? nb : na)) {
-            atomicExch(overflow, 1);
-            continue;
+        if (ghost_entry(F, plane, p, lp, k, r % W - kGhost, r / W - kGhost, g)) atomicAdd(&s_cnt[g.kind >= kGPoint], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(cursor + threadIdx.x, s_cnt[threadIdx.x]) : 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    unsigned long long run0 = s_base[0], run1 = s_base[1];
+    for (int e0 = 0; e0 < total; e0 += blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        GhostEntry g;
+        bool v = false;
+        if (e < total) {
+            const int k = e / (W * W), r = e - k * W * W;
+            v = ghost_entry(F, plane, p, lp, k, r % W - kGhost, r / W - kGhost, g);
         }
-        plan[(b ? na : 0) + (long long)slot] = g;
+        const int b = v ? (g.kind >= kGPoint) : 0;
+        const unsigned m0 = __ballot_sync(0xffffffffu, v && b == 0), m1 = __ballot_sync(0xffffffffu, v && b == 1);
+        if (lane == 0) {
+            s_warp[0][warp] = __popc(m0);
+            s_warp[1][warp] = __popc(m1);
+        }
+        __syncthreads();
+        unsigned off0 = 0, off1 = 0, tot0 = 0, tot1 = 0;
+        for (int w = 0; w < nwarp; ++w) {
+            if (w < warp) {
+                off0 += s_warp[0][w];
+                off1 += s_warp[1][w];
+            }
+            tot0 += s_warp[0][w];
+            tot1 += s_warp[1][w];
+        }
+        if (v) {
+            const unsigned long long slot = b ? run1 + off1 + __popc(m1 & below) : run0 + off0 + __popc(m0 & below);
+            if ((long long)slot >= (b ? nb : na)) {
+                atomicExch(overflow, 1);
+            } else {
+                plan[(b ? na : 0) + (long long)slot] = g;
+            }
+        }
+        run0 += tot0;
+        run1 += tot1;
+        __syncthreads();
     }
 }
 

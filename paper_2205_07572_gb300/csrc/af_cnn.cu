@@ -6,18 +6,31 @@
 // of the af_cnn_* entry points.
 //
 // Storage is BF16 (inputs, conv weights, layer-1 activations), arithmetic is
-// FP32 with FP32 accumulation.  One CTA runs one patch through both
-// convolutions in shared memory (the layer-1 map never leaves the SM); the
-// backward pass uses that the global max-pool passes gradient to one pixel
-// per channel, so it costs a small fraction of the forward pass, and it
-// accumulates per-CTA partial gradients that a second kernel sums in a
-// fixed order (deterministic).
+// FP32 with FP32 accumulation.  Both convolutions run on the tensor cores
+// (tcgen05.mma, BF16 operands in shared memory, FP32 accumulators in tensor
+// memory) as implicit GEMMs, one patch at a time per CTA:
+//   layer 1: D1[pixel][g] = sum_k Xim[pixel][k] W1[g][k], k = (c, ky, kx)
+//            (the patch's im2col, K = 9 C padded to 16 or 32), M = the
+//            (n+2)^2 pixels in tiles of 128, N = 32 channels;
+//   layer 2: D2[pixel][g] = sum_{ky,kx} sum_f A1[f][y+ky][x+kx] W2[g][f][ky][kx]
+//            as nine accumulating GEMMs with K = 32 channels, their A
+//            operands read from three copies of the layer-1 map shifted by
+//            kx = 0, 1, 2 columns (so that every 128-pixel tile is a
+//            uniformly strided operand), M = n^2 output pixels, N = 32.
+// The epilogues read the accumulators back (tcgen05.ld): layer 1 adds the
+// level embedding, applies relu and BF16 rounding and writes the shifted
+// copies; layer 2 adds b2 and reduces the global max-pool (value and first
+// row-major position per channel).  The backward pass recomputes layer 1 the
+// same way, uses that the max-pool passes gradient to one pixel per channel
+// (a small fraction of the forward work), and accumulates per-CTA partial
+// gradients that a second kernel sums in a fixed order (deterministic).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 
 #include "af_internal.h"
+#include "af_tc.cuh"
 
 namespace af {
 namespace {
@@ -78,123 +91,309 @@ __device__ void load_weights(const float *__restrict__ P, float *sm) {
     if (threadIdx.x == 0) sm[L::b3] = P[off_b3(C)];
 }
 
-// Input of sample b and the layer-1 map A1 = bf16(relu(conv(X, W1) + emb)).
-template <int C, int N>
-__device__ void layer1(const __nv_bfloat16 *__restrict__ X, int b, int level, float *sm) {
-    using L = Smem<C, N>;
-    constexpr int S = L::S, S1 = L::S1;
-    const __nv_bfloat16 *xb = X + (int64_t)b * C * S * S;
-    for (int e = threadIdx.x; e < C * S * S; e += blockDim.x) sm[L::x + e] = __bfloat162float(xb[e]);
-    __syncthreads();
-    const float *emb = sm + L::emb + level * kF;
-    for (int e = threadIdx.x; e < kF * S1 * S1; e += blockDim.x) {
-        const int f = e / (S1 * S1), r = e - f * S1 * S1, y = r / S1, x = r - y * S1;
-        float z = 0.f;
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                for (int kx = 0; kx < 3; ++kx)
-                    z = fmaf(sm[L::w1 + ((f * C + c) * 3 + ky) * 3 + kx], sm[L::x + (c * S + y + ky) * S + x + kx], z);
-        z += emb[f];
-        sm[L::a1 + e] = rbf(fmaxf(z, 0.f));
+// Bounded tensor-core waits that gave up (read by af_step_wait_timeouts).
+__device__ unsigned int g_cnn_timeouts;
+
+__host__ __device__ constexpr int align128(int b) { return (b + 127) / 128 * 128; }
+__host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
+
+// Tensor-core geometry and shared-memory regions (bytes) of the two
+// convolutions for n x n patches (N = n, C components).  BWD: the backward
+// pass's layout (layer 1 only: no W2t, the region holds the im2col only).
+template <int C, int N, bool BWD = false>
+struct TcGeo {
+    static constexpr int S = N + 4, S1 = N + 2;
+    static constexpr int P1 = S1 * S1;                // layer-1 pixels
+    static constexpr int MT1 = (P1 + 127) / 128;      // layer-1 M tiles of 128 pixels
+    static constexpr int K1 = C * 9 <= 16 ? 16 : 32;  // layer-1 K: 9 C padded to the MMA's K step
+    static constexpr int KC1 = K1 / 8;                // 8-wide column blocks of Xim / W1t
+    static constexpr int RT = 128 / N;                // output rows per layer-2 M tile
+    static constexpr int MT2 = (N * N + 127) / 128;   // layer-2 M tiles
+    static constexpr int R2 = MT2 * RT + 2;           // rows of each shifted copy of A1 (>= S1)
+    static constexpr int xim_chunk = MT1 * 128 * 16;  // Xim column block: MT1*128 rows of 16 bytes
+    static constexpr int a1_chunk = R2 * N * 16;      // one 8-channel block of one shifted copy
+    static constexpr int a1_copy = 4 * a1_chunk;      // one shifted copy (32 channels)
+    static constexpr int xs = 0;                                   // input patch, BF16 [C][S][S]
+    static constexpr int w1t = align128(C * S * S * 2);            // layer-1 B: [KC1][32 g][8 k] BF16
+    static constexpr int w2t = w1t + KC1 * 32 * 16;                // layer-2 B: [9][4][32 g][8 f] BF16
+    static constexpr int reg = w2t + (BWD ? 0 : 9 * 4 * 32 * 16);   // Xim, then (aliased) A1s
+    static constexpr int reg_bytes = BWD ? KC1 * xim_chunk : imax(KC1 * xim_chunk, 3 * a1_copy);
+    static constexpr int end = reg + reg_bytes;
+    static_assert(S1 <= R2, "shifted copies hold every layer-1 row");
+    static_assert(128 % N == 0, "output rows tile the 128-pixel M tile");
+};
+constexpr int kTmemCols = 128;  // >= 32 x max(MT1, MT2) columns of FP32 accumulators
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+
+// The tensor-core B operands (BF16, K-major core-matrix blocks) from the
+// FP32 parameters: W1t[kc][g][kk] = W1[g][k = 8 kc + kk] (zero for k >= 9C),
+// W2t[ky*3+kx][kc][g][kk] = W2[g][8 kc + kk][ky][kx].
+template <int C, int N, int NT, bool BWD>
+__device__ void tc_load_weights(const float *__restrict__ P, unsigned char *smem) {
+    using G = TcGeo<C, N, BWD>;
+    uint16_t *w1 = reinterpret_cast<uint16_t *>(smem + G::w1t);
+    for (int e = threadIdx.x; e < G::KC1 * 32 * 8; e += NT) {
+        const int kk = e & 7, g = (e >> 3) & 31, kc = e >> 8, k = kc * 8 + kk;
+        w1[e] = k < C * 9 ? bf16_bits(P[off_w1() + g * C * 9 + k]) : (uint16_t)0;
     }
-    __syncthreads();
+    if (BWD) return;
+    uint16_t *w2 = reinterpret_cast<uint16_t *>(smem + G::w2t);
+    for (int e = threadIdx.x; e < 9 * 4 * 32 * 8; e += NT) {
+        const int kk = e & 7, g = (e >> 3) & 31, kc = (e >> 8) & 3, sft = e >> 10;
+        w2[e] = bf16_bits(P[off_w2(C) + (g * kF + kc * 8 + kk) * 9 + sft]);
+    }
 }
 
-// Layer 2 and the global max-pool: thread (cg, row) computes channels
-// 2cg, 2cg+1 of output row `row`; returns per channel the maximum of
-// Z2 = conv(A1, W2) + b2 and its first row-major position.
+// Issue (one thread) layer 1's MMAs for the im2col in the Xim region and
+// commit them to *bar.
+template <int C, int N, bool BWD>
+__device__ __forceinline__ void tc_issue_layer1(unsigned char *smem, uint32_t tmem, uint64_t *bar) {
+    using G = TcGeo<C, N, BWD>;
+    const uint32_t a0 = tc::saddr(smem + G::reg), b0 = tc::saddr(smem + G::w1t);
+    constexpr uint32_t id = tc::idesc_bf16(128, 32);
+#pragma unroll
+    for (int mt = 0; mt < G::MT1; ++mt)
+#pragma unroll
+        for (int ks = 0; ks < G::KC1 / 2; ++ks)
+            tc::mma_bf16(tmem + 32 * mt, tc::smem_desc(a0 + ks * 2 * G::xim_chunk + mt * 128 * 16, G::xim_chunk, 128),
+                         tc::smem_desc(b0 + ks * 2 * 32 * 16, 32 * 16, 128), id, ks > 0);
+    tc::mma_commit(bar);
+}
+
+// Issue (one thread) layer 2's MMAs (nine shifts x two K steps per M tile)
+// for the shifted copies in the A1s region and commit them to *bar.
 template <int C, int N>
-__device__ void layer2_max(const float *sm, float *mval, int *marg) {
-    using L = Smem<C, N>;
-    constexpr int S1 = L::S1;
-    const int cg = threadIdx.x / N, row = threadIdx.x - cg * N;
-    const bool active = cg < kF / 2;
-    float acc[2][N];
+__device__ __forceinline__ void tc_issue_layer2(unsigned char *smem, uint32_t tmem, uint64_t *bar) {
+    using G = TcGeo<C, N>;
+    const uint32_t a0 = tc::saddr(smem + G::reg), b0 = tc::saddr(smem + G::w2t);
+    constexpr uint32_t id = tc::idesc_bf16(128, 32);
+#pragma unroll 1
+    for (int mt = 0; mt < G::MT2; ++mt)
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+        for (int sft = 0; sft < 9; ++sft) {
+            const int ky = sft / 3, kx = sft - 3 * ky;
 #pragma unroll
-        for (int x = 0; x < N; ++x) acc[h][x] = 0.f;
-    if (active) {
-        const float *w0 = sm + L::w2 + (2 * cg) * kW2Pitch, *w1 = w0 + kW2Pitch;
-        for (int f = 0; f < kF; ++f) {
+            for (int ks = 0; ks < 2; ++ks)
+                tc::mma_bf16(tmem + 32 * mt,
+                             tc::smem_desc(a0 + kx * G::a1_copy + 2 * ks * G::a1_chunk + (mt * G::RT + ky) * N * 16,
+                                           G::a1_chunk, 128),
+                             tc::smem_desc(b0 + sft * 4 * 32 * 16 + 2 * ks * 32 * 16, 32 * 16, 128), id,
+                             sft > 0 || ks > 0);
+        }
+    tc::mma_commit(bar);
+}
+
+// Wait (every thread) for the MMAs committed to *bar, phase `parity`; all
+// threads agree on the outcome.  On a wait that gave up: count it, wait once
+// more (bounded) so nothing is in flight when the caller frees its tensor
+// memory, and return false.
+template <int NT>
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity) {
+    const bool ok = tc::mbar_wait(bar, parity);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicAdd(&g_cnn_timeouts, 1u);
+            tc::mbar_wait(bar, parity);
+        }
+        __syncthreads();
+        return false;
+    }
+    tc::fence_after_sync();
+    return true;
+}
+
+// Layer 1 of sample b on the tensor cores: input patch, im2col, MMAs, and
+// the epilogue A1 = bf16(relu(D1 + emb[level])) written either as the three
+// shifted BF16 copies layer 2 reads (F32OUT false) or as an FP32 map
+// a1[f][y][x] (F32OUT true, the backward pass).  Ends with a barrier; false
+// if the wait gave up.
+template <int C, int N, int NT, bool F32OUT>
+__device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const float *emb, unsigned char *smem,
+                          uint32_t tmem, uint64_t *bar, unsigned &phase, float *a1) {
+    using G = TcGeo<C, N, F32OUT>;
+    constexpr int S = G::S, S1 = G::S1;
+    const uint16_t *xb = reinterpret_cast<const uint16_t *>(X) + (int64_t)b * C * S * S;
+    uint16_t *xs = reinterpret_cast<uint16_t *>(smem + G::xs);
+    for (int e = threadIdx.x; e < C * S * S; e += NT) xs[e] = xb[e];
+    __syncthreads();
+    // im2col: Xim[kc][m][kk] = X[c][y + ky][x + kx], k = 8 kc + kk = 9 c + 3 ky + kx, m = y S1 + x
+    uint16_t *xim = reinterpret_cast<uint16_t *>(smem + G::reg);
+    for (int e = threadIdx.x; e < G::KC1 * G::MT1 * 128 * 8; e += NT) {
+        const int kk = e & 7, r = e >> 3, m = r % (G::MT1 * 128), kc = r / (G::MT1 * 128), k = kc * 8 + kk;
+        uint16_t v = 0;
+        if (m < G::P1 && k < C * 9) {
+            const int c = k / 9, q = k - 9 * c, ky = q / 3, kx = q - 3 * ky, y = m / S1, x = m - y * S1;
+            v = xs[(c * S + y + ky) * S + x + kx];
+        }
+        xim[e] = v;
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after_sync();
+        tc_issue_layer1<C, N, F32OUT>(smem, tmem, bar);
+    }
+    if (!tc_wait<NT>(bar, phase)) return false;
+    phase ^= 1u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+    for (int mt = warp >> 2; mt < G::MT1; mt += NT / 128) {
+        float z[32];
+        tc::tmem_ld32(tmem + lanes + 32 * mt, z);
+        const int m = mt * 128 + 32 * (warp & 3) + lane;
+        if (m < G::P1) {
+            const int y = m / S1, x = m - y * S1;
+            if constexpr (F32OUT) {
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-                float a[N + 2];
-                const float *src = sm + L::a1 + (f * S1 + row + ky) * S1;
+                for (int g = 0; g < kF; ++g) a1[g * G::P1 + m] = rbf(fmaxf(z[g] + emb[g], 0.f));
+            } else {
 #pragma unroll
-                for (int x = 0; x < N + 2; ++x) a[x] = src[x];
+                for (int kc = 0; kc < 4; ++kc) {
+                    uint32_t w[4];
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const float u = w0[f * 9 + ky * 3 + kx], v = w1[f * 9 + ky * 3 + kx];
+                    for (int h = 0; h < 4; ++h) {
+                        const int g = kc * 8 + 2 * h;
+                        w[h] = (uint32_t)bf16_bits(fmaxf(z[g] + emb[g], 0.f)) |
+                               ((uint32_t)bf16_bits(fmaxf(z[g + 1] + emb[g + 1], 0.f)) << 16);
+                    }
+                    const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
 #pragma unroll
-                    for (int x = 0; x < N; ++x) {
-                        acc[0][x] = fmaf(u, a[x + kx], acc[0][x]);
-                        acc[1][x] = fmaf(v, a[x + kx], acc[1][x]);
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const int xp = x - kx;
+                        if (xp >= 0 && xp < N)
+                            *reinterpret_cast<uint4 *>(smem + G::reg + kx * G::a1_copy + kc * G::a1_chunk +
+                                                       (y * N + xp) * 16) = v;
                     }
                 }
             }
         }
     }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const float bias = active ? sm[L::b2 + 2 * cg + h] : 0.f;
-        float best = -INFINITY;
-        int bi = 0x7fffffff;
-#pragma unroll
-        for (int x = 0; x < N; ++x) {
-            const float z = acc[h][x] + bias;
-            if (z > best) {
-                best = z;
-                bi = row * N + x;
-            }
-        }
-        // reduce over the N rows held by consecutive lanes
-#pragma unroll
-        for (int o = N / 2; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o, N);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o, N);
-            if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-            }
-        }
-        if (active && row == 0) {
-            mval[2 * cg + h] = best > 0.f ? best : 0.f;
-            marg[2 * cg + h] = best > 0.f ? bi : -1;
-        }
-    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    return true;
 }
 
+// Forward pass: one CTA (one warpgroup) per patch at a time.
 template <int C, int N>
-__global__ void __launch_bounds__(256) cnn_forward_kernel(int nsample, const __nv_bfloat16 *__restrict__ X,
+__global__ void __launch_bounds__(128) cnn_forward_kernel(int nsample, const __nv_bfloat16 *__restrict__ X,
                                                           const int32_t *__restrict__ level,
                                                           const float *__restrict__ P, float *__restrict__ logit,
                                                           float *__restrict__ Mout, int32_t *__restrict__ Aout) {
-    using L = Smem<C, N>;
-    extern __shared__ __align__(16) float sm[];
-    __shared__ int s_arg[kF];
-    load_weights<C, N>(P, sm);
+    using G = TcGeo<C, N>;
+    constexpr int NT = 128;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    __shared__ float s_emb[kLevels * kF], s_b2[kF], s_w3[kF], s_b3;
+    __shared__ float s_best[4][kF];
+    __shared__ int s_idx[4][kF];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    tc_load_weights<C, N, NT, false>(P, smem);
+    for (int e = threadIdx.x; e < kLevels * kF; e += NT) s_emb[e] = P[off_emb(C) + e];
+    if (threadIdx.x < kF) {
+        s_b2[threadIdx.x] = P[off_b2(C) + threadIdx.x];
+        s_w3[threadIdx.x] = P[off_w3(C) + threadIdx.x];
+    }
+    if (threadIdx.x == 0) {
+        s_b3 = P[off_b3(C)];
+        tc::mbar_init(&bar, 1);
+    }
+    if (warp == 0) tc::tmem_alloc(&tslot, kTmemCols);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
     __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tslot, lanes = (uint32_t)(32 * warp) << 16;
+    unsigned phase = 0;
     for (int b = blockIdx.x; b < nsample; b += gridDim.x) {
         const int lv = min(max(level[b], 0), kLevels - 1);
-        layer1<C, N>(X, b, lv, sm);
-        layer2_max<C, N>(sm, sm + L::m, s_arg);
+        if (!tc_layer1<C, N, NT, false>(X, b, s_emb + lv * kF, smem, tmem, &bar, phase, nullptr)) break;
+        if (threadIdx.x == 0) {
+            tc::fence_after_sync();
+            tc_issue_layer2<C, N>(smem, tmem, &bar);
+        }
+        if (!tc_wait<NT>(&bar, phase)) break;
+        phase ^= 1u;
+        // max-pool of Z2 = D2 + b2 over the n^2 output pixels (pixel index =
+        // row-major position y n + x; the first maximum wins)
+        float best[kF];
+        int bi[kF];
+#pragma unroll
+        for (int g = 0; g < kF; ++g) {
+            best[g] = -INFINITY;
+            bi[g] = 0x7fffffff;
+        }
+#pragma unroll 1
+        for (int mt = 0; mt < G::MT2; ++mt) {
+            float z[32];
+            tc::tmem_ld32(tmem + lanes + 32 * mt, z);
+            const int p = mt * 128 + 32 * warp + lane;
+            if (p < N * N) {
+#pragma unroll
+                for (int g = 0; g < kF; ++g) {
+                    const float v = z[g] + s_b2[g];
+                    if (v > best[g]) {
+                        best[g] = v;
+                        bi[g] = p;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kF; ++g) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best[g], o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi[g], o);
+                if (ob > best[g] || (ob == best[g] && oi < bi[g])) {
+                    best[g] = ob;
+                    bi[g] = oi;
+                }
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int g = 0; g < kF; ++g) {
+                s_best[warp][g] = best[g];
+                s_idx[warp][g] = bi[g];
+            }
+        }
+        tc::fence_before_sync();
         __syncthreads();
-        if (threadIdx.x < 32) {
-            const int g = threadIdx.x;
-            float v = sm[L::w3 + g] * sm[L::m + g];
+        if (warp == 0) {
+            const int g = lane;
+            float bv = s_best[0][g];
+            int ix = s_idx[0][g];
+#pragma unroll
+            for (int w = 1; w < 4; ++w) {
+                const float ob = s_best[w][g];
+                const int oi = s_idx[w][g];
+                if (ob > bv || (ob == bv && oi < ix)) {
+                    bv = ob;
+                    ix = oi;
+                }
+            }
+            const float mg = bv > 0.f ? bv : 0.f;
+            float v = s_w3[g] * mg;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            Mout[(int64_t)b * kF + g] = sm[L::m + g];
-            Aout[(int64_t)b * kF + g] = s_arg[g];
-            if (g == 0) logit[b] = v + sm[L::b3];
+            Mout[(int64_t)b * kF + g] = mg;
+            Aout[(int64_t)b * kF + g] = bv > 0.f ? ix : -1;
+            if (g == 0) logit[b] = v + s_b3;
         }
         __syncthreads();
     }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
+
+// Byte offset of the backward pass's tensor-core region, after its FP32 arrays.
+template <int C, int N>
+__host__ __device__ constexpr int bwd_tc_offset() { return align128(4 * Smem<C, N>::bwd_end); }
 
 template <int C, int N>
 __global__ void __launch_bounds__(256) cnn_backward_kernel(int nsample, const __nv_bfloat16 *__restrict__ X,
@@ -209,16 +408,32 @@ __global__ void __launch_bounds__(256) cnn_backward_kernel(int nsample, const __
     using L = Smem<C, N>;
     constexpr int S = L::S, S1 = L::S1;
     constexpr int NP = cnn_params(C);
-    extern __shared__ __align__(16) float sm[];
+    constexpr int NT = 256;
+    extern __shared__ __align__(128) float sm[];
     __shared__ float s_dz[kF];
     __shared__ int s_arg[kF];
     __shared__ float s_dlogit;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    unsigned char *const tcs = reinterpret_cast<unsigned char *>(sm) + bwd_tc_offset<C, N>();
     load_weights<C, N>(P, sm);
+    tc_load_weights<C, N, NT, true>(P, tcs);
     for (int e = threadIdx.x; e < L::bwd_end - L::gw1; e += blockDim.x) sm[L::gw1 + e] = 0.f;
+    if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+    if (threadIdx.x < 32) tc::tmem_alloc(&tslot, kTmemCols);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
     __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    unsigned phase = 0;
     for (int b = blockIdx.x; b < nsample; b += gridDim.x) {
         const int lv = min(max(level[b], 0), kLevels - 1);
-        layer1<C, N>(X, b, lv, sm);
+        // layer 1 recomputed on the tensor cores (A1 as an FP32 map), and the
+        // input patch in FP32 for the W1 gradient
+        if (!tc_layer1<C, N, NT, true>(X, b, sm + L::emb + lv * kF, tcs, tmem, &bar, phase, sm + L::a1)) break;
+        const uint16_t *xs = reinterpret_cast<const uint16_t *>(tcs + TcGeo<C, N, true>::xs);
+        for (int e = threadIdx.x; e < C * S * S; e += NT) sm[L::x + e] = __uint_as_float((uint32_t)xs[e] << 16);
         if (threadIdx.x == 0) {
             const float l = logit[b];
             s_dlogit = omega[b] * (1.f / (1.f + expf(-l)) - label[b]) * inv_omega_sum;
@@ -276,6 +491,9 @@ __global__ void __launch_bounds__(256) cnn_backward_kernel(int nsample, const __
         }
         __syncthreads();
     }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(tmem, kTmemCols);
     // partial gradient of this CTA, in parameter order
     float *out = partial + (int64_t)blockIdx.x * NP;
     for (int e = threadIdx.x; e < NP; e += blockDim.x) {
@@ -380,10 +598,12 @@ __global__ void combine_kernel(int n, const float *__restrict__ logit, const int
     tags[i] = t;
 }
 
+// Allows `bytes` of dynamic shared memory (the default limit of 48 KB covers
+// static and dynamic shared memory together).
 template <typename K>
 af_status smem_attr(K k, size_t bytes) {
     if (bytes > 227 * 1024) return AF_ERR_UNIMPLEMENTED;
-    if (bytes > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return AF_ERR_CUDA;
     return AF_OK;
 }
@@ -394,10 +614,18 @@ template <int C, int N>
 af_status forward_launch(int nsample, const void *X, const int32_t *lev, const float *P, float *lg, float *M,
                          int32_t *A, cudaStream_t s) {
     auto k = cnn_forward_kernel<C, N>;
-    const size_t bytes = sizeof(float) * Smem<C, N>::fwd_end;
+    const size_t bytes = TcGeo<C, N>::end;
     if (const af_status e = smem_attr(k, bytes)) return e;
-    const int grid = nsample < 152 * 4 ? nsample : 152 * 4;
-    k<<<grid, 256, bytes, s>>>(nsample, static_cast<const __nv_bfloat16 *>(X), lev, P, lg, M, A);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, bytes) != cudaSuccess)
+        return AF_ERR_CUDA;
+    // tensor memory: at most 512 columns per SM
+    per_sm = per_sm < 1 ? 1 : (per_sm > 512 / kTmemCols ? 512 / kTmemCols : per_sm);
+    const int slots = sms * per_sm;
+    const int grid = nsample < slots ? nsample : slots;
+    k<<<grid, 128, bytes, s>>>(nsample, static_cast<const __nv_bfloat16 *>(X), lev, P, lg, M, A);
     return launched();
 }
 
@@ -406,7 +634,7 @@ af_status backward_launch(int nsample, const void *X, const int32_t *lev, const 
                           const float *M, const int32_t *A, const float *y, const float *om, float inv_om,
                           float *partial, int nblocks, float *grad, cudaStream_t s) {
     auto k = cnn_backward_kernel<C, N>;
-    const size_t bytes = sizeof(float) * Smem<C, N>::bwd_end;
+    const size_t bytes = bwd_tc_offset<C, N>() + TcGeo<C, N, true>::end;
     if (const af_status e = smem_attr(k, bytes)) return e;
     k<<<nblocks, 256, bytes, s>>>(nsample, static_cast<const __nv_bfloat16 *>(X), lev, P, lg, M, A, y, om, inv_om,
                                   partial);
@@ -419,6 +647,19 @@ af_status backward_launch(int nsample, const void *X, const int32_t *lev, const 
 bool cnn_shape_ok(int ncomp, int n) { return (ncomp == 1 || ncomp == 3) && (n == 8 || n == 16); }
 
 }  // namespace
+
+// Reads (and, if reset, clears) the count of tagger kernels whose bounded
+// tensor-core wait gave up.
+af_status wait_timeouts_cnn(unsigned int *count, bool reset) {
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_cnn_timeouts, sizeof(v)) != cudaSuccess) return AF_ERR_CUDA;
+    *count = v;
+    if (reset && v != 0) {
+        const unsigned int zero = 0;
+        if (cudaMemcpyToSymbol(g_cnn_timeouts, &zero, sizeof(zero)) != cudaSuccess) return AF_ERR_CUDA;
+    }
+    return AF_OK;
+}
 }  // namespace af
 
 using namespace af;

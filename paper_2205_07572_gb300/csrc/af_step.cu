@@ -186,13 +186,14 @@ extern "C" af_status af_patch_step(const af_config *cfg, int32_t nwork, const af
 
 extern "C" af_status af_step_wait_timeouts(uint32_t *count, int32_t reset) {
     if (count == nullptr) return AF_ERR_ARG;
-    unsigned int a = 0, b = 0, c = 0, d = 0, e = 0;
+    unsigned int a = 0, b = 0, c = 0, d = 0, e = 0, f = 0;
     af_status st = af::wait_timeouts_f32(&a, reset != 0);
     if (st == AF_OK) st = af::wait_timeouts_f64(&b, reset != 0);
     if (st == AF_OK) st = af::wait_timeouts_f32_n16(&c, reset != 0);
     if (st == AF_OK) st = af::wait_timeouts_f32_n32(&d, reset != 0);
     if (st == AF_OK) st = af::wait_timeouts_var(&e, reset != 0);
+    if (st == AF_OK) st = af::wait_timeouts_cnn(&f, reset != 0);
     if (st != AF_OK) return st;
-    *count = a + b + c + d + e;
+    *count = a + b + c + d + e + f;
     return AF_OK;
 }

@@ -1006,6 +1006,7 @@ af_status wait_timeouts_f64(unsigned int *count, bool reset);
 af_status wait_timeouts_f32_n16(unsigned int *count, bool reset);
 af_status wait_timeouts_f32_n32(unsigned int *count, bool reset);
 af_status wait_timeouts_var(unsigned int *count, bool reset);
+af_status wait_timeouts_cnn(unsigned int *count, bool reset);
 
 // Instantiated once each, in af_step_f32.cu and af_step_f64.cu.
 extern template af_status launch_step<float, AF_ACOUSTICS>(int, const StepArgs<float> &,

@@ -148,6 +148,17 @@ def ring_wave_at(r0: float, width: float = 0.001, k: float = 80.0):
     return f
 
 
+def per_unit_tree(f, origin=(0.0, 0.0)):
+    """f repeated in every unit tree [ox + k, ox + k + 1) x [oy + m, oy + m + 1)
+    (k, m integers) of a brick, each copy the values f takes on the tree at
+    the origin: g(x, y) = f(ox + frac(x - ox), oy + frac(y - oy))."""
+    ox, oy = origin
+
+    def g(x, y):
+        return f(ox + np.mod(x - ox, 1.0), oy + np.mod(y - oy, 1.0))
+    return g
+
+
 def swirl_gaussians(x, y):
     """Two Gaussians exp(-100 |x - c|^2) at (0.5, 0.25) and (0.5, 0.75) (Section 4.3)."""
     return np.exp(-100.0 * ((x - 0.5) ** 2 + (y - 0.25) ** 2)) + np.exp(-100.0 * ((x - 0.5) ** 2 + (y - 0.75) ** 2))

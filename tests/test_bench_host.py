@@ -84,3 +84,19 @@ def test_clock_sampler_follows_a_remapped_device(tmp_path, monkeypatch):
     ck.stop()
     args = (tmp_path / "args.txt").read_text().split()
     assert args[:2] == ["-i", "GPU-1234abcd-0000-1111-2222-333344445555"]
+
+
+def test_pareto_front_and_rate_at_equal_l1():
+    """The equal-L1 comparison of the learned-tagging runs: a Pareto front
+    keeps the points no other point beats (lower L1 and higher rate), and
+    rate_at interpolates a front in log L1 / log rate, is None below its
+    lowest L1 and holds its best rate beyond its largest."""
+    import math
+    pts = [(2e-3, 3.0), (1e-3, 1.0), (1.5e-3, 0.5), (3e-3, 2.0), (4e-3, 4.0)]
+    assert bench.pareto_front(pts) == [(1e-3, 1.0), (2e-3, 3.0), (4e-3, 4.0)]
+    fr = [(1e-3, 1.0), (4e-3, 4.0)]
+    assert bench.rate_at(fr, 5e-4) is None
+    assert math.isclose(bench.rate_at(fr, 2e-3), 2.0)
+    assert math.isclose(bench.rate_at(fr, 1e-3), 1.0)
+    assert bench.rate_at(fr, 1e-2) == 4.0
+    assert bench.rate_at([], 1e-3) is None

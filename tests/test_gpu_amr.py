@@ -491,3 +491,82 @@ def test_bench_amr_workloads_conserve_mass_at_full_size(af, case):
     m1 = run.mass()
     assert np.abs(m1 - m0).max() < 1e-12 * max(1.0, np.abs(m0).max()), (m0, m1)
     assert af.step_wait_timeouts() == 0
+
+
+def _input_as_kernel_reads(lat, nbr, p, n):
+    """Lattice of leaf p as the step kernel stages it: its own entries (ghost
+    ring from the exchange), with every entry in a direction that has a
+    same-level neighbour read from that neighbour's entry at the same place
+    (the same-level ghost copy fused into the kernel's halo load)."""
+    out = lat[p].copy()
+    w = n + 2 * G + 1
+    for J in range(w):
+        for I in range(w):
+            li, lj = I - G, J - G
+            sx = -1 if li < 0 else (1 if li >= n else 0)
+            sy = -1 if lj < 0 else (1 if lj >= n else 0)
+            if sx == 0 and sy == 0:
+                continue
+            d = (0 if sx < 0 else 1) if sy == 0 else ((2 if sy < 0 else 3) if sx == 0 else
+                                                       4 + (sx > 0) + 2 * (sy > 0))
+            q = nbr[p, d]
+            if q >= 0:
+                out[:, :, J, I] = lat[q, :, :, lj - sy * n + G, li - sx * n + G]
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bench_acoustics_forest_sampled_leaves_match_oracle(af, prec):
+    """The benchmark's acoustics forest at full size (levels 3-7, 4944
+    leaves of 16 x 16 cells), in the launch configuration it times (batched
+    work list, 16 x 16-cell tiles, after graph-replayed coarse steps): the
+    first substep of a coarse step advances every level in one launch;
+    sampled leaves of every level -- with and without coarser or finer
+    neighbours -- equal the oracle's single-patch step on the input the
+    kernel read, every interior average and point value (FP64 1e-12, FP32
+    1e-5, normwise against each component's largest value on the
+    samples)."""
+    import bench
+    from paper_2205_07572_gb300.amr import AMRRun
+    case = "acoustics_levels3-7"
+    leaves, st = bench.amr_initial(case)
+    c = bench.AMR_CASES[case]
+    n, nc = bench.AMR_N, 3
+    dx0 = (c["hi"][0] - c["lo"][0]) / (c["B"] * n)
+    dt0 = bench.CFL * dx0
+    k = [t[:3] for t in af.step_tilings()].index((16, 16, 128))
+    run = AMRRun(af.config(1, prec, n, c=1.0), c["B"], c["lmax"], leaves, st, c["lo"], c["hi"], dt0,
+                 graphs=True, tiling=k)
+    assert run.forest.nleaf > 4000
+    for _ in range(4):
+        run.coarse_step()
+    torch.cuda.synchronize()
+    F = run.forest
+    lay = S.Layout(n, nc)
+    before = lay.lattice(run.current().double().cpu().numpy().reshape(F.nleaf, nc, 4, -1)).copy()
+    af.step_wait_timeouts(reset=True)
+    run.advance_from(F.levels[0])
+    torch.cuda.synchronize()
+    after = lay.lattice(run.current().double().cpu().numpy().reshape(F.nleaf, nc, 4, -1))
+    assert af.step_wait_timeouts() == 0
+    rng = np.random.default_rng(5)
+    ext = (F.nbr < 0).any(axis=1)
+    samples = []
+    for l in F.levels:
+        for kind in (True, False):
+            idx = np.nonzero((F.level == l) & (ext == kind))[0]
+            if len(idx):
+                samples += rng.choice(idx, size=min(4, len(idx)), replace=False).tolist()
+    assert ext[samples].any() and (~ext[samples]).any()
+    got, ref = [], []
+    for p in samples:
+        l = int(F.level[p])
+        cf = O.cfg(1, n, dx0 / (1 << l), dx0 / (1 << l), dt0 / (1 << l), c=1.0)
+        patch = np.zeros((nc, 4, lay.plane))
+        lay.lattice(patch)[...] = _input_as_kernel_reads(before, F.nbr, p, n)
+        ref.append(lay.lattice(O.step_patch(cf, patch))[..., G:G + n, G:G + n])
+        got.append(after[p][..., G:G + n, G:G + n])
+    got, ref = np.array(got), np.array(ref)
+    for comp in range(nc):
+        err = np.abs(got[:, comp] - ref[:, comp]).max() / np.abs(ref[:, comp]).max()
+        assert err < TOL[prec], (comp, err)
