@@ -12,15 +12,19 @@
 //   layer 1: D1[pixel][g] = sum_k Xim[pixel][k] W1[g][k], k = (c, ky, kx)
 //            (the patch's im2col, K = 9 C padded to 16 or 32), M = the
 //            (n+2)^2 pixels in tiles of 128, N = 32 channels;
-//   layer 2: D2[pixel][g] = sum_{ky,kx} sum_f A1[f][y+ky][x+kx] W2[g][f][ky][kx]
-//            as nine accumulating GEMMs with K = 32 channels, their A
-//            operands read from three copies of the layer-1 map shifted by
-//            kx = 0, 1, 2 columns (so that every 128-pixel tile is a
-//            uniformly strided operand), M = n^2 output pixels, N = 32.
+//   layer 2: D2[q][g] = sum_{ky,kx} sum_f A1[f][q + ky (n+2) + kx] W2[g][f][ky][kx]
+//            as nine accumulating GEMMs with K = 32 channels.  The layer-1
+//            map is stored once, pixel-major with its own row pitch n + 2,
+//            so for every shift (ky, kx) the A operand of a 128-row tile is
+//            the same uniformly strided block started (ky (n+2) + kx) rows
+//            later; output position q = y (n+2) + x is pixel (y, x) for
+//            x < n, and the two positions per row with x >= n (which read
+//            across a row end) are computed and ignored.  M = n (n+2)
+//            positions in tiles of 128, N = 32.
 // The epilogues read the accumulators back (tcgen05.ld): layer 1 adds the
-// level embedding, applies relu and BF16 rounding and writes the shifted
-// copies; layer 2 adds b2 and reduces the global max-pool (value and first
-// row-major position per channel).  The backward pass recomputes layer 1 the
+// level embedding, applies relu and BF16 rounding and writes the map; layer
+// 2 adds b2 and reduces the global max-pool (value and first row-major
+// position per channel, by a butterfly exchange inside each warp).  The backward pass recomputes layer 1 the
 // same way, uses that the max-pool passes gradient to one pixel per channel
 // (a small fraction of the forward work), and accumulates per-CTA partial
 // gradients that a second kernel sums in a fixed order (deterministic).
@@ -103,24 +107,22 @@ __host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
 template <int C, int N, bool BWD = false>
 struct TcGeo {
     static constexpr int S = N + 4, S1 = N + 2;
-    static constexpr int P1 = S1 * S1;                // layer-1 pixels
+    static constexpr int P1 = S1 * S1;                // layer-1 pixels (= rows of the layer-1 map)
     static constexpr int MT1 = (P1 + 127) / 128;      // layer-1 M tiles of 128 pixels
     static constexpr int K1 = C * 9 <= 16 ? 16 : 32;  // layer-1 K: 9 C padded to the MMA's K step
     static constexpr int KC1 = K1 / 8;                // 8-wide column blocks of Xim / W1t
-    static constexpr int RT = 128 / N;                // output rows per layer-2 M tile
-    static constexpr int MT2 = (N * N + 127) / 128;   // layer-2 M tiles
-    static constexpr int R2 = MT2 * RT + 2;           // rows of each shifted copy of A1 (>= S1)
+    static constexpr int Q2 = N * S1;                 // layer-2 output positions y (n+2) + x, y < n
+    static constexpr int MT2 = (Q2 + 127) / 128;      // layer-2 M tiles
+    static constexpr int R1 = MT2 * 128 + 2 * S1 + 2;  // rows of the map a layer-2 tile may read (>= P1)
     static constexpr int xim_chunk = MT1 * 128 * 16;  // Xim column block: MT1*128 rows of 16 bytes
-    static constexpr int a1_chunk = R2 * N * 16;      // one 8-channel block of one shifted copy
-    static constexpr int a1_copy = 4 * a1_chunk;      // one shifted copy (32 channels)
+    static constexpr int a1_chunk = R1 * 16;          // one 8-channel block of the layer-1 map
     static constexpr int xs = 0;                                   // input patch, BF16 [C][S][S]
     static constexpr int w1t = align128(C * S * S * 2);            // layer-1 B: [KC1][32 g][8 k] BF16
     static constexpr int w2t = w1t + KC1 * 32 * 16;                // layer-2 B: [9][4][32 g][8 f] BF16
-    static constexpr int reg = w2t + (BWD ? 0 : 9 * 4 * 32 * 16);   // Xim, then (aliased) A1s
-    static constexpr int reg_bytes = BWD ? KC1 * xim_chunk : imax(KC1 * xim_chunk, 3 * a1_copy);
+    static constexpr int reg = w2t + (BWD ? 0 : 9 * 4 * 32 * 16);   // Xim, then (aliased) the map A1m
+    static constexpr int reg_bytes = BWD ? KC1 * xim_chunk : imax(KC1 * xim_chunk, 4 * a1_chunk);
     static constexpr int end = reg + reg_bytes;
-    static_assert(S1 <= R2, "shifted copies hold every layer-1 row");
-    static_assert(128 % N == 0, "output rows tile the 128-pixel M tile");
+    static_assert(R1 >= P1, "the map holds every layer-1 pixel");
 };
 constexpr int kTmemCols = 128;  // >= 32 x max(MT1, MT2) columns of FP32 accumulators
 
@@ -162,7 +164,7 @@ __device__ __forceinline__ void tc_issue_layer1(unsigned char *smem, uint32_t tm
 }
 
 // Issue (one thread) layer 2's MMAs (nine shifts x two K steps per M tile)
-// for the shifted copies in the A1s region and commit them to *bar.
+// on the layer-1 map in the A1m region and commit them to *bar.
 template <int C, int N>
 __device__ __forceinline__ void tc_issue_layer2(unsigned char *smem, uint32_t tmem, uint64_t *bar) {
     using G = TcGeo<C, N>;
@@ -176,7 +178,7 @@ __device__ __forceinline__ void tc_issue_layer2(unsigned char *smem, uint32_t tm
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks)
                 tc::mma_bf16(tmem + 32 * mt,
-                             tc::smem_desc(a0 + kx * G::a1_copy + 2 * ks * G::a1_chunk + (mt * G::RT + ky) * N * 16,
+                             tc::smem_desc(a0 + 2 * ks * G::a1_chunk + (mt * 128 + ky * G::S1 + kx) * 16,
                                            G::a1_chunk, 128),
                              tc::smem_desc(b0 + sft * 4 * 32 * 16 + 2 * ks * 32 * 16, 32 * 16, 128), id,
                              sft > 0 || ks > 0);
@@ -217,16 +219,24 @@ __device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const floa
     uint16_t *xs = reinterpret_cast<uint16_t *>(smem + G::xs);
     for (int e = threadIdx.x; e < C * S * S; e += NT) xs[e] = xb[e];
     __syncthreads();
-    // im2col: Xim[kc][m][kk] = X[c][y + ky][x + kx], k = 8 kc + kk = 9 c + 3 ky + kx, m = y S1 + x
-    uint16_t *xim = reinterpret_cast<uint16_t *>(smem + G::reg);
-    for (int e = threadIdx.x; e < G::KC1 * G::MT1 * 128 * 8; e += NT) {
-        const int kk = e & 7, r = e >> 3, m = r % (G::MT1 * 128), kc = r / (G::MT1 * 128), k = kc * 8 + kk;
-        uint16_t v = 0;
-        if (m < G::P1 && k < C * 9) {
-            const int c = k / 9, q = k - 9 * c, ky = q / 3, kx = q - 3 * ky, y = m / S1, x = m - y * S1;
-            v = xs[(c * S + y + ky) * S + x + kx];
+    // im2col, one 16-byte row per item: Xim[kc][m][kk] = X[c][y + ky][x + kx]
+    // with k = 8 kc + kk = 9 c + 3 ky + kx (zero for k >= 9 C or m >= P1),
+    // m = y S1 + x
+    for (int e = threadIdx.x; e < G::KC1 * G::MT1 * 128; e += NT) {
+        const int m = e % (G::MT1 * 128), kc = e / (G::MT1 * 128);
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (m < G::P1) {
+            const int y = m / S1, x = m - y * S1;
+            const uint16_t *src = xs + y * S + x;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const int k = kc * 8 + kk;
+                const int c = k / 9, q = k - 9 * c, ky = q / 3, kx = q - 3 * ky;
+                const uint32_t v = k < C * 9 ? (uint32_t)src[(c * S + ky) * S + kx] : 0u;
+                w[kk >> 1] |= v << (16 * (kk & 1));
+            }
         }
-        xim[e] = v;
+        *reinterpret_cast<uint4 *>(smem + G::reg + (kc * G::MT1 * 128 + m) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -244,11 +254,11 @@ __device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const floa
         tc::tmem_ld32(tmem + lanes + 32 * mt, z);
         const int m = mt * 128 + 32 * (warp & 3) + lane;
         if (m < G::P1) {
-            const int y = m / S1, x = m - y * S1;
             if constexpr (F32OUT) {
 #pragma unroll
                 for (int g = 0; g < kF; ++g) a1[g * G::P1 + m] = rbf(fmaxf(z[g] + emb[g], 0.f));
             } else {
+                // the map A1m[kc][m][8 channels], row m = the layer-1 pixel
 #pragma unroll
                 for (int kc = 0; kc < 4; ++kc) {
                     uint32_t w[4];
@@ -258,14 +268,8 @@ __device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const floa
                         w[h] = (uint32_t)bf16_bits(fmaxf(z[g] + emb[g], 0.f)) |
                                ((uint32_t)bf16_bits(fmaxf(z[g + 1] + emb[g + 1], 0.f)) << 16);
                     }
-                    const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
-#pragma unroll
-                    for (int kx = 0; kx < 3; ++kx) {
-                        const int xp = x - kx;
-                        if (xp >= 0 && xp < N)
-                            *reinterpret_cast<uint4 *>(smem + G::reg + kx * G::a1_copy + kc * G::a1_chunk +
-                                                       (y * N + xp) * 16) = v;
-                    }
+                    *reinterpret_cast<uint4 *>(smem + G::reg + kc * G::a1_chunk + m * 16) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
                 }
             }
         }
@@ -330,37 +334,40 @@ __global__ void __launch_bounds__(128) cnn_forward_kernel(int nsample, const __n
         for (int mt = 0; mt < G::MT2; ++mt) {
             float z[32];
             tc::tmem_ld32(tmem + lanes + 32 * mt, z);
-            const int p = mt * 128 + 32 * warp + lane;
-            if (p < N * N) {
+            const int q = mt * 128 + 32 * warp + lane, y = q / G::S1, x = q - y * G::S1;
+            if (y < N && x < N) {
+                const int p = y * N + x;
 #pragma unroll
                 for (int g = 0; g < kF; ++g) {
                     const float v = z[g] + s_b2[g];
-                    if (v > best[g]) {
+                    if (v > best[g] || (v == best[g] && p < bi[g])) {
                         best[g] = v;
                         bi[g] = p;
                     }
                 }
             }
         }
+        // butterfly over the warp: after the exchange at distance o, a lane
+        // keeps the half of its channels selected by its bit o and merges
+        // them with its partner's; lane L ends with channel L
 #pragma unroll
-        for (int g = 0; g < kF; ++g) {
+        for (int o = 16, w = 16; o >= 1; o >>= 1, w >>= 1) {
+            const bool upper = (lane & o) != 0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best[g], o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi[g], o);
-                if (ob > best[g] || (ob == best[g] && oi < bi[g])) {
-                    best[g] = ob;
-                    bi[g] = oi;
-                }
+            for (int j = 0; j < w; ++j) {
+                const float sv = upper ? best[j] : best[j + w];
+                const int si = upper ? bi[j] : bi[j + w];
+                const float kv = upper ? best[j + w] : best[j];
+                const int ki = upper ? bi[j + w] : bi[j];
+                const float ov = __shfl_xor_sync(0xffffffffu, sv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, si, o);
+                const bool take = ov > kv || (ov == kv && oi < ki);
+                best[j] = take ? ov : kv;
+                bi[j] = take ? oi : ki;
             }
         }
-        if (lane == 0) {
-#pragma unroll
-            for (int g = 0; g < kF; ++g) {
-                s_best[warp][g] = best[g];
-                s_idx[warp][g] = bi[g];
-            }
-        }
+        s_best[warp][lane] = best[0];
+        s_idx[warp][lane] = bi[0];
         tc::fence_before_sync();
         __syncthreads();
         if (warp == 0) {
@@ -599,11 +606,14 @@ __global__ void combine_kernel(int n, const float *__restrict__ logit, const int
 }
 
 // Allows `bytes` of dynamic shared memory (the default limit of 48 KB covers
-// static and dynamic shared memory together).
+// static and dynamic shared memory together) and asks for the largest
+// shared-memory carveout, so that several CTAs fit on an SM.
 template <typename K>
 af_status smem_attr(K k, size_t bytes) {
     if (bytes > 227 * 1024) return AF_ERR_UNIMPLEMENTED;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess)
         return AF_ERR_CUDA;
     return AF_OK;
 }

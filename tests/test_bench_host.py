@@ -100,3 +100,20 @@ def test_pareto_front_and_rate_at_equal_l1():
     assert math.isclose(bench.rate_at(fr, 1e-3), 1.0)
     assert bench.rate_at(fr, 1e-2) == 4.0
     assert bench.rate_at([], 1e-3) is None
+
+
+def test_roofline_traffic_comes_from_the_committed_record(tmp_path):
+    """roofline.traffic is the ncu record of the committed summary when it
+    covers the timed tiling and the kernel's sources are unchanged (their
+    hash); otherwise it is None with the reason."""
+    t = {"tile": (32, 8), "threads": 128, "persistent": False}
+    h = bench.kernel_source_hash()
+    rec = tmp_path / "p.md"
+    rec.write_text(f"x\ntraffic: tiling=32x8x128 bytes_per_launch=1951111424 source_hash={h}\n")
+    assert bench.profiled_traffic(t, str(rec))[0] == 1951111424.0
+    rec.write_text("traffic: tiling=32x8x128 bytes_per_launch=1951111424 source_hash=0000000000000000\n")
+    v, why = bench.profiled_traffic(t, str(rec))
+    assert v is None and why.startswith("stale")
+    v, why = bench.profiled_traffic({"tile": (32, 16), "threads": 192, "persistent": False}, str(rec))
+    assert v is None
+    assert bench.profiled_traffic(t, str(tmp_path / "missing.md"))[0] is None
