@@ -147,6 +147,24 @@ __device__ __forceinline__ R recon_eval(R c00, R c10, R c01, R c11, R xl, R xr, 
            ly2 * (lx0 * c01 + lx1 * yt + lx2 * c11);
 }
 
+// Mean of the biquadratic reconstruction of a cell (nodal values as for
+// recon_eval) over one of its four quarters: qx, qy = 0 for the lower half
+// (xi or eta in [-1, 0]), 1 for the upper half.  The mean of each 1D
+// Lagrange basis function over a half interval replaces its point value:
+// over [-1, 0] the three functions average 5/12, 2/3, -1/12, over [0, 1]
+// -1/12, 2/3, 5/12.  This is exactly the Simpson rule over the quarter
+// (exact for quadratics), in 9 multiply-adds instead of 9 evaluations.
+template <typename R>
+__device__ __forceinline__ R recon_quarter_mean(R c00, R c10, R c01, R c11, R xl, R xr, R yb, R yt, R avg, int qx,
+                                                int qy) {
+    const R cen = R(2.25) * avg - R(0.0625) * (c00 + c10 + c01 + c11) - R(0.25) * (xl + xr + yb + yt);
+    const R lo = R(5) / R(12), mid = R(2) / R(3), hi = R(-1) / R(12);
+    const R lx0 = qx ? hi : lo, lx1 = mid, lx2 = qx ? lo : hi;
+    const R ly0 = qy ? hi : lo, ly1 = mid, ly2 = qy ? lo : hi;
+    return ly0 * (lx0 * c00 + lx1 * yb + lx2 * c10) + ly1 * (lx0 * xl + lx1 * cen + lx2 * xr) +
+           ly2 * (lx0 * c01 + lx1 * yt + lx2 * c11);
+}
+
 // Simpson's rule over a cell from the values f(a, b) at its 3 x 3 points
 // (a, b in {0, 1, 2}): exact for the biquadratic reconstruction.
 template <typename R, typename Fn>
@@ -158,9 +176,12 @@ __device__ __forceinline__ R simpson9(Fn f) {
     return s;
 }
 
-// Value of the reconstruction of leaf q, component c, at (x, y).
+// Value of the reconstruction of leaf q, component c, at (x, y); with
+// quarter >= 0 instead the mean of the reconstruction over the quarter of
+// the cell holding (x, y) that (x, y) lies in (the centre of a finer cell).
 template <typename T>
-__device__ T recon_at(const DevForest &F, const StateView<T> &S, int q, int c, long long x, long long y) {
+__device__ T recon_at(const DevForest &F, const StateView<T> &S, int q, int c, long long x, long long y,
+                      bool quarter = false) {
     const long long hw = hwid(F, __ldg(F.level + q));
     const long long dx = reld(F, x, leaf_x0(F, q)), dy = reld(F, y, leaf_y0(F, q));
     long long ci = dx >= 0 ? dx / hw : -1, cj = dy >= 0 ? dy / hw : -1;
@@ -168,6 +189,7 @@ __device__ T recon_at(const DevForest &F, const StateView<T> &S, int q, int c, l
     cj = cj < 0 ? 0 : (cj > F.n - 1 ? F.n - 1 : cj);
     const T xi = (T)(2.0 * (double)(dx - ci * hw) / (double)hw - 1.0);  // exact: a multiple of 1/2
     const T eta = (T)(2.0 * (double)(dy - cj * hw) / (double)hw - 1.0);
+    const int qx = 2 * (dx - ci * hw) >= hw, qy = 2 * (dy - cj * hw) >= hw;
     const int i = (int)ci, j = (int)cj;
     // Point values on the leaf's boundary lines are read from their owner:
     // a leaf whose neighbours are all same-level does not keep the copies in
@@ -190,6 +212,7 @@ __device__ T recon_at(const DevForest &F, const StateView<T> &S, int q, int c, l
     const T xl = node(kXmid, i, j), xr = node(kXmid, i + 1, j);
     const T yb = node(kYmid, i, j), yt = node(kYmid, i, j + 1);
     const T avg = *S.at(q, c, kAvg, i, j);
+    if (quarter) return recon_quarter_mean<T>(c00, c10, c01, c11, xl, xr, yb, yt, avg, qx, qy);
     return recon_eval<T>(c00, c10, c01, c11, xl, xr, yb, yt, avg, xi, eta);
 }
 
@@ -221,8 +244,9 @@ __device__ double transfer(const DevForest &F, const StateView<T> &S, int lp, in
         return *S.at(q, c, kCorner, i, j);
     }
     if (k != kAvg) return (double)recon_at<T>(F, S, q, c, x, y);
-    // Simpson's rule over the destination cell (half width h), exact for the
-    // coarse biquadratic
+    // the mean of the coarse biquadratic over the destination cell, a quarter
+    // of a coarse cell (the Simpson rule over it, exact for the biquadratic)
+    if (lq == lp - 1) return (double)recon_at<T>(F, S, q, c, x, y, true);
     const long long h = hwid(F, lp) / 2;
     return (double)simpson9<T>([&](int a, int b) { return recon_at<T>(F, S, q, c, x + (a - 1) * h, y + (b - 1) * h); });
 }
@@ -468,7 +492,9 @@ __global__ void plan_exec_b(StateView<T> S, int n, const GhostEntry *__restrict_
         const int W = S.W;
         // value at quarter-cell position (u, v) of the source leaf, with the
         // cell chosen as the direct exchange chooses it
-        auto at = [&](const T *b, int u, int v) -> T {
+        // quarter: the mean over the quarter of the cell holding (u, v) that
+        // (u, v), the centre of a cell one level finer, lies in
+        auto at = [&](const T *b, int u, int v, bool quarter) -> T {
             int ci = u / 4, cj = v / 4;
             ci = ci > n - 1 ? n - 1 : ci;
             cj = cj > n - 1 ? n - 1 : cj;
@@ -477,12 +503,14 @@ __global__ void plan_exec_b(StateView<T> S, int n, const GhostEntry *__restrict_
             const T *xm = b + kXmid * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
             const T *ym = b + kYmid * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
             const T *av = b + kAvg * S.plane + (int64_t)(cj + kGhost) * W + (ci + kGhost);
+            if (quarter)
+                return recon_quarter_mean<T>(cr[0], cr[1], cr[W], cr[W + 1], xm[0], xm[1], ym[0], ym[W], av[0],
+                                             u - 4 * ci >= 2, v - 4 * cj >= 2);
             return recon_eval<T>(cr[0], cr[1], cr[W], cr[W + 1], xm[0], xm[1], ym[0], ym[W], av[0], xi, eta);
         };
         for (int c = 0; c < S.ncomp; ++c) {
             const T *b = q + c * cs;
-            dst[c * cs] = g.kind == kGPoint ? at(b, u0, v0)
-                                            : simpson9<T>([&](int a, int bb) { return at(b, u0 + a - 1, v0 + bb - 1); });
+            dst[c * cs] = at(b, u0, v0, g.kind != kGPoint);
         }
     }
 }

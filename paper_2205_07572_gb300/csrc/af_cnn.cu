@@ -219,24 +219,29 @@ __device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const floa
     uint16_t *xs = reinterpret_cast<uint16_t *>(smem + G::xs);
     for (int e = threadIdx.x; e < C * S * S; e += NT) xs[e] = xb[e];
     __syncthreads();
-    // im2col, one 16-byte row per item: Xim[kc][m][kk] = X[c][y + ky][x + kx]
-    // with k = 8 kc + kk = 9 c + 3 ky + kx (zero for k >= 9 C or m >= P1),
-    // m = y S1 + x
-    for (int e = threadIdx.x; e < G::KC1 * G::MT1 * 128; e += NT) {
-        const int m = e % (G::MT1 * 128), kc = e / (G::MT1 * 128);
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
-        if (m < G::P1) {
-            const int y = m / S1, x = m - y * S1;
-            const uint16_t *src = xs + y * S + x;
+    // im2col, one pixel (all KC1 16-byte rows of it) per item:
+    // Xim[kc][m][kk] = X[c][y + ky][x + kx] with k = 8 kc + kk = 9 c + 3 ky + kx
+    // (zero for k >= 9 C or m >= P1), m = y S1 + x; the offsets of the nine
+    // taps are compile-time constants
+    for (int m = threadIdx.x; m < G::MT1 * 128; m += NT) {
+        const bool in = m < G::P1;
+        const int y = m / S1, x = m - y * S1;
+        const uint16_t *src = xs + (in ? y * S + x : 0);
+#pragma unroll
+        for (int kc = 0; kc < G::KC1; ++kc) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
                 const int k = kc * 8 + kk;
-                const int c = k / 9, q = k - 9 * c, ky = q / 3, kx = q - 3 * ky;
-                const uint32_t v = k < C * 9 ? (uint32_t)src[(c * S + ky) * S + kx] : 0u;
-                w[kk >> 1] |= v << (16 * (kk & 1));
+                if (k < C * 9) {
+                    const int c = k / 9, q = k - 9 * c, ky = q / 3, kx = q - 3 * ky;
+                    const uint32_t v = in ? (uint32_t)src[(c * S + ky) * S + kx] : 0u;
+                    w[kk >> 1] |= v << (16 * (kk & 1));
+                }
             }
+            *reinterpret_cast<uint4 *>(smem + G::reg + (kc * G::MT1 * 128 + m) * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
         }
-        *reinterpret_cast<uint4 *>(smem + G::reg + (kc * G::MT1 * 128 + m) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -626,14 +631,14 @@ af_status forward_launch(int nsample, const void *X, const int32_t *lev, const f
     auto k = cnn_forward_kernel<C, N>;
     const size_t bytes = TcGeo<C, N>::end;
     if (const af_status e = smem_attr(k, bytes)) return e;
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, bytes) != cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return AF_ERR_CUDA;
-    // tensor memory: at most 512 columns per SM
-    per_sm = per_sm < 1 ? 1 : (per_sm > 512 / kTmemCols ? 512 / kTmemCols : per_sm);
-    const int slots = sms * per_sm;
+    // persistent CTAs: as many per SM as tensor memory holds (512 columns);
+    // shared memory and registers allow that many, and CTAs that do not fit
+    // yet simply start later
+    const int slots = sms * (512 / kTmemCols);
     const int grid = nsample < slots ? nsample : slots;
     k<<<grid, 128, bytes, s>>>(nsample, static_cast<const __nv_bfloat16 *>(X), lev, P, lg, M, A);
     return launched();
