@@ -522,12 +522,17 @@ __host__ __device__ constexpr int min_ctas() {
 
 // Shared-memory geometry of a TMX x TMY tile.  The window is TMX + 3 node
 // columns wide; its pitch is two more, the lattice width of TMX-cell patches,
-// so that their full-width tiles can be staged in bulk; each plane has room
-// for the window origin's offset and the bulk copies' rounding to 16 bytes
-// (12 elements), and a size that keeps every plane 16-byte aligned.
-template <int TMX, int TMY>
+// so that their full-width tiles can be staged in bulk -- except for a tile
+// two cells wider than patches of a compile-time size NN (the whole patch
+// with its first ghost layer), whose pitch is the lattice width of NN-cell
+// patches: its window is then the whole patch lattice, staged in bulk too.
+// Each plane has room for the window origin's offset and the bulk copies'
+// rounding to 16 bytes (12 elements), and a size that keeps every plane
+// 16-byte aligned.
+template <int TMX, int TMY, int NN = 0>
 struct Geo {
-    static constexpr int WX = TMX + 2 * kGhost + 1, WY = TMY + 3, WSZ = (WX * WY + 12 + 3) / 4 * 4;  // window
+    static constexpr int WX = (NN > 0 && TMX == NN + 2) ? NN + 2 * kGhost + 1 : TMX + 2 * kGhost + 1;
+    static constexpr int WY = TMY + 3, WSZ = (WX * WY + 12 + 3) / 4 * 4;  // window
     static constexpr int TX = TMX + 1, TY = TMY + 1, TSZ = TX * TY;  // T arrays
 };
 
@@ -710,6 +715,75 @@ __device__ __forceinline__ bool stage_bulk(const StepArgs<T> &A, const af_work &
     return true;
 }
 
+// True if work item wk is a whole patch with its first ghost layer ([-1,
+// n+1)^2) and the window (pitch WX, WY rows) is exactly the patch lattice:
+// the window is then one contiguous span of each plane from lattice offset 0.
+template <typename T, int WX, int WY>
+__device__ __forceinline__ bool ext_bulk_tile(const StepArgs<T> &A, const af_work &wk) {
+    return A.n + 2 * kGhost + 1 == WX && WY == WX && wk.x0 == -1 && wk.x1 == A.n + 1 && wk.y0 == -1 &&
+           wk.y1 == A.n + 1;
+}
+
+// Stage work item wk (ext_bulk_tile true) into the window at Sx (16-byte
+// aligned): one bulk copy of each whole plane lattice, then the entries
+// outside the patch interior in a direction with a same-level neighbour
+// overwritten with that neighbour's values (read with plain loads before the
+// wait, stored after it).  Returns false (in every thread) if the wait gave
+// up; g_wait_timeouts is then incremented.  Ends with a CTA barrier.
+template <typename T, int NT, int WX, int WSZ, int NC>
+__device__ __forceinline__ bool stage_bulk_ext(const StepArgs<T> &A, const af_work &wk, T *Sx, uint64_t *bar) {
+    constexpr int n = WX - 2 * kGhost - 1;
+    constexpr int E = 16 / (int)sizeof(T);
+    constexpr int ncp = NC * kPlanes;
+    constexpr int64_t plane = plane_stride(n), pw = ncp * plane;
+    constexpr unsigned bytes = (unsigned)((WX * WX + E - 1) / E * E * (int)sizeof(T));
+    static_assert((WX * WX + E - 1) / E * E <= plane, "the copy stays inside the plane");
+    static_assert(E + (WX * WX + E - 1) / E * E <= WSZ, "the copy stays inside the window slot");
+    const T *const in = src_buf(A, wk.level);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !(wk.flags & AF_WORK_SKIP_BULK_COPY)) {
+        mbar_expect_tx(bar, bytes * ncp);
+        const T *src = in + (int64_t)wk.patch * pw;
+#pragma unroll
+        for (int cp = 0; cp < ncp; ++cp) bulk_copy_g2s(Sx + cp * WSZ, src + cp * plane, bytes, bar);
+    }
+    int nb[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) nb[d] = wk.nbr[d];
+    bool waited = false, ok = true;
+    for (int t = threadIdx.x; t < WX * WX; t += NT) {
+        const int lj = t / WX - kGhost, li = t - (lj + kGhost) * WX - kGhost;
+        const int sx = li < 0 ? -1 : (li >= n ? 1 : 0);
+        const int sy = lj < 0 ? -1 : (lj >= n ? 1 : 0);
+        if (!(sx | sy)) continue;
+        const int d = dir_index(sx, sy);
+        int q = nb[0];
+#pragma unroll
+        for (int e = 1; e < 8; ++e) q = (d == e) ? nb[e] : q;
+        if (q < 0) continue;
+        const T *g = in + (int64_t)q * pw + ((lj - sy * n + kGhost) * WX + (li - sx * n + kGhost));
+        T v[ncp];
+#pragma unroll
+        for (int cp = 0; cp < ncp; ++cp) v[cp] = __ldg(g + cp * plane);
+        if (!waited) {  // the bulk copy must land before its entries are overwritten
+            ok = mbar_wait(bar, 0);
+            waited = true;
+        }
+#pragma unroll
+        for (int cp = 0; cp < ncp; ++cp) Sx[cp * WSZ + t] = v[cp];
+    }
+    if (!waited) ok = mbar_wait(bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicAdd(&g_wait_timeouts, 1u);
+            mbar_wait(bar, 0);  // bounded: give the copies in flight a second chance to land
+        }
+        return false;
+    }
+    return true;
+}
+
 // Issue (every thread, without waiting) the halo copies of a bulk-staged
 // tile whose bulk copies have landed.
 template <typename T, int NT, int WX, int WSZ, int NC>
@@ -766,18 +840,28 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 template <typename T, int EQ, int NT, int TMX, int TMY, int NN = 0>
 __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel(const __grid_constant__ StepArgs<T> A,
                                                   const __grid_constant__ typename WeightsOf<T, EQ>::type W) {
-    using Gm = Geo<TMX, TMY>;
+    using Gm = Geo<TMX, TMY, NN>;
     constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *const Sbase = reinterpret_cast<T *>(smem_raw);
-    T *const Sin = Sbase + win_off<T, Gm::WX>();
+    T *Sin = Sbase + win_off<T, Gm::WX>();
     T *ST = Sbase + ncomp * kPlanes * Gm::WSZ;
     const af_work wk = A.work[blockIdx.x];  // by value: read once
     if (wk.x1 - wk.x0 > TMX || wk.y1 - wk.y0 > TMY) return;  // built for another tiling
+    __shared__ __align__(8) uint64_t bar;
+    bool staged = false;
     if (bulk_tile<T, Gm::WX>(A, wk)) {
-        __shared__ __align__(8) uint64_t bar;
         if (!stage_bulk<T, NT, Gm::WX, Gm::WSZ, ncomp>(A, wk, Sin, &bar)) return;  // counted in g_wait_timeouts
-    } else {
+        staged = true;
+    }
+    if constexpr (NN > 0 && TMX == NN + 2 && TMY == NN + 2) {
+        if (!staged && ext_bulk_tile<T, Gm::WX, Gm::WY>(A, wk)) {
+            Sin = Sbase + 16 / (int)sizeof(T);  // the window origin is lattice offset 0: 16-byte aligned
+            if (!stage_bulk_ext<T, NT, Gm::WX, Gm::WSZ, ncomp>(A, wk, Sin, &bar)) return;
+            staged = true;
+        }
+    }
+    if (!staged) {
         stage_issue<T, NT, Gm::WX, Gm::WSZ, ncomp, NN>(A, wk, Sin);
         cp_async_commit();
         cp_async_wait_all();
@@ -811,7 +895,7 @@ template <typename T, int EQ, int NT, int TMX, int TMY, int NN = 0>
 __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel_pipe(const __grid_constant__ StepArgs<T> A,
                                                        const __grid_constant__ typename WeightsOf<T, EQ>::type W,
                                                        int nwork) {
-    using Gm = Geo<TMX, TMY>;
+    using Gm = Geo<TMX, TMY, NN>;
     constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
     constexpr int wbuf = ncomp * kPlanes * Gm::WSZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -910,7 +994,7 @@ inline cudaError_t ensure_smem(Kern k, size_t bytes) {
 template <typename T, int EQ, int NT, int TMX, int TMY, int PIPE, int NN>
 af_status launch_tiling(const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W, int nwork,
                         cudaStream_t stream) {
-    using Gm = dev::Geo<TMX, TMY>;
+    using Gm = dev::Geo<TMX, TMY, NN>;
     constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
     const size_t win = sizeof(T) * (size_t)ncomp * kPlanes * Gm::WSZ;
     const size_t tarr = sizeof(T) * (size_t)ncomp * 3 * Gm::TSZ;
