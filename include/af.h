@@ -417,8 +417,11 @@ af_status af_fill_ghosts_planned(const af_config *cfg, const af_forest *forest, 
                                  void *stream);
 
 /* Regrid transfer (Section 3.1 cases 1 and 2): every leaf of new_forest that
- * is a leaf of old_forest is copied whole from d_old; every other new leaf
- * gets, from the owners in old_forest (coarse -> fine interpolation, fine ->
+ * is a leaf of old_forest is copied whole from d_old, except the point values
+ * on its right and top faces, which are taken from their owners in old_forest
+ * (a leaf whose neighbours are all same-level does not keep those copies
+ * current, and it owns them once the neighbour across has coarsened); every
+ * other new leaf gets, from the owners in old_forest (coarse -> fine interpolation, fine ->
  * coarse averaging over one level, the coinciding vertex of a finer owner),
  * its cell averages and the point values on its cells' boundaries -- node
  * lines 0 .. n, the right and top lines included, which the leaf owns where

@@ -526,16 +526,34 @@ __global__ void transfer_kernel(DevForest Fo, StateView<T> So, DevForest Fn, Sta
         const long long side = (long long)Fo.B << l;
         same = __ldg(Fo.map + map_offset(Fo.B, l) + (long long)py * side + px);
     }
+    const int n = Fn.n, m = n + 1;
+    const long long hwn = 2LL << (Fn.lmax - l);
+    const long long x0 = (long long)px * n * hwn, y0 = (long long)py * n * hwn;
     if (same >= 0) {
         const T *srcp = So.patch(same);
         for (int64_t e = threadIdx.x; e < words; e += blockDim.x) dst[e] = srcp[e];
+        __syncthreads();
+        // The point values on the right (i = n) and top (j = n) faces: where the
+        // neighbour across was the owner in the old forest (same level, or
+        // finer) the leaf's own copy is not kept current -- a step of a leaf
+        // with eight same-level neighbours stores node lines 0 .. n-1 only --
+        // yet the leaf owns them in the new forest if that neighbour became
+        // coarser.  Take them from their old owner.
+        for (int e = threadIdx.x; e < 4 * m; e += blockDim.x) {
+            const int side = e / m, r = e - side * m;  // 0, 1: corner / left-mid on line i = n; 2, 3: on j = n
+            const int k = side == 0 || side == 2 ? kCorner : (side == 1 ? kXmid : kYmid);
+            const int i = side < 2 ? n : r, j = side < 2 ? r : n;
+            if ((k == kXmid && j == n) || (k == kYmid && i == n)) continue;
+            const long long x = x0 + (long long)i * hwn + (k == kYmid ? hwn / 2 : 0);
+            const long long y = y0 + (long long)j * hwn + (k == kXmid ? hwn / 2 : 0);
+            const int q = entry_owner(Fo, k, x, y);
+            if (q < 0 || q == same) continue;
+            for (int c = 0; c < Sn.ncomp; ++c) *Sn.at(p, c, k, i, j) = (T)transfer<T>(Fo, So, l, q, c, k, x, y);
+        }
         return;
     }
     for (int64_t e = threadIdx.x; e < words; e += blockDim.x) dst[e] = T(0);
     __syncthreads();
-    const int n = Fn.n, m = n + 1;
-    const long long hwn = 2LL << (Fn.lmax - l);
-    const long long x0 = (long long)px * n * hwn, y0 = (long long)py * n * hwn;
     // The cells' averages and the point values on their boundaries: node
     // lines 0 .. n, the right (i = n) and top (j = n) lines included -- a leaf
     // finer than its neighbour across that face owns those nodes (the finer

@@ -515,11 +515,14 @@ def _input_as_kernel_reads(lat, nbr, p, n):
     return out
 
 
+@pytest.mark.parametrize("tile", [(16, 16, 128), (18, 18, 256)])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_bench_acoustics_forest_sampled_leaves_match_oracle(af, prec):
+def test_bench_acoustics_forest_sampled_leaves_match_oracle(af, prec, tile):
     """The benchmark's acoustics forest at full size (levels 3-7, 4944
     leaves of 16 x 16 cells), in the launch configuration it times (batched
-    work list, 16 x 16-cell tiles, after graph-replayed coarse steps): the
+    work list, 16 x 16-cell tiles, after graph-replayed coarse steps) and in
+    the default tiling of 16 x 16 patches (18 x 18 tiles: whole-patch bulk
+    staging for leaves that advance their ghost layer): the
     first substep of a coarse step advances every level in one launch;
     sampled leaves of every level -- with and without coarser or finer
     neighbours -- equal the oracle's single-patch step on the input the
@@ -534,7 +537,7 @@ def test_bench_acoustics_forest_sampled_leaves_match_oracle(af, prec):
     n, nc = bench.AMR_N, 3
     dx0 = (c["hi"][0] - c["lo"][0]) / (c["B"] * n)
     dt0 = bench.CFL * dx0
-    k = [t[:3] for t in af.step_tilings()].index((16, 16, 128))
+    k = [t[:3] for t in af.step_tilings()].index(tile)
     run = AMRRun(af.config(1, prec, n, c=1.0), c["B"], c["lmax"], leaves, st, c["lo"], c["hi"], dt0,
                  graphs=True, tiling=k)
     assert run.forest.nleaf > 4000
@@ -570,3 +573,41 @@ def test_bench_acoustics_forest_sampled_leaves_match_oracle(af, prec):
     for comp in range(nc):
         err = np.abs(got[:, comp] - ref[:, comp]).max() / np.abs(ref[:, comp]).max()
         assert err < TOL[prec], (comp, err)
+
+
+@pytest.mark.parametrize("tile", [(16, 16, 128), (18, 18, 256)])
+def test_regrid_where_a_neighbour_family_coarsens_matches_oracle(af, tile):
+    """A leaf with eight same-level neighbours advances only its interior,
+    so the copies it keeps of the point values on its right and top faces
+    (owned then by its neighbours) are not current.  When the family to its
+    right (or above) coarsens, the leaf becomes the owner of those values
+    (Section 3.2: the finer grid's values on a coarse-fine face): the regrid
+    must take them from their previous owners.  Two coarse steps, a regrid
+    that coarsens the families right of and above an unchanged leaf, one
+    more coarse step: equal to the oracle (FP64 1e-12)."""
+    from paper_2205_07572_gb300.amr import AMRRun
+    n, lmax = 16, 3
+    block = {(x, y) for x in (1, 2, 3) for y in (1, 2, 3)}
+    leaves = _sorted(S.balanced_forest(1, 2, lmax, lambda l, x, y: l == 2 and (x, y) in block))
+    st = S.forest_state(n, 3, 1, lmax, leaves, S.pulse_plus_vortex(), nq=3)
+    dx0 = 1.0 / n
+    dt0 = 0.4 * dx0
+    Fo = OracleForest(1, n, 1, lmax, leaves, (0, 0), (1, 1), dt0, 1.0, 0.5, 1.0, state=st)
+    Fo.sync_fill((1 << (lmax + 1)) - 1)
+    k = [t[:3] for t in af.step_tilings()].index(tile)
+    run = AMRRun(af.config(1, 0, n, c=1.0), 1, lmax, leaves, st, (0, 0), (1, 1), dt0, tiling=k)
+    assert (run.forest.nbr[run.forest.leaves.index((3, 5, 5))] >= 0).all()   # eight same-level neighbours
+    for _ in range(2):
+        Fo.coarse_step()
+        run.coarse_step()
+    # coarsen the families (level-2 parents) right of and above leaf (3, 5, 5)
+    gone = {(3, 2), (2, 3)}
+    tags = np.array([-1 if (l == 3 and (x // 2, y // 2) in gone) else 0 for (l, x, y) in Fo.leaves], np.int8)
+    order = {leaf: i for i, leaf in enumerate(Fo.leaves)}
+    Fo.regrid(tags, 2)
+    run.regrid(tags[[order[lf] for lf in run.forest.leaves]], 2)
+    assert Fo.leaves == run.forest.leaves and (2, 3, 2) in Fo.leaves and (3, 5, 5) in Fo.leaves
+    Fo.coarse_step()
+    run.coarse_step()
+    torch.cuda.synchronize()
+    _compare(Fo, run, n, 3, TOL[0])
