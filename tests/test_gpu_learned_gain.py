@@ -3,8 +3,10 @@ forest (2 x 2 brick, levels 2-5): trained on runs of the method from two
 ring waves, on a third ring it predicts the plain criterion's tags over the
 next regrid interval; regridding every 4 coarse steps with it keeps the
 solution closer to a uniform finest-level run than the plain criterion does
-with the same regrids; and the equal-L1 comparison of the two Pareto fronts
-(L1 distance against cell updates per second) is well formed."""
+with the same regrids; it reaches the L1 error of the plain criterion
+regridding every coarse step (the paper's practice) at a higher rate of cell
+updates; and the equal-L1 comparison of the two Pareto fronts (L1 distance
+against cell updates per second) is well formed."""
 import math
 
 import pytest
@@ -53,3 +55,11 @@ def test_equal_l1_comparison_is_consistent(lt):
         assert m["learned"] > 0 and m["plain"] > 0
         assert math.isclose(m["learned_over_plain"], m["learned"] / m["plain"])
         assert math.isclose(m["learned"], bench.rate_at(lt["pareto"]["learned_f32"], m["l1"]))
+
+
+def test_learned_tagging_reaches_plain_l1_at_higher_throughput(lt):
+    """At the L1 error of the plain criterion regridding every coarse step,
+    the learned tags (regridding every 4 steps) deliver more cell updates
+    per second, regrids and tagging included."""
+    m = lt["equal_l1_at_plain_every_step"]
+    assert m["learned"] is not None and m["learned"] > m["plain"], m
