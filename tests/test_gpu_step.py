@@ -621,3 +621,39 @@ def test_bench_workload_full_size_sampled_patches_match_oracle(af, bench_workloa
             err = np.abs(g[c] - ref[c]).max() / scale[c]
             assert err < TOL[prec], (p, c, err)
     assert af.step_wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("neighbours", [False, True])
+def test_whole_patch_bulk_staging_equals_elementwise_staging(af, neighbours):
+    """FP32 16 x 16 patches that advance their first ghost layer: the 18 x 18
+    tiling stages the whole patch lattice by one bulk copy per plane (window
+    pitch = lattice width), the 18 x 10 tiling element by element; both give
+    the same step bit for bit, with the patches' own ghost rings, and with
+    same-level neighbours in some directions (their entries read from the
+    neighbours)."""
+    n, P, nc = 16, 6, 3
+    lay = S.Layout(n, nc)
+    st = S.random_state(lay, P, seed=321).astype(np.float32).reshape(P, -1)
+    cfg = af.config(af.ACOUSTICS, af.F32, n, c=1.0)
+    nbr = None
+    if neighbours:   # a ring of six patches: W/E neighbours same-level, the rest not
+        nbr = np.full((P, 8), -1, np.int32)
+        for p in range(P):
+            nbr[p, 0], nbr[p, 1] = (p - 1) % P, (p + 1) % P
+        nbr[2, 1] = -1                      # patch 2 misses its E neighbour: extended anyway
+    tl = [t[:3] for t in af.step_tilings()]
+    dt = 0.4 / n
+    outs = []
+    af.step_wait_timeouts(reset=True)
+    for k in (tl.index((18, 18, 256)), tl.index((18, 10, 192))):
+        work = af.build_step_work(cfg, np.arange(P), nbr=nbr, tiling=k)
+        w = np.frombuffer(work.tobytes(), dtype=np.int16).reshape(-1, 32)
+        assert (w[:, 20] == -1).all() and (w[:, 21] == n + 1).all()    # every item covers [-1, n+1) in x
+        din = torch.from_numpy(st).cuda()
+        dout = din.clone()
+        af.patch_step(cfg, torch.from_numpy(work).cuda(), len(work) // 64, din, dout, dt, 1.0 / n, 1.0 / n,
+                      tiling=k)
+        torch.cuda.synchronize()
+        outs.append(dout.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert af.step_wait_timeouts() == 0
