@@ -155,7 +155,8 @@ af_status af_build_step_work_at(const af_config *cfg, int32_t tiling, int32_t np
  *   2. fluxes by the 3 x 3 space-time Simpson rule (Eq. Simpson-2d);
  *   3. the conservative update of the cell averages (Eq. 2dfv).
  *
- * d_work     device copy of the af_build_step_work output (nwork entries)
+ * d_work     device copy of the af_build_step_work output (nwork entries),
+ *            16-byte aligned (AF_ERR_LAYOUT otherwise)
  * d_in       state at t^n (npatch_total patches, layout above)
  * d_out      receives the new averages and point values of every advanced
  *            cell.  A patch that advances its first ghost layer (one with a

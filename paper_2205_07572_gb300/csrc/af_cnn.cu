@@ -116,13 +116,15 @@ struct TcGeo {
     static constexpr int R1 = MT2 * 128 + 2 * S1 + 2;  // rows of the map a layer-2 tile may read (>= P1)
     static constexpr int xim_chunk = MT1 * 128 * 16;  // Xim column block: MT1*128 rows of 16 bytes
     static constexpr int a1_chunk = R1 * 16;          // one 8-channel block of the layer-1 map
-    static constexpr int xs = 0;                                   // input patch, BF16 [C][S][S]
-    static constexpr int w1t = align128(C * S * S * 2);            // layer-1 B: [KC1][32 g][8 k] BF16
+    static constexpr int xbytes = C * S * S * 2;                   // one input patch, BF16 [C][S][S]
+    static constexpr int xs = 0;                                   // input patch (forward: two buffers)
+    static constexpr int w1t = align128((BWD ? 1 : 2) * xbytes);   // layer-1 B: [KC1][32 g][8 k] BF16
     static constexpr int w2t = w1t + KC1 * 32 * 16;                // layer-2 B: [9][4][32 g][8 f] BF16
     static constexpr int reg = w2t + (BWD ? 0 : 9 * 4 * 32 * 16);   // Xim, then (aliased) the map A1m
     static constexpr int reg_bytes = BWD ? KC1 * xim_chunk : imax(KC1 * xim_chunk, 4 * a1_chunk);
     static constexpr int end = reg + reg_bytes;
     static_assert(R1 >= P1, "the map holds every layer-1 pixel");
+    static_assert(xbytes % 16 == 0, "a patch is a whole number of 16-byte bulk-copy units");
 };
 constexpr int kTmemCols = 128;  // >= 32 x max(MT1, MT2) columns of FP32 accumulators
 
@@ -206,19 +208,24 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity) {
 }
 
 // Layer 1 of sample b on the tensor cores: input patch, im2col, MMAs, and
-// the epilogue A1 = bf16(relu(D1 + emb[level])) written either as the three
-// shifted BF16 copies layer 2 reads (F32OUT false) or as an FP32 map
-// a1[f][y][x] (F32OUT true, the backward pass).  Ends with a barrier; false
-// if the wait gave up.
+// the epilogue A1 = bf16(relu(D1 + emb[level])) written either as the BF16
+// map layer 2 reads (F32OUT false) or as an FP32 map a1[f][y][x] (F32OUT
+// true, the backward pass).  xin: the patch already in shared memory, or
+// null (it is then read from X[b]).  Ends with a barrier; false if the wait
+// gave up.
 template <int C, int N, int NT, bool F32OUT>
-__device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const float *emb, unsigned char *smem,
-                          uint32_t tmem, uint64_t *bar, unsigned &phase, float *a1) {
+__device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const uint16_t *xin, const float *emb,
+                          unsigned char *smem, uint32_t tmem, uint64_t *bar, unsigned &phase, float *a1) {
     using G = TcGeo<C, N, F32OUT>;
     constexpr int S = G::S, S1 = G::S1;
-    const uint16_t *xb = reinterpret_cast<const uint16_t *>(X) + (int64_t)b * C * S * S;
-    uint16_t *xs = reinterpret_cast<uint16_t *>(smem + G::xs);
-    for (int e = threadIdx.x; e < C * S * S; e += NT) xs[e] = xb[e];
-    __syncthreads();
+    const uint16_t *xs = xin;
+    if (xs == nullptr) {
+        const uint16_t *xb = reinterpret_cast<const uint16_t *>(X) + (int64_t)b * C * S * S;
+        uint16_t *xw = reinterpret_cast<uint16_t *>(smem + G::xs);
+        for (int e = threadIdx.x; e < C * S * S; e += NT) xw[e] = xb[e];
+        __syncthreads();
+        xs = xw;
+    }
     // im2col, one pixel (all KC1 16-byte rows of it) per item:
     // Xim[kc][m][kk] = X[c][y + ky][x + kx] with k = 8 kc + kk = 9 c + 3 ky + kx
     // (zero for k >= 9 C or m >= P1), m = y S1 + x; the offsets of the nine
@@ -294,9 +301,9 @@ __global__ void __launch_bounds__(128) cnn_forward_kernel(int nsample, const __n
     using G = TcGeo<C, N>;
     constexpr int NT = 128;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, xbar[2];
     __shared__ uint32_t tslot;
-    __shared__ float s_emb[kLevels * kF], s_b2[kF], s_w3[kF], s_b3;
+    __shared__ __align__(16) float s_emb[kLevels * kF], s_b2[kF], s_w3[kF], s_b3;
     __shared__ float s_best[4][kF];
     __shared__ int s_idx[4][kF];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -306,20 +313,44 @@ __global__ void __launch_bounds__(128) cnn_forward_kernel(int nsample, const __n
         s_b2[threadIdx.x] = P[off_b2(C) + threadIdx.x];
         s_w3[threadIdx.x] = P[off_w3(C) + threadIdx.x];
     }
+    // the input patches go through two buffers, each filled by one bulk copy
+    // completing on its own mbarrier; the next patch's copy is issued at the
+    // start of the current one
+    auto xbuf = [&](int k) { return reinterpret_cast<uint16_t *>(smem + G::xs + k * G::xbytes); };
+    const uint16_t *const X16 = reinterpret_cast<const uint16_t *>(X);
     if (threadIdx.x == 0) {
         s_b3 = P[off_b3(C)];
         tc::mbar_init(&bar, 1);
+        tc::mbar_init(&xbar[0], 1);
+        tc::mbar_init(&xbar[1], 1);
     }
     if (warp == 0) tc::tmem_alloc(&tslot, kTmemCols);
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    if (threadIdx.x == 0 && blockIdx.x < nsample) {
+        tc::mbar_expect_tx(&xbar[0], G::xbytes);
+        tc::bulk_g2s(xbuf(0), X16 + (int64_t)blockIdx.x * (G::xbytes / 2), G::xbytes, &xbar[0]);
+    }
     const uint32_t tmem = tslot, lanes = (uint32_t)(32 * warp) << 16;
     unsigned phase = 0;
-    for (int b = blockIdx.x; b < nsample; b += gridDim.x) {
+    int it = 0;
+    bool next_pending = false;  // a bulk copy into buffer (it + 1) & 1 is in flight
+    for (int b = blockIdx.x; b < nsample; b += gridDim.x, ++it) {
+        const int cur = it & 1;
+        next_pending = b + (int)gridDim.x < nsample;
+        if (threadIdx.x == 0 && next_pending) {
+            // the other buffer was last read before the barrier that ended
+            // layer 1 of the previous patch
+            tc::fence_smem_to_async();
+            tc::mbar_expect_tx(&xbar[cur ^ 1], G::xbytes);
+            tc::bulk_g2s(xbuf(cur ^ 1), X16 + (int64_t)(b + gridDim.x) * (G::xbytes / 2), G::xbytes,
+                         &xbar[cur ^ 1]);
+        }
         const int lv = min(max(level[b], 0), kLevels - 1);
-        if (!tc_layer1<C, N, NT, false>(X, b, s_emb + lv * kF, smem, tmem, &bar, phase, nullptr)) break;
+        if (!tc_wait<NT>(&xbar[cur], (unsigned)(it >> 1) & 1u)) break;
+        if (!tc_layer1<C, N, NT, false>(X, b, xbuf(cur), s_emb + lv * kF, smem, tmem, &bar, phase, nullptr)) break;
         if (threadIdx.x == 0) {
             tc::fence_after_sync();
             tc_issue_layer2<C, N>(smem, tmem, &bar);
@@ -341,11 +372,15 @@ __global__ void __launch_bounds__(128) cnn_forward_kernel(int nsample, const __n
             tc::tmem_ld32(tmem + lanes + 32 * mt, z);
             const int q = mt * 128 + 32 * warp + lane, y = q / G::S1, x = q - y * G::S1;
             if (y < N && x < N) {
+                // a thread visits its positions in increasing order, so a
+                // strict comparison keeps the first maximum; a channel whose
+                // maximum is not positive reports no position (-1) below,
+                // whatever a thread kept for -inf or NaN values
                 const int p = y * N + x;
 #pragma unroll
                 for (int g = 0; g < kF; ++g) {
                     const float v = z[g] + s_b2[g];
-                    if (v > best[g] || (v == best[g] && p < bi[g])) {
+                    if (v > best[g]) {
                         best[g] = v;
                         bi[g] = p;
                     }
@@ -398,6 +433,9 @@ __global__ void __launch_bounds__(128) cnn_forward_kernel(int nsample, const __n
         }
         __syncthreads();
     }
+    // after a wait that gave up: the copy of the next patch may still be in
+    // flight (bounded wait)
+    if (next_pending && threadIdx.x == 0) tc::mbar_wait(&xbar[(it + 1) & 1], (unsigned)((it + 1) >> 1) & 1u);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
@@ -443,7 +481,8 @@ __global__ void __launch_bounds__(256) cnn_backward_kernel(int nsample, const __
         const int lv = min(max(level[b], 0), kLevels - 1);
         // layer 1 recomputed on the tensor cores (A1 as an FP32 map), and the
         // input patch in FP32 for the W1 gradient
-        if (!tc_layer1<C, N, NT, true>(X, b, sm + L::emb + lv * kF, tcs, tmem, &bar, phase, sm + L::a1)) break;
+        if (!tc_layer1<C, N, NT, true>(X, b, nullptr, sm + L::emb + lv * kF, tcs, tmem, &bar, phase, sm + L::a1))
+            break;
         const uint16_t *xs = reinterpret_cast<const uint16_t *>(tcs + TcGeo<C, N, true>::xs);
         for (int e = threadIdx.x; e < C * S * S; e += NT) sm[L::x + e] = __uint_as_float((uint32_t)xs[e] << 16);
         if (threadIdx.x == 0) {
@@ -635,10 +674,17 @@ af_status forward_launch(int nsample, const void *X, const int32_t *lev, const f
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return AF_ERR_CUDA;
-    // persistent CTAs: as many per SM as tensor memory holds (512 columns);
-    // shared memory and registers allow that many, and CTAs that do not fit
-    // yet simply start later
-    const int slots = sms * (512 / kTmemCols);
+    // persistent CTAs: as many per SM as tensor memory holds (512 columns)
+    // and shared memory allows (static + dynamic + the per-CTA reserve)
+    int smem_sm = 0, reserved = 0;
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k) != cudaSuccess)
+        return AF_ERR_CUDA;
+    int per_sm = smem_sm / (int)(bytes + fa.sharedSizeBytes + reserved);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 512 / kTmemCols ? 512 / kTmemCols : per_sm);
+    const int slots = sms * per_sm;
     const int grid = nsample < slots ? nsample : slots;
     k<<<grid, 128, bytes, s>>>(nsample, static_cast<const __nv_bfloat16 *>(X), lev, P, lg, M, A);
     return launched();

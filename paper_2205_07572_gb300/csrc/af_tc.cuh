@@ -1,7 +1,7 @@
 // Fifth-generation tensor core (tcgen05) helpers for sm_103a: tensor-memory
 // allocation, BF16 x BF16 -> FP32 matrix multiply-accumulate with operands
 // in shared memory and the accumulator in tensor memory, completion through
-// an mbarrier, and tensor-memory loads.  Inline PTX only (PTX ISA 8.7+,
+// an mbarrier, tensor-memory loads, and bulk copies into shared memory.  Inline PTX only (PTX ISA 8.7+,
 // tcgen05 instruction family); used by the learned tagger's convolutions.
 //
 // Operand layout (both operands K-major, no swizzle): a matrix of R rows and
@@ -91,6 +91,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float r[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
     for (int j = 0; j < 32; ++j) r[j] = __uint_as_float(v[j]);
+}
+
+// The mbarrier at `bar` expects `bytes` more transaction bytes in its
+// current phase (and receives this thread's arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
+// Bulk (TMA) copy of `bytes` from global to shared memory completing on
+// `bar`: both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     saddr(dst)),
+                 "l"(src), "r"(bytes), "r"(saddr(bar))
+                 : "memory");
 }
 
 // mbarrier helpers with a bounded wait (about a second of SM cycles, and an
