@@ -110,11 +110,11 @@ namespace af {
 struct Tiling {
     int tmx, tmy, threads, persistent;
 };
-constexpr int kNumTilings = 9;
+constexpr int kNumTilings = 10;
 AF_HD constexpr Tiling tiling(int k) {
     constexpr Tiling t[kNumTilings] = {
         {32, 32, 256, 0}, {32, 16, 192, 0}, {32, 16, 160, 0}, {32, 8, 128, 0}, {16, 16, 128, 0},
-        {32, 8, 256, 1}, {18, 18, 256, 0}, {18, 10, 192, 0}, {10, 10, 128, 0}};
+        {32, 8, 256, 1}, {18, 18, 256, 0}, {18, 10, 192, 0}, {10, 10, 128, 0}, {18, 18, 128, 0}};
     return t[k];
 }
 // Default tiling for patches of n cells (overridden per configuration by

@@ -348,6 +348,13 @@ __device__ __forceinline__ T adv_eval(const T *w, const T *Sin, int cq, int cr) 
     return v;
 }
 
+// Tile width whose node and cell items are enumerated with a compile-time
+// pitch (tile_nodes, tile_fluxes).
+template <int TMX, int NN>
+__host__ __device__ constexpr int fast_width() {
+    return (NN > 0 && TMX == NN + 2) ? NN : TMX;
+}
+
 // Point values of one staged tile (Eq. advection-update / Eq. ERFormula):
 // Q^{n+1} of every node the tile owns to the output, T = Q^n + 4 Q^{n+1/2}
 // + Q^{n+1} to ST.  Sin: window (pitch WX, plane size WSZ); ST: T arrays
@@ -368,28 +375,32 @@ __device__ __forceinline__ void tile_nodes(const StepArgs<T> &A, const typename 
     const int syhi = (y1 == n + 1) ? y1 : y1 - 1;
 
     // ---- point values.  Node-cells (ii, jj), ii in [0, tw], jj in [0, th].
-    // A full-width tile (tw == TMX) enumerates columns [0, TMX) with the
-    // compile-time pitch TMX -- one warp covers consecutive words of one row,
-    // so the block loads are free of bank conflicts -- and its last node
-    // column (ii = TMX) as a short list after them; narrower tiles use the
-    // pitch tw + 1.
-    const bool full = (tw == TMX);
-    const int pitch = full ? TMX : tw + 1;
+    // A tile of the fast width FW (tw == FW) enumerates columns [0, FW) with
+    // the compile-time pitch FW -- one warp covers consecutive words of one
+    // row, so the block loads are free of bank conflicts -- and its last node
+    // column (ii = FW) as a short list after them; other tiles use the pitch
+    // tw + 1.  FW is the tiling's width, except in a tiling two cells wider
+    // than patches of a compile-time size NN (built for whole patches with
+    // their first ghost layer), where it is NN: the tiles of patches that
+    // advance only their interior.
+    constexpr int FW = fast_width<TMX, NN>();
+    const bool full = (tw == FW);
+    const int pitch = full ? FW : tw + 1;
     const int nmain = pitch * (th + 1);
     const int nitems = nmain + (full ? th + 1 : 0);
     for (int it = threadIdx.x; it < nitems; it += NT) {
         int jj, ii;
         if (it < nmain) {
             if (full) {
-                jj = it / TMX;
-                ii = it - jj * TMX;
+                jj = it / FW;
+                ii = it - jj * FW;
             } else {
                 jj = it / pitch;
                 ii = it - jj * pitch;
             }
         } else {
             jj = it - nmain;
-            ii = TMX;
+            ii = FW;
         }
         const int i = x0 + ii, j = y0 + jj;
         const int qi = ii + 1, rj = jj + 1;
@@ -445,12 +456,13 @@ __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, 
     const int plane = NN > 0 ? (int)plane_stride(NN) : (int)A.plane;
     const int64_t pw = (int64_t)ncomp * kPlanes * plane;
     T *outp = dst_buf(A, level) + (int64_t)patch * pw;
-    const bool full = (tw == TMX);
+    constexpr int FW = fast_width<TMX, NN>();  // as in tile_nodes
+    const bool full = (tw == FW);
     for (int it = threadIdx.x; it < tw * th; it += NT) {
         int jj, ii;
         if (full) {
-            jj = it / TMX;
-            ii = it - jj * TMX;
+            jj = it / FW;
+            ii = it - jj * FW;
         } else {
             jj = it / tw;
             ii = it - jj * tw;
@@ -1051,7 +1063,7 @@ af_status launch_tiling(const StepArgs<T> &A, const typename WeightsOf<T, EQ>::t
 template <typename T, int EQ, int NN>
 af_status launch_step_nn(int k, const StepArgs<T> &A, const typename WeightsOf<T, EQ>::type &W, int nwork,
                          cudaStream_t stream) {
-    static_assert(kNumTilings == 9, "one case per compiled tiling");
+    static_assert(kNumTilings == 10, "one case per compiled tiling");
     switch (k) {
         AF_TILING_CASE(0)
         AF_TILING_CASE(1)
@@ -1062,6 +1074,7 @@ af_status launch_step_nn(int k, const StepArgs<T> &A, const typename WeightsOf<T
         AF_TILING_CASE(6)
         AF_TILING_CASE(7)
         AF_TILING_CASE(8)
+        AF_TILING_CASE(9)
     }
     return AF_ERR_ARG;
 }

@@ -283,7 +283,7 @@ af_status launch_var_tiling(const VarArgs<T> &V, int nwork, cudaStream_t stream)
 
 template <typename T, int FIELD>
 af_status launch_var(int k, const VarArgs<T> &V, int nwork, cudaStream_t stream) {
-    static_assert(kNumTilings == 9, "one case per compiled tiling");
+    static_assert(kNumTilings == 10, "one case per compiled tiling");
     switch (k) {
         AF_VAR_CASE(0)
         AF_VAR_CASE(1)
@@ -294,6 +294,7 @@ af_status launch_var(int k, const VarArgs<T> &V, int nwork, cudaStream_t stream)
         AF_VAR_CASE(6)
         AF_VAR_CASE(7)
         AF_VAR_CASE(8)
+        AF_VAR_CASE(9)
     }
     return AF_ERR_ARG;
 }

@@ -515,7 +515,7 @@ def _input_as_kernel_reads(lat, nbr, p, n):
     return out
 
 
-@pytest.mark.parametrize("tile", [(16, 16, 128), (18, 18, 256)])
+@pytest.mark.parametrize("tile", [(16, 16, 128), (18, 18, 256), (18, 18, 128)])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_bench_acoustics_forest_sampled_leaves_match_oracle(af, prec, tile):
     """The benchmark's acoustics forest at full size (levels 3-7, 4944
@@ -575,7 +575,7 @@ def test_bench_acoustics_forest_sampled_leaves_match_oracle(af, prec, tile):
         assert err < TOL[prec], (comp, err)
 
 
-@pytest.mark.parametrize("tile", [(16, 16, 128), (18, 18, 256)])
+@pytest.mark.parametrize("tile", [(16, 16, 128), (18, 18, 256), (18, 18, 128)])
 def test_regrid_where_a_neighbour_family_coarsens_matches_oracle(af, tile):
     """A leaf with eight same-level neighbours advances only its interior,
     so the copies it keeps of the point values on its right and top faces
