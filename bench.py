@@ -721,6 +721,7 @@ def learned_tagging(B=3, lmin=3, lmax=7, train_radii=(0.2, 0.3), test_radius=0.2
                         f"test r0 {test_radius}; gradient criterion (refine >= thr, coarsen < thr/4)"),
            "levels": [lmin, lmax]}
     tagq = lambda thr: (comp, kind, thr, thr / 4.0)
+    t16 = _tiling_index(16, 16, 128)  # the tiling the autotuner picks for these forests
     # ---- one tagger per regrid interval
     taggers, out["training"] = {}, {}
     for R in intervals:
@@ -728,7 +729,7 @@ def learned_tagging(B=3, lmin=3, lmax=7, train_radii=(0.2, 0.3), test_radius=0.2
         parts = []
         for r0 in train_radii:
             leaves, st = adapt_initial(cfg, B, lmin, lmax, lo, hi, [S.ring_wave_at(r0), zero, zero], tagq(4.0))
-            run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
+            run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0, tiling=t16)
             parts.append(collect(run, train_steps, tagq(4.0), lmin, 4.0, horizon=R))
             del run
         data = {k: torch.cat([p[k] for p in parts]) for k in parts[0]}
@@ -756,13 +757,13 @@ def learned_tagging(B=3, lmin=3, lmax=7, train_radii=(0.2, 0.3), test_radius=0.2
     # how well each tagger predicts the plain criterion on the test ring
     out["test_eval"] = {}
     for R, tg in taggers.items():
-        run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
+        run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0, tiling=t16)
         test = prepare(collect(run, min(test_steps, 64), tagq(4.0), lmin, 4.0, horizon=R), batch, seed=seed + 1)
         out["test_eval"][str(R)] = tg.evaluate(test)
         del run, test
 
     def tagged_run(c, tagger, every, thr, mode="batched"):
-        run = AMRRun(c, B, lmax, leaves, st, lo, hi, dt0, mode=mode)
+        run = AMRRun(c, B, lmax, leaves, st, lo, hi, dt0, mode=mode, tiling=t16)
         leaves_sum = cu = falls = regrids = steps = 0
         torch.cuda.synchronize()
         t2 = time.perf_counter()

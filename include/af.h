@@ -317,16 +317,18 @@ typedef struct {
     const int32_t *d_iy;    /* [nleaf] row */
     const int32_t *d_map;   /* per level l: (B << l)^2 entries starting at
                                af_forest_map_offset(B, l), row-major; entry
-                               (iy, ix) is the leaf index of region (l, ix, iy)
-                               if that region is a leaf, else -1 */
+                               (iy, ix) is the leaf index q of region
+                               (l, ix, iy) if that region is a leaf, -2 - q if
+                               it lies inside the coarser leaf q, else -1 */
 } af_forest;
 
 /* Offset of level l in d_map: sum over m < l of (B << m)^2. */
 int64_t af_forest_map_offset(int32_t B, int32_t level);
 
 /* Fill h_map (af_forest_map_offset(B, lmax + 1) entries, host memory) from
- * host copies of the leaf arrays.  AF_ERR_ARG on an out-of-range leaf or two
- * leaves claiming one region. */
+ * host copies of the leaf arrays (the d_map layout above).  AF_ERR_ARG on an
+ * out-of-range leaf or two leaves claiming one region (also one inside the
+ * other). */
 af_status af_forest_build_map(int32_t nleaf, int32_t B, int32_t lmax, const int32_t *h_level,
                               const int32_t *h_ix, const int32_t *h_iy, int32_t *h_map);
 

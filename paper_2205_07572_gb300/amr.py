@@ -43,36 +43,57 @@ def _leaf_order(leaves):
 
 class Forest:
     """Leaves (level, ix, iy) of a periodic forest with their region maps and
-    same-level neighbour table."""
+    same-level neighbour table.  `leaves` is a list of tuples or, with
+    arrays=(level, ix, iy), three integer arrays (any order)."""
 
-    def __init__(self, B: int, lmax: int, leaves, device="cuda"):
+    def __init__(self, B: int, lmax: int, leaves=None, device="cuda", arrays=None):
         import torch
         self.B, self.lmax = B, lmax
-        self.leaves = _leaf_order([tuple(int(v) for v in t) for t in leaves])
-        n = len(self.leaves)
-        arr = np.array(self.leaves, dtype=np.int32).reshape(n, 3)
-        self.level = np.ascontiguousarray(arr[:, 0])
-        self.ix = np.ascontiguousarray(arr[:, 1])
-        self.iy = np.ascontiguousarray(arr[:, 2])
+        if arrays is None:
+            arr = np.asarray(list(leaves), dtype=np.int32).reshape(-1, 3)
+            lv, x, y = arr[:, 0], arr[:, 1], arr[:, 2]
+        else:
+            lv, x, y = (np.asarray(a, dtype=np.int32) for a in arrays)
+        order = np.lexsort((x, y, lv))  # by level, then row, then column
+        self.level = np.ascontiguousarray(lv[order])
+        self.ix = np.ascontiguousarray(x[order])
+        self.iy = np.ascontiguousarray(y[order])
+        self._leaves = None
         self.map = af.forest_build_map(B, lmax, self.level, self.ix, self.iy)
         self.offsets = [af.forest_map_offset(B, l) for l in range(lmax + 2)]
         self.nbr = forest_neighbours(B, lmax, self.level, self.ix, self.iy, self.map)
-        t = lambda a: torch.from_numpy(a).to(device)
+        t = lambda a: torch.from_numpy(a).to(device, non_blocking=True)
         self.d_level, self.d_ix, self.d_iy, self.d_map = t(self.level), t(self.ix), t(self.iy), t(self.map)
-        self.c = af.forest_struct(n, B, lmax, self.d_level, self.d_ix, self.d_iy, self.d_map)
+        self.c = af.forest_struct(self.nleaf, B, lmax, self.d_level, self.d_ix, self.d_iy, self.d_map)
+
+    @property
+    def leaves(self):
+        """The leaves as (level, ix, iy) tuples in storage order."""
+        if self._leaves is None:
+            self._leaves = list(zip(self.level.tolist(), self.ix.tolist(), self.iy.tolist()))
+        return self._leaves
+
+    def same_leaves(self, level, ix, iy) -> bool:
+        """True if the arrays hold exactly this forest's leaves (any order)."""
+        if len(level) != self.nleaf:
+            return False
+        o = np.lexsort((ix, iy, level))
+        return (np.array_equal(np.asarray(level)[o], self.level) and np.array_equal(np.asarray(ix)[o], self.ix)
+                and np.array_equal(np.asarray(iy)[o], self.iy))
 
     @property
     def nleaf(self) -> int:
-        return len(self.leaves)
+        return len(self.level)
 
     @property
     def levels(self):
-        return sorted(set(self.level.tolist()))
+        return np.unique(self.level).tolist()
 
     def region(self, l: int, x: int, y: int) -> int:
         """Leaf index of region (l, x, y) (periodic) if it is a leaf, else -1."""
         side = self.B << l
-        return int(self.map[self.offsets[l] + (y % side) * side + (x % side)])
+        q = int(self.map[self.offsets[l] + (y % side) * side + (x % side)])
+        return q if q >= 0 else -1
 
     def level_slice(self, l: int) -> slice:
         lo = int(np.searchsorted(self.level, l, side="left"))
@@ -111,23 +132,33 @@ def forest_neighbours(B, lmax, level, ix, iy, fmap) -> np.ndarray:
     return out
 
 
-def regrid_leaves(forest: Forest, tags, lmin: int):
-    """New leaf set from per-leaf tags (af_forest_regrid): leaves tagged 1
-    below lmax are split, complete families of four leaves tagged -1 above
-    lmin are merged unless the merged leaf would sit next to a leaf two levels
-    finer, then leaves are split until the forest is 2:1 balanced."""
+def regrid_arrays(forest: Forest, tags, lmin: int):
+    """New leaf set from per-leaf tags (af_forest_regrid) as arrays (level,
+    ix, iy): leaves tagged 1 below lmax are split, complete families of four
+    leaves tagged -1 above lmin are merged unless the merged leaf would sit
+    next to a leaf two levels finer, then leaves are split until the forest
+    is 2:1 balanced."""
     tags = np.ascontiguousarray(tags, dtype=np.int8)
     L = _lib()
     cnt = C.c_int32(0)
     args = (forest.nleaf, forest.B, lmin, forest.lmax, _ip(forest.level), _ip(forest.ix), _ip(forest.iy),
             tags.ctypes.data)
-    st = L.af_forest_regrid(*args, 0, None, None, None, C.byref(cnt))
-    if st != 0 and cnt.value == 0:
-        af._check(st, "af_forest_regrid")
+    # at most four leaves per leaf before balancing; try that capacity first
+    cap = 4 * forest.nleaf + 64
+    lv, x, y = (np.empty(cap, dtype=np.int32) for _ in range(3))
+    st = L.af_forest_regrid(*args, cap, _ip(lv), _ip(x), _ip(y), C.byref(cnt))
     m = cnt.value
-    lv, x, y = (np.empty(max(m, 1), dtype=np.int32) for _ in range(3))
-    af._check(L.af_forest_regrid(*args, m, _ip(lv), _ip(x), _ip(y), C.byref(cnt)), "af_forest_regrid")
-    return list(zip(lv[:m].tolist(), x[:m].tolist(), y[:m].tolist()))
+    if st != 0 and m > cap:  # a larger forest after balancing: ask again with the size it reported
+        lv, x, y = (np.empty(m, dtype=np.int32) for _ in range(3))
+        st = L.af_forest_regrid(*args, m, _ip(lv), _ip(x), _ip(y), C.byref(cnt))
+    af._check(st, "af_forest_regrid")
+    return lv[:m], x[:m], y[:m]
+
+
+def regrid_leaves(forest: Forest, tags, lmin: int):
+    """regrid_arrays as a list of (level, ix, iy) tuples."""
+    lv, x, y = regrid_arrays(forest, tags, lmin)
+    return list(zip(lv.tolist(), x.tolist(), y.tolist()))
 
 
 MODES = ("batched", "per_level", "per_patch")
@@ -163,7 +194,12 @@ class AMRRun:
         self.forest = Forest(B, lmax, leaves, device)
         order = {leaf: k for k, leaf in enumerate(_leaf_order(leaves))}
         st = np.asarray(state).reshape(len(leaves), -1)[[order[leaf] for leaf in self.forest.leaves]]
-        self.a = torch.as_tensor(st).to(device=device, dtype=self.dtype).contiguous()
+        # three state buffers of growing capacity: the current pair and the
+        # one a regrid transfers into (so a regrid allocates nothing large)
+        self._pool = [None, None, None]
+        self._ia, self._ib = 0, 1
+        self.a = self._buffer(0, self.forest.nleaf)
+        self.a.copy_(torch.as_tensor(st).to(dtype=self.dtype))
         self.parity = 0
         self.time = 0.0
         self._setup()
@@ -178,10 +214,25 @@ class AMRRun:
     def pair(self) -> af.StatePair:
         return af.state_pair(self.a, self.b, self.parity)
 
+    def _buffer(self, i: int, nleaf: int):
+        """View [nleaf, words] of pool buffer i, grown (by a quarter beyond
+        the request) if it is too small."""
+        import torch
+        need = max(1, nleaf) * self.words
+        buf = self._pool[i]
+        if buf is None or buf.numel() < need:
+            buf = torch.empty(need + need // 4, dtype=self.dtype, device=self.device)
+            self._pool[i] = buf
+        return buf[:nleaf * self.words].view(nleaf, self.words)
+
     def _setup(self):
         import torch
         F = self.forest
-        self.b = torch.zeros_like(self.a) if self.mode == "batched" else self.a.clone()
+        self.b = self._buffer(self._ib, F.nleaf)
+        if self.mode == "batched":
+            self.b.zero_()
+        else:
+            self.b.copy_(self.a)
         self.freg = torch.zeros((F.nleaf, 4, self.cfg.ncomp, self.cfg.n), dtype=torch.float64, device=self.device)
         # work items are in leaf order, so every level's items are contiguous
         self.set_tiling(self.tiling)
@@ -207,17 +258,18 @@ class AMRRun:
             groups = [(np.nonzero(~ext)[0], self.tiling), (np.nonzero(ext)[0], self.ext_tiling)]
         # one work list per group, each in leaf order (levels contiguous)
         self.work_groups = []
+        w0 = None
         for idx, til in groups:
             w = af.build_step_work(self.cfg, idx, F.level[idx], F.nbr[idx], tiling=til, ix=F.ix[idx], iy=F.iy[idx])
+            w0 = w if w0 is None else w0
             nw = len(w) // 64
             wl = w.view(np.int32).reshape(nw, 16)[:, 1] if nw else np.zeros(0, np.int32)
             starts = [int(np.searchsorted(wl, l, side="left")) for l in range(self.lmax + 2)]
             self.work_groups.append((torch.from_numpy(w).to(self.device), nw, starts, til))
         self.work_all, nwork, self.work_start, _ = self.work_groups[0]
-        wi = (self.work_all.cpu().numpy().view(np.int32).reshape(nwork, 16) if nwork
-              else np.zeros((0, 16), np.int32))
         self.nwork = nwork
         if self.mode == "per_patch":
+            wi = w0.view(np.int32).reshape(nwork, 16) if nwork else np.zeros((0, 16), np.int32)
             p = np.arange(F.nleaf)
             self.patch_work = list(zip(np.searchsorted(wi[:, 0], p, side="left").tolist(),
                                        np.searchsorted(wi[:, 0], p, side="right").tolist()))
@@ -367,16 +419,19 @@ class AMRRun:
         return t.cpu().numpy(), ind.cpu().numpy()
 
     def regrid(self, tags, lmin: int) -> bool:
-        import torch
-        new = regrid_leaves(self.forest, tags, lmin)
-        if new == self.forest.leaves:
+        lv, x, y = regrid_arrays(self.forest, tags, lmin)
+        if self.forest.same_leaves(lv, x, y):
             return False
-        old_forest, old_pair = self.forest, self.pair
-        old_bufs = (self.a, self.b)
-        self.forest = Forest(self.B, self.lmax, new, self.device)
-        self.a = torch.empty((self.forest.nleaf, self.words), dtype=self.dtype, device=self.device)
+        old_forest, old_pair, old_bufs = self.forest, self.pair, (self.a, self.b)
+        self.forest = Forest(self.B, self.lmax, device=self.device, arrays=(lv, x, y))
+        # the new state goes to the pool buffer the old pair does not use; the
+        # old current array's buffer then holds the new second array (zeroed
+        # by _setup after the transfer, in stream order)
+        ic = 3 - self._ia - self._ib
+        self.a = self._buffer(ic, self.forest.nleaf)
         af.transfer_pair(self.cfg, old_forest.c, old_pair, self.forest.c, self.a)
         self._keep = (old_forest, old_bufs)  # the old arrays stay alive until the copy ran
+        self._ia, self._ib = ic, self._ia
         self.parity = 0
         self._setup()
         self.fill(self.all_levels, self.all_levels)

@@ -42,15 +42,29 @@ __host__ __device__ inline long long map_offset(int B, int l) {
 __device__ __forceinline__ long long hwid(const DevForest &F, int l) { return 2LL << (F.lmax - l); }
 
 __device__ __forceinline__ long long wrapd(const DevForest &F, long long x) {
+    // positions are at most one domain width outside [0, D)
+    if (x >= 0 && x < F.D) return x;
+    if (x < 0 && x >= -F.D) return x + F.D;
+    if (x >= F.D && x < 2 * F.D) return x - F.D;
     long long r = x % F.D;
     return r < 0 ? r + F.D : r;
 }
 
-// Leaf whose half-open extent contains (x, y).
+// Leaf whose half-open extent contains (x, y).  A region of the finest level
+// lmax is a leaf (entry q >= 0) or lies inside the coarser leaf -2 - entry
+// (af_forest_build_map), so one load finds it; a map without that second
+// kind of entry is searched level by level.
 __device__ int lookup(const DevForest &F, long long x, long long y) {
     x = wrapd(F, x);
     y = wrapd(F, y);
-    for (int l = F.lmax; l >= 0; --l) {
+    {
+        const long long pw = 2LL * F.n;  // a finest-level region, in units
+        const long long side = (long long)F.B << F.lmax;
+        const int q = __ldg(F.map + map_offset(F.B, F.lmax) + (y / pw) * side + (x / pw));
+        if (q >= 0) return q < F.nleaf ? q : -1;
+        if (q <= -2) return -2 - q < F.nleaf ? -2 - q : -1;
+    }
+    for (int l = F.lmax - 1; l >= 0; --l) {
         const long long pw = (long long)F.n * hwid(F, l);
         const long long side = (long long)F.B << l;
         const int q = __ldg(F.map + map_offset(F.B, l) + (y / pw) * side + (x / pw));
@@ -120,31 +134,63 @@ struct StateView {
 // Lattice indices (i, j) of point (x, y) in plane k of leaf q.
 __device__ __forceinline__ void lattice_of(const DevForest &F, int q, int k, long long x, long long y, int &i,
                                            int &j) {
-    const long long hw = hwid(F, __ldg(F.level + q));
+    const int sh = F.lmax - __ldg(F.level + q) + 1;  // hw = 2^sh
+    const long long hw = 1LL << sh;
     long long dx = reld(F, x, leaf_x0(F, q)), dy = reld(F, y, leaf_y0(F, q));
     if (k == kAvg || k == kYmid) dx -= hw / 2;
     if (k == kAvg || k == kXmid) dy -= hw / 2;
-    i = (int)(dx >= 0 ? dx / hw : -((-dx + hw - 1) / hw));
-    j = (int)(dy >= 0 ? dy / hw : -((-dy + hw - 1) / hw));
+    i = (int)(dx >> sh);  // floor division (arithmetic shift)
+    j = (int)(dy >> sh);
     // owners are always within two cells of the lattice; clamp defensively
     const int lo = -kGhost, hi = F.n + kGhost;
     i = i < lo ? lo : (i > hi ? hi : i);
     j = j < lo ? lo : (j > hi ? hi : j);
 }
 
+// Explicitly rounded operations: the reconstruction below is evaluated in
+// one fixed order of roundings wherever it is inlined, so the direct and the
+// planned ghost exchange (and the regrid transfer) agree bit for bit.
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// sum_a w_a row_a of the three rows of nodal values with weights (l0, l1, l2)
+// in x and (m0, m1, m2) in y.
+template <typename R>
+__device__ __forceinline__ R recon_combine(R c00, R c10, R c01, R c11, R xl, R xr, R yb, R yt, R cen, R l0, R l1,
+                                           R l2, R m0, R m1, R m2) {
+    const R r0 = r_fma(l2, c10, r_fma(l1, yb, r_mul(l0, c00)));
+    const R r1 = r_fma(l2, xr, r_fma(l1, cen, r_mul(l0, xl)));
+    const R r2 = r_fma(l2, c11, r_fma(l1, yt, r_mul(l0, c01)));
+    return r_fma(m2, r2, r_fma(m1, r1, r_mul(m0, r0)));
+}
+
+// The centre value of the biquadratic from its average and boundary nodes:
+// (9/4) Q - (1/16) sum(corners) - (1/4) sum(edge midpoints).
+template <typename R>
+__device__ __forceinline__ R recon_centre(R c00, R c10, R c01, R c11, R xl, R xr, R yb, R yt, R avg) {
+    const R sc = r_add(r_add(c00, c10), r_add(c01, c11)), se = r_add(r_add(xl, xr), r_add(yb, yt));
+    return r_sub(r_sub(r_mul(R(2.25), avg), r_mul(R(0.0625), sc)), r_mul(R(0.25), se));
+}
+
 // The reconstruction (Eq. poly) of one cell at (xi, eta) in [-1, 1]^2 from
 // its corners c.., edge midpoints x./y. and average: the tensor Lagrange
-// interpolant on {-1,0,1}^2 whose centre value follows from the average,
-// (9/4) Q - (1/16) sum(corners) - (1/4) sum(edge midpoints).
+// interpolant on {-1,0,1}^2 whose centre value follows from the average.
 // Evaluated in the state's precision R (FP32 for an FP32 state: GB300's
 // FP64 rate is a small fraction of its FP32 rate).
 template <typename R>
 __device__ __forceinline__ R recon_eval(R c00, R c10, R c01, R c11, R xl, R xr, R yb, R yt, R avg, R xi, R eta) {
-    const R cen = R(2.25) * avg - R(0.0625) * (c00 + c10 + c01 + c11) - R(0.25) * (xl + xr + yb + yt);
-    const R lx0 = R(0.5) * xi * (xi - R(1)), lx1 = R(1) - xi * xi, lx2 = R(0.5) * xi * (xi + R(1));
-    const R ly0 = R(0.5) * eta * (eta - R(1)), ly1 = R(1) - eta * eta, ly2 = R(0.5) * eta * (eta + R(1));
-    return ly0 * (lx0 * c00 + lx1 * yb + lx2 * c10) + ly1 * (lx0 * xl + lx1 * cen + lx2 * xr) +
-           ly2 * (lx0 * c01 + lx1 * yt + lx2 * c11);
+    const R cen = recon_centre<R>(c00, c10, c01, c11, xl, xr, yb, yt, avg);
+    const R lx0 = r_mul(r_mul(R(0.5), xi), r_sub(xi, R(1))), lx1 = r_sub(R(1), r_mul(xi, xi));
+    const R lx2 = r_mul(r_mul(R(0.5), xi), r_add(xi, R(1)));
+    const R ly0 = r_mul(r_mul(R(0.5), eta), r_sub(eta, R(1))), ly1 = r_sub(R(1), r_mul(eta, eta));
+    const R ly2 = r_mul(r_mul(R(0.5), eta), r_add(eta, R(1)));
+    return recon_combine<R>(c00, c10, c01, c11, xl, xr, yb, yt, cen, lx0, lx1, lx2, ly0, ly1, ly2);
 }
 
 // Mean of the biquadratic reconstruction of a cell (nodal values as for
@@ -157,12 +203,10 @@ __device__ __forceinline__ R recon_eval(R c00, R c10, R c01, R c11, R xl, R xr, 
 template <typename R>
 __device__ __forceinline__ R recon_quarter_mean(R c00, R c10, R c01, R c11, R xl, R xr, R yb, R yt, R avg, int qx,
                                                 int qy) {
-    const R cen = R(2.25) * avg - R(0.0625) * (c00 + c10 + c01 + c11) - R(0.25) * (xl + xr + yb + yt);
+    const R cen = recon_centre<R>(c00, c10, c01, c11, xl, xr, yb, yt, avg);
     const R lo = R(5) / R(12), mid = R(2) / R(3), hi = R(-1) / R(12);
-    const R lx0 = qx ? hi : lo, lx1 = mid, lx2 = qx ? lo : hi;
-    const R ly0 = qy ? hi : lo, ly1 = mid, ly2 = qy ? lo : hi;
-    return ly0 * (lx0 * c00 + lx1 * yb + lx2 * c10) + ly1 * (lx0 * xl + lx1 * cen + lx2 * xr) +
-           ly2 * (lx0 * c01 + lx1 * yt + lx2 * c11);
+    return recon_combine<R>(c00, c10, c01, c11, xl, xr, yb, yt, cen, qx ? hi : lo, mid, qx ? lo : hi,
+                            qy ? hi : lo, mid, qy ? lo : hi);
 }
 
 // Simpson's rule over a cell from the values f(a, b) at its 3 x 3 points
@@ -172,48 +216,81 @@ __device__ __forceinline__ R simpson9(Fn f) {
     const R w[3] = {R(1) / R(6), R(2) / R(3), R(1) / R(6)};
     R s = R(0);
     for (int b = 0; b < 3; ++b)
-        for (int a = 0; a < 3; ++a) s += w[a] * w[b] * f(a, b);
+        for (int a = 0; a < 3; ++a) s = r_fma(r_mul(w[a], w[b]), f(a, b), s);
     return s;
 }
 
-// Value of the reconstruction of leaf q, component c, at (x, y); with
-// quarter >= 0 instead the mean of the reconstruction over the quarter of
-// the cell holding (x, y) that (x, y) lies in (the centre of a finer cell).
+// The nine values the reconstruction of one cell of leaf q combines at
+// (x, y) (component 0; component c is cstride entries further), and where
+// (x, y) lies in the cell.
 template <typename T>
-__device__ T recon_at(const DevForest &F, const StateView<T> &S, int q, int c, long long x, long long y,
-                      bool quarter = false) {
-    const long long hw = hwid(F, __ldg(F.level + q));
+struct ReconSite {
+    const T *v[9];  // c00, c10, c01, c11, xl, xr, yb, yt, avg
+    T xi, eta;      // position in [-1, 1]^2
+    int qx, qy;     // quarter holding (x, y)
+};
+
+template <typename T>
+__device__ void recon_locate(const DevForest &F, const StateView<T> &S, int q, long long x, long long y,
+                             ReconSite<T> &r) {
+    const int sh = F.lmax - __ldg(F.level + q) + 1;  // hw = 2^sh
+    const long long hw = 1LL << sh;
     const long long dx = reld(F, x, leaf_x0(F, q)), dy = reld(F, y, leaf_y0(F, q));
-    long long ci = dx >= 0 ? dx / hw : -1, cj = dy >= 0 ? dy / hw : -1;
+    long long ci = dx >= 0 ? (dx >> sh) : -1, cj = dy >= 0 ? (dy >> sh) : -1;
     ci = ci < 0 ? 0 : (ci > F.n - 1 ? F.n - 1 : ci);
     cj = cj < 0 ? 0 : (cj > F.n - 1 ? F.n - 1 : cj);
-    const T xi = (T)(2.0 * (double)(dx - ci * hw) / (double)hw - 1.0);  // exact: a multiple of 1/2
-    const T eta = (T)(2.0 * (double)(dy - cj * hw) / (double)hw - 1.0);
-    const int qx = 2 * (dx - ci * hw) >= hw, qy = 2 * (dy - cj * hw) >= hw;
+    r.xi = (T)(2.0 * (double)(dx - ci * hw) / (double)hw - 1.0);  // exact: a multiple of 1/2
+    r.eta = (T)(2.0 * (double)(dy - cj * hw) / (double)hw - 1.0);
+    r.qx = 2 * (dx - ci * hw) >= hw;
+    r.qy = 2 * (dy - cj * hw) >= hw;
     const int i = (int)ci, j = (int)cj;
     // Point values on the leaf's boundary lines are read from their owner:
     // a leaf whose neighbours are all same-level does not keep the copies in
     // its ghost ring current (its step reads the neighbours directly).
-    auto node = [&](int k, int ii, int jj) -> T {
-        if (ii > 0 && ii < F.n && jj > 0 && jj < F.n) return *S.at(q, c, k, ii, jj);
-        long long nx, ny;
+    auto node = [&](int k, int ii, int jj) -> const T * {
+        if (ii > 0 && ii < F.n && jj > 0 && jj < F.n) return S.at(q, 0, k, ii, jj);
         const long long x0 = leaf_x0(F, q), y0 = leaf_y0(F, q);
-        nx = x0 + (long long)ii * hw + (k == kYmid ? hw / 2 : 0);
-        ny = y0 + (long long)jj * hw + (k == kXmid ? hw / 2 : 0);
+        const long long nx = x0 + (long long)ii * hw + (k == kYmid ? hw / 2 : 0);
+        const long long ny = y0 + (long long)jj * hw + (k == kXmid ? hw / 2 : 0);
         const int o = node_owner(F, nx, ny);
-        if (o < 0 || o == q) return *S.at(q, c, k, ii, jj);
+        if (o < 0 || o == q) return S.at(q, 0, k, ii, jj);
         const int lo = __ldg(F.level + o);
+        const int ko = lo == __ldg(F.level + q) ? k : kCorner;
         int oi, oj;
-        lattice_of(F, o, lo == __ldg(F.level + q) ? k : kCorner, nx, ny, oi, oj);
-        return *S.at(o, c, lo == __ldg(F.level + q) ? k : kCorner, oi, oj);
+        lattice_of(F, o, ko, nx, ny, oi, oj);
+        return S.at(o, 0, ko, oi, oj);
     };
-    const T c00 = node(kCorner, i, j), c10 = node(kCorner, i + 1, j);
-    const T c01 = node(kCorner, i, j + 1), c11 = node(kCorner, i + 1, j + 1);
-    const T xl = node(kXmid, i, j), xr = node(kXmid, i + 1, j);
-    const T yb = node(kYmid, i, j), yt = node(kYmid, i, j + 1);
-    const T avg = *S.at(q, c, kAvg, i, j);
-    if (quarter) return recon_quarter_mean<T>(c00, c10, c01, c11, xl, xr, yb, yt, avg, qx, qy);
-    return recon_eval<T>(c00, c10, c01, c11, xl, xr, yb, yt, avg, xi, eta);
+    r.v[0] = node(kCorner, i, j);
+    r.v[1] = node(kCorner, i + 1, j);
+    r.v[2] = node(kCorner, i, j + 1);
+    r.v[3] = node(kCorner, i + 1, j + 1);
+    r.v[4] = node(kXmid, i, j);
+    r.v[5] = node(kXmid, i + 1, j);
+    r.v[6] = node(kYmid, i, j);
+    r.v[7] = node(kYmid, i, j + 1);
+    r.v[8] = S.at(q, 0, kAvg, i, j);
+}
+
+// The reconstruction at a located site (quarter: its mean over the quarter
+// of the cell holding the site instead), component offset coff.
+template <typename T>
+__device__ __forceinline__ T recon_value(const ReconSite<T> &r, int64_t coff, bool quarter) {
+    T v[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) v[e] = r.v[e][coff];
+    if (quarter) return recon_quarter_mean<T>(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], r.qx, r.qy);
+    return recon_eval<T>(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], r.xi, r.eta);
+}
+
+// Value of the reconstruction of leaf q, component c, at (x, y); with
+// quarter set instead the mean of the reconstruction over the quarter of the
+// cell holding (x, y) that (x, y) lies in (the centre of a finer cell).
+template <typename T>
+__device__ T recon_at(const DevForest &F, const StateView<T> &S, int q, int c, long long x, long long y,
+                      bool quarter = false) {
+    ReconSite<T> r;
+    recon_locate<T>(F, S, q, x, y, r);
+    return recon_value<T>(r, (int64_t)c * kPlanes * S.plane, quarter);
 }
 
 // Value for an entry of plane k of a destination at level lp from owner q
@@ -249,6 +326,51 @@ __device__ double transfer(const DevForest &F, const StateView<T> &S, int lp, in
     if (lq == lp - 1) return (double)recon_at<T>(F, S, q, c, x, y, true);
     const long long h = hwid(F, lp) / 2;
     return (double)simpson9<T>([&](int a, int b) { return recon_at<T>(F, S, q, c, x + (a - 1) * h, y + (b - 1) * h); });
+}
+
+// transfer() for every component c < nc at once (the owner's sites are
+// located once): out[c].
+template <typename T>
+__device__ void transfer_all(const DevForest &F, const StateView<T> &S, int lp, int q, int k, long long x,
+                             long long y, int nc, double out[3]) {
+    const int lq = __ldg(F.level + q);
+    const int64_t cs = (int64_t)kPlanes * S.plane;
+    int i, j;
+    if (lq == lp || (lq > lp && k != kAvg)) {
+        const int ko = lq == lp ? k : kCorner;
+        lattice_of(F, q, ko, x, y, i, j);
+        const T *v = S.at(q, 0, ko, i, j);
+        for (int c = 0; c < nc; ++c) out[c] = (double)v[c * cs];
+        return;
+    }
+    if (lq > lp) {  // an average from a finer owner: the mean of its four cells
+        const long long h = hwid(F, lq) / 2;
+        const T *v[4];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                lattice_of(F, q, kAvg, x + (2 * a - 1) * h, y + (2 * b - 1) * h, i, j);
+                v[2 * b + a] = S.at(q, 0, kAvg, i, j);
+            }
+        for (int c = 0; c < nc; ++c) {
+            // the same order of additions as transfer()
+            double s = 0.0;
+            s += (double)v[0][c * cs];
+            s += (double)v[1][c * cs];
+            s += (double)v[2][c * cs];
+            s += (double)v[3][c * cs];
+            out[c] = 0.25 * s;
+        }
+        return;
+    }
+    if (k != kAvg || lq == lp - 1) {  // a coarser owner: its reconstruction (quarter mean for an average)
+        ReconSite<T> r;
+        recon_locate<T>(F, S, q, x, y, r);
+        for (int c = 0; c < nc; ++c) out[c] = (double)recon_value<T>(r, c * cs, k == kAvg);
+        return;
+    }
+    for (int c = 0; c < nc; ++c) out[c] = transfer<T>(F, S, lp, q, c, k, x, y);
 }
 
 __device__ __forceinline__ void entry_xy(const DevForest &F, int p, int k, int i, int j, long long &x, long long &y) {
@@ -297,7 +419,9 @@ __global__ void fill_kernel(DevForest F, StateView<T> S, uint32_t dst, uint32_t 
         const int rel_pass = lq > lp ? 0 : (lq == lp ? 1 : 2);
         if (rel_pass != pass || !((src >> lq) & 1u)) continue;
         if ((flags & AF_FILL_SAME_LEVEL_ONLY) && lq != lp) continue;
-        for (int c = 0; c < S.ncomp; ++c) *S.at(p, c, k, i, j) = (T)transfer<T>(F, S, lp, q, c, k, x, y);
+        double v[3];
+        transfer_all<T>(F, S, lp, q, k, x, y, S.ncomp, v);
+        for (int c = 0; c < S.ncomp; ++c) *S.at(p, c, k, i, j) = (T)v[c];
     }
 }
 
@@ -548,7 +672,9 @@ __global__ void transfer_kernel(DevForest Fo, StateView<T> So, DevForest Fn, Sta
             const long long y = y0 + (long long)j * hwn + (k == kXmid ? hwn / 2 : 0);
             const int q = entry_owner(Fo, k, x, y);
             if (q < 0 || q == same) continue;
-            for (int c = 0; c < Sn.ncomp; ++c) *Sn.at(p, c, k, i, j) = (T)transfer<T>(Fo, So, l, q, c, k, x, y);
+            double v[3];
+            transfer_all<T>(Fo, So, l, q, k, x, y, Sn.ncomp, v);
+            for (int c = 0; c < Sn.ncomp; ++c) *Sn.at(p, c, k, i, j) = (T)v[c];
         }
         return;
     }
@@ -570,7 +696,9 @@ __global__ void transfer_kernel(DevForest Fo, StateView<T> So, DevForest Fn, Sta
         // an average comes from at most one level finer (the four children's
         // mean); a point value is the coinciding vertex of any finer owner
         if (k == kAvg && __ldg(Fo.level + q) > l + 1) continue;
-        for (int c = 0; c < Sn.ncomp; ++c) *Sn.at(p, c, k, i, j) = (T)transfer<T>(Fo, So, l, q, c, k, x, y);
+        double v[3];
+        transfer_all<T>(Fo, So, l, q, k, x, y, Sn.ncomp, v);
+        for (int c = 0; c < Sn.ncomp; ++c) *Sn.at(p, c, k, i, j) = (T)v[c];
     }
 }
 
@@ -770,6 +898,21 @@ extern "C" af_status af_forest_build_map(int32_t nleaf, int32_t B, int32_t lmax,
         int32_t &slot = h_map[map_offset(B, l) + (long long)h_iy[p] * side + h_ix[p]];
         if (slot >= 0) return AF_ERR_ARG;
         slot = p;
+    }
+    // regions inside a leaf, at every finer level: -2 - (the leaf)
+    for (int p = 0; p < nleaf; ++p) {
+        const int l = h_level[p];
+        for (int m = l + 1; m <= lmax; ++m) {
+            const long long side = (long long)B << m, w = 1LL << (m - l);
+            const long long x0 = (long long)h_ix[p] * w, y0 = (long long)h_iy[p] * w;
+            int32_t *row = h_map + map_offset(B, m);
+            for (long long y = y0; y < y0 + w; ++y)
+                for (long long x = x0; x < x0 + w; ++x) {
+                    int32_t &slot = row[y * side + x];
+                    if (slot != -1) return AF_ERR_ARG;  // overlapping leaves
+                    slot = -2 - p;
+                }
+        }
     }
     return AF_OK;
 }
