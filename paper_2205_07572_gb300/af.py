@@ -162,15 +162,18 @@ def build_step_work(cfg: Config, patches, levels=None, nbr=None, tiling=None, ix
     k = default_tiling(cfg) if tiling is None else int(tiling)
     cnt = C.c_int32(0)
     ip = lambda a: None if a is None else a.ctypes.data_as(_IP)
-    st = L.af_build_step_work_at(C.byref(cfg), k, npatch, ip(patches), ip(lv), ip(px), ip(py), ip(nb), None, 0,
-                                 C.byref(cnt))
-    if st != 0 and cnt.value == 0:
-        _check(st, "af_build_step_work")
-    buf = (Work * max(cnt.value, 1))()
-    st = L.af_build_step_work_at(C.byref(cfg), k, npatch, ip(patches), ip(lv), ip(px), ip(py), ip(nb), buf,
-                                 cnt.value, C.byref(cnt))
+    # a first guess of the capacity (four tiles per patch), then the count the
+    # library reports if that was too small
+    cap = 4 * npatch + 8
+    for _ in range(2):
+        buf = np.empty(64 * cap, dtype=np.uint8)
+        st = L.af_build_step_work_at(C.byref(cfg), k, npatch, ip(patches), ip(lv), ip(px), ip(py), ip(nb),
+                                     buf.ctypes.data_as(C.POINTER(Work)), cap, C.byref(cnt))
+        if st == 0 or cnt.value <= cap:
+            break
+        cap = cnt.value
     _check(st, "af_build_step_work")
-    return np.frombuffer(buf, dtype=np.uint8, count=64 * cnt.value).copy()
+    return buf[:64 * cnt.value].copy() if cnt.value < cap else buf
 
 
 def patch_step(cfg: Config, work, nwork: int, state_in, state_out, dt0: float, dx0: float, dy0: float,

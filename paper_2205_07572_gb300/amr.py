@@ -416,7 +416,8 @@ class AMRRun:
         ind = torch.zeros(self.forest.nleaf, dtype=torch.float64, device=self.device)
         af.tag_pair(self.cfg, self.forest.c, self.pair, comp, kind, self.dx0, self.dy0, refine_thr, coarsen_thr,
                     t, ind)
-        return t.cpu().numpy(), ind.cpu().numpy()
+        ind = ind.cpu().numpy()  # one synchronisation: the tags are in place by then
+        return t.cpu().numpy(), ind
 
     def regrid(self, tags, lmin: int) -> bool:
         lv, x, y = regrid_arrays(self.forest, tags, lmin)

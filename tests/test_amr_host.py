@@ -51,6 +51,33 @@ def test_forest_map_and_neighbours(amr):
         assert all(F.level[sl] == l)
 
 
+def test_forest_map_entries_by_direct_geometry(amr):
+    """af_forest_build_map: at every level, a region that is a leaf holds its
+    index, a region inside a coarser leaf q holds -2 - q, a region holding
+    finer leaves holds -1 (checked region by region from the leaves'
+    extents); a forest whose leaves overlap is refused."""
+    from paper_2205_07572_gb300 import af
+    B, lmax = 2, 3
+    leaves = _sorted(S.balanced_forest(B, 1, 3, lambda l, x, y: x == y))
+    F = amr.Forest(B, lmax, leaves, device="cpu")
+    for l in range(lmax + 1):
+        side = B << l
+        off = F.offsets[l]
+        for y in range(side):
+            for x in range(side):
+                got = int(F.map[off + y * side + x])
+                inside = [k for k, (m, ix, iy) in enumerate(F.leaves)
+                          if m <= l and (x >> (l - m)) == ix and (y >> (l - m)) == iy]
+                if inside:
+                    (k,) = inside
+                    assert got == (k if F.leaves[k][0] == l else -2 - k), (l, x, y)
+                else:
+                    assert got == -1, (l, x, y)
+    lv = np.array([1, 2], np.int32)
+    with pytest.raises(af.AFError):   # leaf (2, 0, 0) lies inside leaf (1, 0, 0)
+        af.forest_build_map(B, lmax, lv, np.zeros(2, np.int32), np.zeros(2, np.int32))
+
+
 def test_batched_schedule_advances_each_level_by_its_substeps(amr, monkeypatch):
     """Host logic of the batched driver, with the library calls recorded
     instead of launched: at every time of the subcycled schedule one step
