@@ -54,10 +54,19 @@ class Forest:
             lv, x, y = arr[:, 0], arr[:, 1], arr[:, 2]
         else:
             lv, x, y = (np.asarray(a, dtype=np.int32) for a in arrays)
-        order = np.lexsort((x, y, lv))  # by level, then row, then column
-        self.level = np.ascontiguousarray(lv[order])
-        self.ix = np.ascontiguousarray(x[order])
-        self.iy = np.ascontiguousarray(y[order])
+        # by level, then row, then column (the native regrid already writes
+        # that order, which one pass over the packed keys confirms)
+        if (B << lmax) < (1 << 21):
+            key = (lv.astype(np.int64) << 42) | (y.astype(np.int64) << 21) | x.astype(np.int64)
+            if len(key) > 1 and not bool(np.all(key[1:] > key[:-1])):
+                order = np.argsort(key, kind="stable")
+                lv, x, y = lv[order], x[order], y[order]
+        else:
+            order = np.lexsort((x, y, lv))
+            lv, x, y = lv[order], x[order], y[order]
+        self.level = np.ascontiguousarray(lv)
+        self.ix = np.ascontiguousarray(x)
+        self.iy = np.ascontiguousarray(y)
         self._leaves = None
         self.map = af.forest_build_map(B, lmax, self.level, self.ix, self.iy)
         self.offsets = [af.forest_map_offset(B, l) for l in range(lmax + 2)]

@@ -98,7 +98,9 @@ extern "C" af_status af_forest_neighbours(int32_t nleaf, int32_t B, int32_t lmax
         const int l = h_level[p], s = B << l;
         const int64_t off = (int64_t)B * B * (((int64_t)1 << (2 * l)) - 1) / 3;
         for (int d = 0; d < 8; ++d) {
-            const int nx = ((h_ix[p] + dirs[d][0]) % s + s) % s, ny = ((h_iy[p] + dirs[d][1]) % s + s) % s;
+            int nx = h_ix[p] + dirs[d][0], ny = h_iy[p] + dirs[d][1];  // periodic wrap
+            nx = nx < 0 ? nx + s : (nx >= s ? nx - s : nx);
+            ny = ny < 0 ? ny + s : (ny >= s ? ny - s : ny);
             const int32_t q = h_map[off + (int64_t)ny * s + nx];
             h_nbr[8 * p + d] = q >= 0 ? q : -1;
         }
