@@ -655,7 +655,14 @@ __global__ void transfer_kernel(DevForest Fo, StateView<T> So, DevForest Fn, Sta
     const long long x0 = (long long)px * n * hwn, y0 = (long long)py * n * hwn;
     if (same >= 0) {
         const T *srcp = So.patch(same);
-        for (int64_t e = threadIdx.x; e < words; e += blockDim.x) dst[e] = srcp[e];
+        constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte load
+        if (words % V == 0 && ((reinterpret_cast<uintptr_t>(srcp) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+            const int4 *s4 = reinterpret_cast<const int4 *>(srcp);
+            int4 *d4 = reinterpret_cast<int4 *>(dst);
+            for (int64_t e = threadIdx.x; e < words / V; e += blockDim.x) d4[e] = __ldg(s4 + e);
+        } else {
+            for (int64_t e = threadIdx.x; e < words; e += blockDim.x) dst[e] = srcp[e];
+        }
         __syncthreads();
         // The point values on the right (i = n) and top (j = n) faces: where the
         // neighbour across was the owner in the old forest (same level, or
