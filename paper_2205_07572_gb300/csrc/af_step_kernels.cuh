@@ -140,7 +140,8 @@ __device__ __forceinline__ void stage_issue(const StepArgs<T> &A, const af_work 
 
 // For a patch that advances its ghost layer, write the staged entries of the
 // tile's share of the patch lattice to the output, so the output holds a
-// complete patch (advanced entries are overwritten afterwards).
+// complete patch: the entries the step does not write (the outer ghost ring
+// and the lines beyond the advanced ones).
 template <typename T, int NT, int WX, int WSZ, int NC = 0, int NN = 0>
 __device__ __forceinline__ void stage_copy_out(const StepArgs<T> &A, const af_work &wk, const T *Sin) {
     T *const out = dst_buf(A, wk.level);
@@ -152,13 +153,25 @@ __device__ __forceinline__ void stage_copy_out(const StepArgs<T> &A, const af_wo
     const int64_t pw = (int64_t)ncp * plane;
     const int cxlo = x0 == -1 ? -2 : x0, cxhi = x1 == n + 1 ? n + 3 : x1;
     const int cylo = y0 == -1 ? -2 : y0, cyhi = y1 == n + 1 ? n + 3 : y1;
+    // the node lines the step stores (as in tile_nodes)
+    const int sxhi = x1 == n + 1 ? x1 : x1 - 1, syhi = y1 == n + 1 ? y1 : y1 - 1;
     for (int pos = threadIdx.x; pos < ww * wh; pos += NT) {
         const int row = pos / ww, col = pos - row * ww;
         const int li = x0 - 1 + col, lj = y0 - 1 + row;
         if (li >= cxlo && li < cxhi && lj >= cylo && lj < cyhi) {
+            // planes whose entry here the step writes afterwards are skipped:
+            // averages of the tile's cells, corners on the stored node lines,
+            // left-edge midpoints on stored lines i beside the tile's rows,
+            // bottom-edge midpoints on stored lines j below its columns
+            const bool cx = li >= x0 && li < x1, cy = lj >= y0 && lj < y1;
+            const bool nx = li >= x0 && li <= sxhi, ny = lj >= y0 && lj <= syhi;
+            const unsigned written = (cx && cy ? 1u << kAvg : 0u) | (nx && cy ? 1u << kXmid : 0u) |
+                                     (nx && ny ? 1u << kCorner : 0u) | (cx && ny ? 1u << kYmid : 0u);
+            if (written == 0xFu) continue;
             T *o = out + (int64_t)patch * pw + (int64_t)(lj + kGhost) * W + (li + kGhost);
             const T *sp = Sin + row * WX + col;
-            for (int cp = 0; cp < ncp; ++cp) o[cp * plane] = sp[cp * WSZ];
+            for (int cp = 0; cp < ncp; ++cp)
+                if (!((written >> (cp % kPlanes)) & 1u)) o[cp * plane] = sp[cp * WSZ];
         }
     }
 }
