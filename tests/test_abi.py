@@ -57,6 +57,20 @@ def test_work_builder_tiles(af):
     assert len(w) // 64 == 9                 # [-1, 65) -> 3 x 3 tiles of 22
 
 
+def test_work_builder_more_tiles_than_its_first_capacity_guess(af):
+    """build_step_work guesses four work items per patch, then asks again
+    with the count the library reports: 64-cell patches in 32 x 8 tiles take
+    16 items each (27 when extended), all of them returned."""
+    k = af.step_tilings().index((32, 8, 128, 0))
+    cfg = af.config(af.ACOUSTICS, af.F32, 64)
+    nbr = np.zeros((5, 8), np.int32)
+    nbr[2, 0] = -1
+    w = af.build_step_work(cfg, np.arange(5), nbr=nbr, tiling=k)
+    items = np.frombuffer(w.tobytes(), dtype=np.int32).reshape(-1, 16)
+    assert len(items) == 4 * 16 + 27
+    assert np.array_equal(np.bincount(items[:, 0], minlength=5), [16, 16, 27, 16, 16])
+
+
 def test_host_side_errors(af):
     cfg = af.config(af.ACOUSTICS, af.F64, 16, c=1.0)
     buf_a, buf_b, work = 1 << 20, 2 << 20, 3 << 20  # fake, aligned, never dereferenced

@@ -51,6 +51,20 @@ def test_forest_map_and_neighbours(amr):
         assert all(F.level[sl] == l)
 
 
+def test_forest_from_arrays_in_any_order(amr):
+    """Forest(arrays=) stores the leaves sorted by (level, row, column)
+    whatever the input order, exactly as from the list of tuples."""
+    leaves = _sorted(S.balanced_forest(2, 1, 4, lambda l, x, y: (x + y) % 3 == 0))
+    F = amr.Forest(2, 4, leaves, device="cpu")
+    perm = np.random.default_rng(3).permutation(len(leaves))
+    arr = np.array(leaves, np.int32)[perm]
+    G = amr.Forest(2, 4, device="cpu", arrays=(arr[:, 0], arr[:, 1], arr[:, 2]))
+    assert G.leaves == F.leaves == leaves
+    assert np.array_equal(G.nbr, F.nbr) and np.array_equal(G.map, F.map)
+    assert G.same_leaves(arr[:, 0], arr[:, 1], arr[:, 2])
+    assert not G.same_leaves(arr[1:, 0], arr[1:, 1], arr[1:, 2])
+
+
 def test_forest_map_entries_by_direct_geometry(amr):
     """af_forest_build_map: at every level, a region that is a leaf holds its
     index, a region inside a coarser leaf q holds -2 - q, a region holding
