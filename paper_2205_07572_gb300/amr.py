@@ -429,6 +429,9 @@ class AMRRun:
         return t.cpu().numpy(), ind
 
     def regrid(self, tags, lmin: int) -> bool:
+        """Regrid from per-leaf tags (af_forest_regrid), move the state to the
+        new forest (af_transfer) and exchange its ghosts; False if the forest
+        is unchanged."""
         lv, x, y = regrid_arrays(self.forest, tags, lmin)
         if self.forest.same_leaves(lv, x, y):
             return False
