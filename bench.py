@@ -599,9 +599,10 @@ def amr_bench(case: str, coarse_steps: int, warmup: int, per_patch: bool = True)
     return out
 
 
-def amr_profile_run(steps: int, warmup: int, case: str = "acoustics_levels3-7"):
+def amr_profile_run(steps: int, warmup: int, case: str = "acoustics_levels3-7", tile=(16, 16, 128)):
     """Batched FP32 coarse steps (no graph capture, so every kernel is its own
-    launch) of one adaptive workload on its initial forest."""
+    launch) of one adaptive workload on its initial forest, with the compiled
+    tiling `tile` (cells x, cells y, threads)."""
     import torch
     from paper_2205_07572_gb300 import af
     from paper_2205_07572_gb300.amr import AMRRun
@@ -609,7 +610,7 @@ def amr_profile_run(steps: int, warmup: int, case: str = "acoustics_levels3-7"):
     leaves, st = amr_initial(case)
     cfg = af.config(c["eq"], af.F32, AMR_N, c["a"], c["b"], 1.0)
     dx0 = (c["hi"][0] - c["lo"][0]) / (c["B"] * AMR_N)
-    run = AMRRun(cfg, c["B"], c["lmax"], leaves, st, c["lo"], c["hi"], CFL * dx0, tiling=4)
+    run = AMRRun(cfg, c["B"], c["lmax"], leaves, st, c["lo"], c["hi"], CFL * dx0, tiling=_tiling_index(*tile))
     for _ in range(warmup):
         run.coarse_step()
     torch.cuda.synchronize()
@@ -1109,6 +1110,8 @@ def main():
     ap.add_argument("--var-only", action="store_true", help="only the variable-velocity advection runs")
     ap.add_argument("--amr-profile", action="store_true",
                     help="only batched FP32 coarse steps of the acoustics levels 3-7 forest (for a launch list)")
+    ap.add_argument("--amr-tile", type=int, nargs=3, default=[16, 16, 128], metavar=("TX", "TY", "THREADS"),
+                    help="compiled tiling of --amr-profile")
     ap.add_argument("--learned-only", action="store_true",
                     help="only the learned-tagging experiment")
     ap.add_argument("--amr-only", action="store_true",
@@ -1174,7 +1177,7 @@ def main():
         return
     if args.amr_profile:
         if rank == 0:
-            print(json.dumps(amr_profile_run(args.steps, warm)), flush=True)
+            print(json.dumps(amr_profile_run(args.steps, warm, tile=tuple(args.amr_tile))), flush=True)
         return
     if args.var_only:
         if rank == 0:
