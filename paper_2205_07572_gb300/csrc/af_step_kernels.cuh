@@ -482,6 +482,23 @@ __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, 
         }
         const int i = x0 + ii, j = y0 + jj;
         const int s00 = jj * TX + ii;
+        // flux registers of a patch-boundary cell: its x side (0 left, 1
+        // right) and y side (2 bottom, 3 top), read first so their latency
+        // overlaps the flux arithmetic (each entry belongs to one cell)
+        double *fr_p = nullptr;
+        int kx = -1, ky = -1;
+        double ox[3], oy[3];
+        if (A.freg != nullptr) {
+            fr_p = A.freg + (int64_t)patch * 4 * ncomp * n;
+            const bool iny = (j >= 0 && j < n), inx = (i >= 0 && i < n);
+            kx = (iny && i == 0) ? 0 : ((iny && i == n - 1) ? 1 : -1);
+            ky = (inx && j == 0) ? 2 : ((inx && j == n - 1) ? 3 : -1);
+#pragma unroll
+            for (int c = 0; c < ncomp; ++c) {
+                if (kx >= 0) ox[c] = fr_p[(kx * ncomp + c) * n + j];
+                if (ky >= 0) oy[c] = fr_p[(ky * ncomp + c) * n + i];
+            }
+        }
         T Fl[3], Fr[3], Gb[3], Gt[3];
 #pragma unroll
         for (int c = 0; c < ncomp; ++c) {
@@ -514,14 +531,10 @@ __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, 
             // dt_l = dt0 / 2^level, scaled exactly by the power of two (no FP64
             // library call outside this branch)
             const double dtl = A.dt0 * __longlong_as_double((long long)(1023 - level) << 52);
-            double *fr_p = A.freg + (int64_t)patch * 4 * ncomp * n;
-            const bool iny = (j >= 0 && j < n), inx = (i >= 0 && i < n);
 #pragma unroll
             for (int c = 0; c < ncomp; ++c) {
-                if (iny && i == 0) fr_p[(0 * ncomp + c) * n + j] += dtl * (double)fl[c];
-                if (iny && i == n - 1) fr_p[(1 * ncomp + c) * n + j] += dtl * (double)fr[c];
-                if (inx && j == 0) fr_p[(2 * ncomp + c) * n + i] += dtl * (double)gb[c];
-                if (inx && j == n - 1) fr_p[(3 * ncomp + c) * n + i] += dtl * (double)gt[c];
+                if (kx >= 0) fr_p[(kx * ncomp + c) * n + j] = ox[c] + dtl * (double)(kx == 0 ? fl[c] : fr[c]);
+                if (ky >= 0) fr_p[(ky * ncomp + c) * n + i] = oy[c] + dtl * (double)(ky == 2 ? gb[c] : gt[c]);
             }
         }
     }
