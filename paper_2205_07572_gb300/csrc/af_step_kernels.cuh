@@ -651,6 +651,16 @@ __device__ __forceinline__ void prefetch_work(const af_work *w, unsigned idx, un
     if (threadIdx.x == 0 && idx < nwork) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(w + idx));
 }
 
+// The patch's flux registers (4 sides x ncomp x n doubles), prefetched into
+// L2 while the tile is staged: the flux phase reads them back.
+template <typename T, int NT>
+__device__ __forceinline__ void prefetch_freg(const StepArgs<T> &A, int patch, int ncomp, int n) {
+    if (A.freg == nullptr) return;
+    const double *p = A.freg + (int64_t)patch * 4 * ncomp * n;
+    const int lines = (4 * ncomp * n * 8 + 127) / 128;
+    for (int t = threadIdx.x; t < lines; t += NT) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p + 16 * t));
+}
+
 // Offset (elements) of the window origin from the start of the shared
 // window buffer: room for the rounding of a bulk copy's start down to 16
 // bytes, plus the 16-byte phase of the window origin of a tile with y0 = 0.
@@ -909,6 +919,7 @@ __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel(const
     prefetch_work(A.work, blockIdx.x + kWorkPrefetch, gridDim.x);
     const af_work wk = load_work(A.work + blockIdx.x);
     if (wk.x1 - wk.x0 > TMX || wk.y1 - wk.y0 > TMY) return;  // built for another tiling
+    prefetch_freg<T, NT>(A, wk.patch, ncomp, NN > 0 ? NN : A.n);
     __shared__ __align__(8) uint64_t bar;
     bool staged = false;
     if (bulk_tile<T, Gm::WX>(A, wk)) {
