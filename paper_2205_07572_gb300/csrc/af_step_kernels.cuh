@@ -439,19 +439,19 @@ __device__ __forceinline__ void tile_nodes(const StepArgs<T> &A, const typename 
             {
                 const T qh = adv_eval<T, WX, WSZ>(W.w[0][0], Sin, qi + W.off[0][0][0], rj + W.off[0][0][1]);
                 const T q1 = adv_eval<T, WX, WSZ>(W.w[0][1], Sin, qi + W.off[0][1][0], rj + W.off[0][1][1]);
-                ST[0 * TSZ + so] = Sin[kCorner * WSZ + own] + T(4) * qh + q1;
+                ST[0 * TSZ + so] = fma(T(4), qh, Sin[kCorner * WSZ + own]) + q1;
                 if (st_x && st_y) ob[kCorner * plane] = q1;
             }
             if (hx) {
                 const T qh = adv_eval<T, WX, WSZ>(W.w[1][0], Sin, qi + W.off[1][0][0], rj + W.off[1][0][1]);
                 const T q1 = adv_eval<T, WX, WSZ>(W.w[1][1], Sin, qi + W.off[1][1][0], rj + W.off[1][1][1]);
-                ST[1 * TSZ + so] = Sin[kXmid * WSZ + own] + T(4) * qh + q1;
+                ST[1 * TSZ + so] = fma(T(4), qh, Sin[kXmid * WSZ + own]) + q1;
                 if (st_x) ob[kXmid * plane] = q1;
             }
             if (hy) {
                 const T qh = adv_eval<T, WX, WSZ>(W.w[2][0], Sin, qi + W.off[2][0][0], rj + W.off[2][0][1]);
                 const T q1 = adv_eval<T, WX, WSZ>(W.w[2][1], Sin, qi + W.off[2][1][0], rj + W.off[2][1][1]);
-                ST[2 * TSZ + so] = Sin[kYmid * WSZ + own] + T(4) * qh + q1;
+                ST[2 * TSZ + so] = fma(T(4), qh, Sin[kYmid * WSZ + own]) + q1;
                 if (st_y) ob[kYmid * plane] = q1;
             }
         }
@@ -460,7 +460,9 @@ __device__ __forceinline__ void tile_nodes(const StepArgs<T> &A, const typename 
 
 // Fluxes (Eq. Simpson-2d) and the update (Eq. 2dfv) of one tile whose T
 // arrays tile_nodes has written; reads the cell averages from the window.
-template <typename T, int EQ, int NT, int WX, int WSZ, int TX, int TSZ, int TMX = TX - 1, int NN = 0>
+// FREG: A.freg is set (adaptive runs); the flux registers of patch-boundary
+// cells are accumulated.
+template <typename T, int EQ, int NT, int WX, int WSZ, int TX, int TSZ, int TMX, int NN, bool FREG>
 __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, const T *ST, int patch, int level,
                                             int x0, int x1, int y0, int y1) {
     constexpr int ncomp = (EQ == AF_ACOUSTICS) ? 3 : 1;
@@ -488,7 +490,7 @@ __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, 
         double *fr_p = nullptr;
         int kx = -1, ky = -1;
         double ox[3], oy[3];
-        if (A.freg != nullptr) {
+        if (FREG) {
             fr_p = A.freg + (int64_t)patch * 4 * ncomp * n;
             const bool iny = (j >= 0 && j < n), inx = (i >= 0 && i < n);
             kx = (iny && i == 0) ? 0 : ((iny && i == n - 1) ? 1 : -1);
@@ -503,11 +505,12 @@ __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, 
 #pragma unroll
         for (int c = 0; c < ncomp; ++c) {
             const T *Tc = ST + (c * 3 + 0) * TSZ, *Tx = ST + (c * 3 + 1) * TSZ, *Ty = ST + (c * 3 + 2) * TSZ;
-            // time-Simpson sums at the three points of each face
-            Fl[c] = Tc[s00] + T(4) * Tx[s00] + Tc[s00 + TX];
-            Fr[c] = Tc[s00 + 1] + T(4) * Tx[s00 + 1] + Tc[s00 + TX + 1];
-            Gb[c] = Tc[s00] + T(4) * Ty[s00] + Tc[s00 + 1];
-            Gt[c] = Tc[s00 + TX] + T(4) * Ty[s00 + TX] + Tc[s00 + TX + 1];
+            // time-Simpson sums at the three points of each face (the
+            // multiply-adds written out, as in the update below)
+            Fl[c] = fma(T(4), Tx[s00], Tc[s00]) + Tc[s00 + TX];
+            Fr[c] = fma(T(4), Tx[s00 + 1], Tc[s00 + 1]) + Tc[s00 + TX + 1];
+            Gb[c] = fma(T(4), Ty[s00], Tc[s00]) + Tc[s00 + 1];
+            Gt[c] = fma(T(4), Ty[s00 + TX], Tc[s00 + TX]) + Tc[s00 + TX + 1];
         }
         T fl[3], fr[3], gb[3], gt[3];
         if constexpr (EQ == AF_ACOUSTICS) {
@@ -524,10 +527,12 @@ __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, 
         const int sa = (jj + 1) * WX + (ii + 1);
 #pragma unroll
         for (int c = 0; c < ncomp; ++c) {
+            // Q - dt/dx (F_r - F_l) - dt/dy (G_t - G_b), the multiply-adds
+            // written out so every instantiation rounds alike
             const T q = Sin[(c * kPlanes + kAvg) * WSZ + sa];
-            ob[c * kPlanes * plane] = q - A.dtdx * (fr[c] - fl[c]) - A.dtdy * (gt[c] - gb[c]);
+            ob[c * kPlanes * plane] = fma(-A.dtdy, gt[c] - gb[c], fma(-A.dtdx, fr[c] - fl[c], q));
         }
-        if (A.freg != nullptr) {
+        if (FREG) {
             // dt_l = dt0 / 2^level, scaled exactly by the power of two (no FP64
             // library call outside this branch)
             const double dtl = A.dt0 * __longlong_as_double((long long)(1023 - level) << 52);
@@ -547,7 +552,12 @@ __device__ __forceinline__ void tile_compute(const StepArgs<T> &A, const typenam
                                              int y1) {
     tile_nodes<T, EQ, NT, WX, WSZ, TX, TSZ, TMX, NN>(A, W, Sin, ST, patch, level, x0, x1, y0, y1);
     __syncthreads();
-    tile_fluxes<T, EQ, NT, WX, WSZ, TX, TSZ, TMX, NN>(A, Sin, ST, patch, level, x0, x1, y0, y1);
+    // flux registers (adaptive runs) or none: two instantiations, so the
+    // uniform grid's loop carries nothing of them
+    if (A.freg != nullptr)
+        tile_fluxes<T, EQ, NT, WX, WSZ, TX, TSZ, TMX, NN, true>(A, Sin, ST, patch, level, x0, x1, y0, y1);
+    else
+        tile_fluxes<T, EQ, NT, WX, WSZ, TX, TSZ, TMX, NN, false>(A, Sin, ST, patch, level, x0, x1, y0, y1);
 }
 
 // Resident CTAs per SM the register allocation must allow: FP32 acoustics
@@ -1038,8 +1048,12 @@ __global__ void __launch_bounds__(NT, (min_ctas<T, EQ, NT>())) step_kernel_pipe(
             cp_async_commit();
         }
         if (fits) {
-            tile_fluxes<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ, TMX, NN>(A, Sc, ST, wk.patch, wk.level, wk.x0,
-                                                                             wk.x1, wk.y0, wk.y1);
+            if (A.freg != nullptr)
+                tile_fluxes<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ, TMX, NN, true>(A, Sc, ST, wk.patch, wk.level,
+                                                                                       wk.x0, wk.x1, wk.y0, wk.y1);
+            else
+                tile_fluxes<T, EQ, NT, Gm::WX, Gm::WSZ, Gm::TX, Gm::TSZ, TMX, NN, false>(A, Sc, ST, wk.patch, wk.level,
+                                                                                        wk.x0, wk.x1, wk.y0, wk.y1);
             if (bulk_tile<T, Gm::WX>(A, wk)) write_ghost_columns<T, NT, Gm::WX, Gm::WSZ, ncomp>(A, wk, Sc);
         }
         cp_async_wait_all();
