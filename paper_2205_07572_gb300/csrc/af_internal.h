@@ -113,11 +113,7 @@ struct Tiling {
 constexpr int kNumTilings = 10;
 AF_HD constexpr Tiling tiling(int k) {
     constexpr Tiling t[kNumTilings] = {
-#ifdef AF_X_T2NT
-        {32, 32, 256, 0}, {32, 16, 192, 0}, {32, AF_X_T2TY, AF_X_T2NT, 0}, {32, 8, 128, 0}, {16, 16, 128, 0},
-#else
         {32, 32, 256, 0}, {32, 16, 192, 0}, {32, 16, 160, 0}, {32, 8, 128, 0}, {16, 16, 128, 0},
-#endif
         {32, 8, 256, 1}, {18, 18, 256, 0}, {18, 10, 192, 0}, {10, 10, 128, 0}, {18, 18, 128, 0}};
     return t[k];
 }
