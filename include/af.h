@@ -118,9 +118,11 @@ af_status af_build_step_work(const af_config *cfg, int32_t npatch, const int32_t
 /* Compiled tile shapes of af_patch_step.  A tiling splits every patch (or
  * its interior plus first ghost layer) into near-equal tiles of at most
  * tile_x x tile_y cells, each advanced by one CTA of `threads` threads;
- * persistent = CTAs loop over tiles with the next tile's copies in flight.
- * Which is fastest depends on the patch size, equation and precision; the
- * autotuner (paper_2205_07572_gb300/tune.py) times them. */
+ * persistent = CTAs loop over tiles with the next tile's copies in flight;
+ * af_patch_step* refuse persistent tilings (AF_ERR_UNIMPLEMENTED: the kernel
+ * is withdrawn), af_patch_step_var runs them as one tile per CTA.  Which is
+ * fastest depends on the patch size, equation and precision; the autotuner
+ * (paper_2205_07572_gb300/tune.py) times them. */
 typedef struct {
     int32_t tile_x, tile_y;
     int32_t threads;

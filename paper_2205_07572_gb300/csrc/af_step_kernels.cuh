@@ -966,7 +966,8 @@ __device__ __forceinline__ int stage_kind(const StepArgs<T> &A, const af_work &w
     return bulk_tile<T, WX>(A, w) ? 2 : 1;
 }
 
-// Persistent variant: one CTA loops over work items t, t + gridDim.x, ...
+// Persistent variant (not launched: launch_tiling refuses persistent
+// tilings): one CTA loops over work items t, t + gridDim.x, ...
 // with two windows, so staging overlaps compute.  The copies of the next
 // tile are issued before the node phase of the current one: its bulk copies
 // (thread 0), or its element-wise copies.  A bulk-staged next tile's halo
@@ -1085,16 +1086,13 @@ af_status launch_tiling(const StepArgs<T> &A, const typename WeightsOf<T, EQ>::t
     const size_t win = sizeof(T) * (size_t)ncomp * kPlanes * Gm::WSZ;
     const size_t tarr = sizeof(T) * (size_t)ncomp * 3 * Gm::TSZ;
     if constexpr (PIPE) {
-        const size_t smem = 2 * win + tarr;
-        if (smem > 227 * 1024) return AF_ERR_UNIMPLEMENTED;
-        auto kern = dev::step_kernel_pipe<T, EQ, NT, TMX, TMY, NN>;
-        if (ensure_smem(kern, smem) != cudaSuccess) return AF_ERR_CUDA;
-        int dev_id = 0, sms = 0, per_sm = 0;
-        if (cudaGetDevice(&dev_id) != cudaSuccess) return AF_ERR_CUDA;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess) return AF_ERR_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) return AF_ERR_CUDA;
-        const int slots = sms * (per_sm > 0 ? per_sm : 1);
-        kern<<<nwork < slots ? nwork : slots, NT, smem, stream>>>(A, W, nwork);
+        // The persistent (two-window) kernel is not launched: in two
+        // experimental builds a launch of it on 48 x 48 patches ended in an
+        // unspecified launch failure, and reading its schedule has not found
+        // the cause.  Until it is found, persistent tilings are refused.
+        (void)win;
+        (void)tarr;
+        return AF_ERR_UNIMPLEMENTED;
     } else {
         const size_t smem = win + tarr;
         if (smem > 227 * 1024) return AF_ERR_UNIMPLEMENTED;

@@ -7,9 +7,9 @@ are memoised per (equation, precision, patch size, patches, neighbour mode)
 for the life of the process.
 
 The default search space leaves out the persistent (two-window pipelined)
-tiling: it is slower on every measured workload, and a variant of it once
-failed on the GPU with a cause that reading the code has not found, so it
-runs only where a caller asks for it by index.
+tiling: the library refuses it (two launches of it failed on the GPU, in
+experimental builds, with a cause that reading the code has not found), and
+it was slower on every workload measured before that.
 """
 from __future__ import annotations
 

@@ -93,6 +93,11 @@ def test_host_side_errors(af):
         af.patch_step(adv, work, 1, buf_a, buf_b, 1.1 * dx, dx, dx, stream=0)
     assert e.value.status == 2               # Eq. cfl-adv
     af.patch_step(adv, work, 0, buf_a, buf_b, 0.5 * dx, dx, dx, stream=0)  # nothing to do: OK
+    # the persistent (two-window) tiling is withdrawn: refused before any launch
+    kp = [i for i, t in enumerate(af.step_tilings()) if t[3] == 1][0]
+    with pytest.raises(af.AFError) as e:
+        af.patch_step(adv, work, 1, buf_a, buf_b, 0.5 * dx, dx, dx, stream=0, tiling=kp)
+    assert e.value.status == 6               # AF_ERR_UNIMPLEMENTED
 
 
 def test_work_items_carry_patch_positions(af):

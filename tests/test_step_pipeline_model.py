@@ -19,8 +19,10 @@ tiles, 9216 work items over the resident CTAs) and for the bench launch:
   * a window is refilled only after the iteration that read it has ended
     (its barrier, after the proxy fence), never while it is being read.
 The ghost-row-skip variant, as described, is checked the same way.  All of
-it holds, so none of these explains the failure; the persistent kernel is
-left out of the autotuner's default search space."""
+it holds, so none of these explains the failure.  A second launch of the
+same shape failed the same way later, in another experimental build; the
+persistent tilings are now refused by the library (AF_ERR_UNIMPLEMENTED) and
+the kernel is not launched until the cause is found."""
 import numpy as np
 import pytest
 
