@@ -211,7 +211,7 @@ __device__ __forceinline__ void dot(T &acc, const T *w, const T *v) {
 // v += A.SS_v + Dy.SA_p (the evolution operators of Eq. ERFormula).
 // out: T and Q^{n+1} of corner (tc, nc), left-edge mid (tx, nx) and
 // bottom-edge mid (ty, ny) for p, u, v.
-template <typename T, int WX, int WSZ>
+template <typename T, int WX, int WSZ, bool PK = true>
 __device__ __forceinline__ void acoustic_item(const AcousticSymWeights<T> &W, const T *Sin, int qi, int rj,
                                               T tc[3], T nc[3], T tx[3], T nx[3], T ty[3], T ny[3]) {
 #pragma unroll
@@ -285,9 +285,27 @@ __device__ __forceinline__ void dot2(float2 &acc, const float (*w)[2], const flo
     for (int k = 0; k < N; ++k) acc = __ffma2_rn(make_float2(w[k][0], w[k][1]), make_float2(v[k], v[k]), acc);
 }
 
+// quad() in FP32 with its two partial sums as one packed add: the lanes
+// (pp, mp) and (pm, mm) give a = pp + pm and b = mp + mm together, and
+// (pp, mp) - (pm, mm) (a multiply-add by -1, exact before its one rounding)
+// gives pp - pm and mp - mm together.  Every result is rounded as in quad().
+__device__ __forceinline__ void quad2(float pp, float pm, float mp, float mm, float &ss, float &as, float &sa) {
+    const float2 s = __fadd2_rn(make_float2(pp, mp), make_float2(pm, mm));
+    ss = s.x + s.y;
+    as = s.x - s.y;
+    const float2 d = __ffma2_rn(make_float2(pm, mm), make_float2(-1.f, -1.f), make_float2(pp, mp));
+    sa = d.x + d.y;
+}
+
 // FP32 acoustic node evaluation: as acoustic_item, with the T and Q^{n+1}
-// accumulators of every node value packed in one float2.
-template <typename T, int WX, int WSZ>
+// accumulators of every node value packed in one float2.  The corner node's
+// four quads take quad2, with the lane pairs (b3, b2), (b1, b0), (b12, b10),
+// (b6, b4), (b18, b16), (b15, b13), (b24, b23), (b20, b19).  The edge
+// midpoints' quads stay scalar: with them too the kernel no longer fits its
+// register budget (measured slower), and the bottom-edge quads would pair b12,
+// b6, b18 and b15 with other partners.  PK = false keeps all quads scalar
+// (whole-patch tiles, which spill with the pairs).
+template <typename T, int WX, int WSZ, bool PK = true>
 __device__ __forceinline__ void acoustic_item(const AcousticPairWeights &W, const float *Sin, int qi, int rj,
                                               float tc[3], float nc[3], float tx[3], float nx[3], float ty[3],
                                               float ny[3]) {
@@ -301,10 +319,17 @@ __device__ __forceinline__ void acoustic_item(const AcousticPairWeights &W, cons
 #pragma unroll
         for (int k = 0; k < 25; ++k) b[k] = base[(ci * kPlanes + blk_plane(k)) * WSZ + blk_b(k) * WX + blk_a(k)];
         float css[9], cas[6], csa[6];
-        quad(b[3], b[1], b[2], b[0], css[0], cas[0], csa[0]);
-        quad(b[12], b[6], b[10], b[4], css[1], cas[1], csa[1]);
-        quad(b[18], b[15], b[16], b[13], css[2], cas[2], csa[2]);
-        quad(b[24], b[20], b[23], b[19], css[3], cas[3], csa[3]);
+        if constexpr (PK) {
+            quad2(b[3], b[1], b[2], b[0], css[0], cas[0], csa[0]);
+            quad2(b[12], b[6], b[10], b[4], css[1], cas[1], csa[1]);
+            quad2(b[18], b[15], b[16], b[13], css[2], cas[2], csa[2]);
+            quad2(b[24], b[20], b[23], b[19], css[3], cas[3], csa[3]);
+        } else {
+            quad(b[3], b[1], b[2], b[0], css[0], cas[0], csa[0]);
+            quad(b[12], b[6], b[10], b[4], css[1], cas[1], csa[1]);
+            quad(b[18], b[15], b[16], b[13], css[2], cas[2], csa[2]);
+            quad(b[24], b[20], b[23], b[19], css[3], cas[3], csa[3]);
+        }
         css[4] = b[9] + b[7];   cas[4] = b[9] - b[7];
         css[5] = b[22] + b[21]; cas[5] = b[22] - b[21];
         css[6] = b[11] + b[5];  csa[4] = b[11] - b[5];
@@ -423,7 +448,7 @@ __device__ __forceinline__ void tile_nodes(const StepArgs<T> &A, const typename 
         const int so = jj * TX + ii;
         if constexpr (EQ == AF_ACOUSTICS) {
             T tc[3], nc[3], tx[3], nx[3], ty[3], ny[3];
-            acoustic_item<T, WX, WSZ>(W, Sin, qi, rj, tc, nc, tx, nx, ty, ny);
+            acoustic_item<T, WX, WSZ, TMX != NN + 2>(W, Sin, qi, rj, tc, nc, tx, nx, ty, ny);
 #pragma unroll
             for (int o = 0; o < 3; ++o) {
                 ST[(o * 3 + 0) * TSZ + so] = tc[o];
