@@ -860,14 +860,14 @@ def learned_tagging(B=3, lmin=3, lmax=7, train_radii=(0.2, 0.3), test_radius=0.2
     tg = taggers[intervals[len(intervals) // 2]]
     run = AMRRun(cfg, B, lmax, leaves, st, lo, hi, dt0)
     x = run.cnn_inputs(4.0)
-    fwd = tg.outputs(run.forest.nleaf)
+    fwd = tg.outputs(run.forest.nleaf)[:2]
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tg.forward(x, run.forest.d_level, fwd)
+    tg.infer(x, run.forest.d_level, fwd)
     e0.record(stream)
     for _ in range(10):
         run.cnn_inputs(4.0)
-        tg.forward(x, run.forest.d_level, fwd)
+        tg.infer(x, run.forest.d_level, fwd)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 10
@@ -875,11 +875,11 @@ def learned_tagging(B=3, lmin=3, lmax=7, train_radii=(0.2, 0.3), test_radius=0.2
     reps = max(1, 65536 // run.forest.nleaf)
     xb = x.repeat(reps, 1, 1, 1).contiguous()
     lb = run.forest.d_level.repeat(reps).contiguous()
-    fb = tg.outputs(int(lb.numel()))
-    tg.forward(xb, lb, fb)
+    fb = tg.outputs(int(lb.numel()))[:2]
+    tg.infer(xb, lb, fb)
     e0.record(stream)
     for _ in range(10):
-        tg.forward(xb, lb, fb)
+        tg.infer(xb, lb, fb)
     e1.record(stream)
     torch.cuda.synchronize()
     msb = e0.elapsed_time(e1) / 10
@@ -897,9 +897,10 @@ def learned_tagging(B=3, lmin=3, lmax=7, train_radii=(0.2, 0.3), test_radius=0.2
 def tagger_kernels(nsample: int = 65536, steps: int = 20, warmup: int = 3, C: int = 3, N: int = 16,
                    batch: int = 4096):
     """The tagger's kernels alone on synthetic BF16 inputs (normal, seed 0):
-    af_cnn_forward on nsample patches, and a training step (forward,
-    backward, Adam) on `batch`; TFLOP/s of the two convolutions (forward)
-    against the measured BF16 tensor peak."""
+    af_cnn_forward on nsample patches, with the maxima's positions (the
+    training forward) and without (inference), and a training step (forward,
+    backward, Adam) on `batch`; TFLOP/s of the two convolutions against the
+    measured BF16 tensor peak."""
     import torch
     from paper_2205_07572_gb300.tagger import Tagger
     g = torch.Generator(device="cpu").manual_seed(0)
@@ -918,6 +919,15 @@ def tagger_kernels(nsample: int = 65536, steps: int = 20, warmup: int = 3, C: in
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    inf_out = out[:2]
+    for _ in range(warmup):
+        tg.infer(x, level, inf_out)
+    e0.record(stream)
+    for _ in range(steps):
+        tg.infer(x, level, inf_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_i = e0.elapsed_time(e1) / steps
     flop = 2 * 32 * ((N + 2) ** 2 * C * 9 + N * N * 32 * 9)
     peak = bf16_peak()
     label = (torch.rand(batch, generator=g) > 0.5).float().cuda()
@@ -933,9 +943,12 @@ def tagger_kernels(nsample: int = 65536, steps: int = 20, warmup: int = 3, C: in
     torch.cuda.synchronize()
     ms_t = e0.elapsed_time(e1) / steps
     tf = nsample * flop / (ms * 1e-3) / 1e12
+    tf_i = nsample * flop / (ms_i * 1e-3) / 1e12
     return {"shape": {"ncomp": C, "n": N, "channels": 32}, "forward": {
                 "samples": nsample, "ms": ms, "samples_per_s": nsample / (ms * 1e-3), "flop_per_sample": flop,
                 "tflops": tf, "peak_tflops": peak[0], "peak_source": peak[1], "frac": tf / peak[0]},
+            "inference": {"samples": nsample, "ms": ms_i, "samples_per_s": nsample / (ms_i * 1e-3),
+                          "tflops": tf_i, "frac": tf_i / peak[0]},
             "train_step": {"batch": batch, "ms": ms_t, "samples_per_s": batch / (ms_t * 1e-3)}}
 
 

@@ -547,7 +547,9 @@ af_status af_cnn_inputs(const af_config *cfg, const af_forest *forest, const af_
 
 /* Forward pass: logits, the pooled maxima M [nsample][F] and their first
  * row-major positions d_arg [nsample][F] (-1 where M = 0), which the
- * backward pass reuses.  d_level[k] in 0..15. */
+ * backward pass reuses.  d_level[k] in 0..15.  d_arg may be NULL
+ * (inference): the positions are then not computed, and the logits and M
+ * are the same bit for bit. */
 af_status af_cnn_forward(int32_t ncomp, int32_t n, int32_t nsample, const uint16_t *d_x, const int32_t *d_level,
                          const float *d_params, float *d_logit, float *d_m, int32_t *d_arg, void *stream);
 

@@ -468,7 +468,7 @@ class AMRRun:
         af.tag_pair(self.cfg, self.forest.c, self.pair, comp, kind, self.dx0, self.dy0, refine_thr, coarsen_thr,
                     plain, None)
         x = self.cnn_inputs(refine_thr)
-        logit, _, _ = tagger.forward(x, self.forest.d_level)
+        logit, _ = tagger.infer(x, self.forest.d_level)
         tags = torch.zeros(nl, dtype=torch.int8, device=self.device)
         nf = torch.zeros(1, dtype=torch.int32, device=self.device)
         af.cnn_tags(nl, logit, plain, cmin, tags, nf)

@@ -292,8 +292,12 @@ __device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const uint
     return true;
 }
 
-// Forward pass: one CTA (one warpgroup) per patch at a time.
-template <int C, int N>
+// Forward pass: one CTA (one warpgroup) per patch at a time.  POS: also the
+// first row-major position of every channel's maximum (training: the
+// backward pass needs it); without it (inference) a channel's maximum is
+// max_q D2[q][g] + b2[g], which equals max_q (D2[q][g] + b2[g]) bit for bit
+// because rounding an addition of the same b2 is monotonic.
+template <int C, int N, bool POS>
 __global__ void __launch_bounds__(128) cnn_forward_kernel(int nsample, const __nv_bfloat16 *__restrict__ X,
                                                           const int32_t *__restrict__ level,
                                                           const float *__restrict__ P, float *__restrict__ logit,
@@ -372,18 +376,25 @@ __global__ void __launch_bounds__(128) cnn_forward_kernel(int nsample, const __n
             tc::tmem_ld32(tmem + lanes + 32 * mt, z);
             const int q = mt * 128 + 32 * warp + lane, y = q / G::S1, x = q - y * G::S1;
             if (y < N && x < N) {
-                // a thread visits its positions in increasing order, so a
-                // strict comparison keeps the first maximum; a channel whose
-                // maximum is not positive reports no position (-1) below,
-                // whatever a thread kept for -inf or NaN values
-                const int p = y * N + x;
+                if constexpr (POS) {
+                    // a thread visits its positions in increasing order, so a
+                    // strict comparison keeps the first maximum; a channel whose
+                    // maximum is not positive reports no position (-1) below,
+                    // whatever a thread kept for -inf or NaN values
+                    const int p = y * N + x;
 #pragma unroll
-                for (int g = 0; g < kF; ++g) {
-                    const float v = z[g] + s_b2[g];
-                    if (v > best[g]) {
-                        best[g] = v;
-                        bi[g] = p;
+                    for (int g = 0; g < kF; ++g) {
+                        const float v = z[g] + s_b2[g];
+                        if (v > best[g]) {
+                            best[g] = v;
+                            bi[g] = p;
+                        }
                     }
+                } else {
+                    // b2 is added after the reduction (NaN accumulators are
+                    // skipped by fmaxf as by the comparison above)
+#pragma unroll
+                    for (int g = 0; g < kF; ++g) best[g] = fmaxf(best[g], z[g]);
                 }
             }
         }
@@ -396,39 +407,50 @@ __global__ void __launch_bounds__(128) cnn_forward_kernel(int nsample, const __n
 #pragma unroll
             for (int j = 0; j < w; ++j) {
                 const float sv = upper ? best[j] : best[j + w];
-                const int si = upper ? bi[j] : bi[j + w];
                 const float kv = upper ? best[j + w] : best[j];
-                const int ki = upper ? bi[j + w] : bi[j];
                 const float ov = __shfl_xor_sync(0xffffffffu, sv, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, si, o);
-                const bool take = ov > kv || (ov == kv && oi < ki);
-                best[j] = take ? ov : kv;
-                bi[j] = take ? oi : ki;
+                if constexpr (POS) {
+                    const int si = upper ? bi[j] : bi[j + w];
+                    const int ki = upper ? bi[j + w] : bi[j];
+                    const int oi = __shfl_xor_sync(0xffffffffu, si, o);
+                    const bool take = ov > kv || (ov == kv && oi < ki);
+                    best[j] = take ? ov : kv;
+                    bi[j] = take ? oi : ki;
+                } else {
+                    best[j] = fmaxf(ov, kv);
+                }
             }
         }
         s_best[warp][lane] = best[0];
-        s_idx[warp][lane] = bi[0];
+        if constexpr (POS) s_idx[warp][lane] = bi[0];
         tc::fence_before_sync();
         __syncthreads();
         if (warp == 0) {
             const int g = lane;
             float bv = s_best[0][g];
-            int ix = s_idx[0][g];
+            int ix = 0;
+            if constexpr (POS) {
+                ix = s_idx[0][g];
 #pragma unroll
-            for (int w = 1; w < 4; ++w) {
-                const float ob = s_best[w][g];
-                const int oi = s_idx[w][g];
-                if (ob > bv || (ob == bv && oi < ix)) {
-                    bv = ob;
-                    ix = oi;
+                for (int w = 1; w < 4; ++w) {
+                    const float ob = s_best[w][g];
+                    const int oi = s_idx[w][g];
+                    if (ob > bv || (ob == bv && oi < ix)) {
+                        bv = ob;
+                        ix = oi;
+                    }
                 }
+            } else {
+#pragma unroll
+                for (int w = 1; w < 4; ++w) bv = fmaxf(bv, s_best[w][g]);
+                bv += s_b2[g];
             }
             const float mg = bv > 0.f ? bv : 0.f;
             float v = s_w3[g] * mg;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             Mout[(int64_t)b * kF + g] = mg;
-            Aout[(int64_t)b * kF + g] = bv > 0.f ? ix : -1;
+            if constexpr (POS) Aout[(int64_t)b * kF + g] = bv > 0.f ? ix : -1;
             if (g == 0) logit[b] = v + s_b3;
         }
         __syncthreads();
@@ -664,10 +686,10 @@ af_status smem_attr(K k, size_t bytes) {
 
 inline af_status launched() { return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ERR_CUDA; }
 
-template <int C, int N>
+template <int C, int N, bool POS>
 af_status forward_launch(int nsample, const void *X, const int32_t *lev, const float *P, float *lg, float *M,
                          int32_t *A, cudaStream_t s) {
-    auto k = cnn_forward_kernel<C, N>;
+    auto k = cnn_forward_kernel<C, N, POS>;
     const size_t bytes = TcGeo<C, N>::end;
     if (const af_status e = smem_attr(k, bytes)) return e;
     int dev = 0, sms = 0;
@@ -765,13 +787,20 @@ extern "C" af_status af_cnn_forward(int32_t ncomp, int32_t n, int32_t nsample, c
                                     int32_t *d_arg, void *stream) {
     if (!cnn_shape_ok(ncomp, n) || nsample < 0) return AF_ERR_ARG;
     if (nsample == 0) return AF_OK;
-    if (!d_x || !d_level || !d_params || !d_logit || !d_m || !d_arg) return AF_ERR_ARG;
+    if (!d_x || !d_level || !d_params || !d_logit || !d_m) return AF_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (d_arg != nullptr) {  // training: the positions too
+        if (ncomp == 3)
+            return n == 16 ? forward_launch<3, 16, true>(nsample, d_x, d_level, d_params, d_logit, d_m, d_arg, s)
+                           : forward_launch<3, 8, true>(nsample, d_x, d_level, d_params, d_logit, d_m, d_arg, s);
+        return n == 16 ? forward_launch<1, 16, true>(nsample, d_x, d_level, d_params, d_logit, d_m, d_arg, s)
+                       : forward_launch<1, 8, true>(nsample, d_x, d_level, d_params, d_logit, d_m, d_arg, s);
+    }
     if (ncomp == 3)
-        return n == 16 ? forward_launch<3, 16>(nsample, d_x, d_level, d_params, d_logit, d_m, d_arg, s)
-                       : forward_launch<3, 8>(nsample, d_x, d_level, d_params, d_logit, d_m, d_arg, s);
-    return n == 16 ? forward_launch<1, 16>(nsample, d_x, d_level, d_params, d_logit, d_m, d_arg, s)
-                   : forward_launch<1, 8>(nsample, d_x, d_level, d_params, d_logit, d_m, d_arg, s);
+        return n == 16 ? forward_launch<3, 16, false>(nsample, d_x, d_level, d_params, d_logit, d_m, nullptr, s)
+                       : forward_launch<3, 8, false>(nsample, d_x, d_level, d_params, d_logit, d_m, nullptr, s);
+    return n == 16 ? forward_launch<1, 16, false>(nsample, d_x, d_level, d_params, d_logit, d_m, nullptr, s)
+                   : forward_launch<1, 8, false>(nsample, d_x, d_level, d_params, d_logit, d_m, nullptr, s);
 }
 
 extern "C" int64_t af_cnn_partial_floats(int32_t ncomp, int32_t nblocks) {

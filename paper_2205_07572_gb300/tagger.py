@@ -65,6 +65,14 @@ class Tagger:
         af.cnn_forward(self.ncomp, self.n, nsample, x, level, self.params, logit, m, arg, stream)
         return logit, m, arg
 
+    def infer(self, x, level, out=None, stream=None):
+        """Inference: logits and pooled maxima without the maxima's positions
+        (af_cnn_forward with d_arg NULL; the same logits bit for bit)."""
+        nsample = int(level.numel())
+        logit, m = out if out is not None else self.outputs(nsample)[:2]
+        af.cnn_forward(self.ncomp, self.n, nsample, x, level, self.params, logit, m, None, stream)
+        return logit, m
+
     def gradient(self, x, level, label, weight, weight_sum: float, fwd, stream=None):
         logit, m, arg = fwd
         af.cnn_backward(self.ncomp, self.n, int(level.numel()), x, level, self.params, logit, m, arg, label, weight,

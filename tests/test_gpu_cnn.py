@@ -49,6 +49,29 @@ def _problem(C, N, P, seed):
 
 
 @pytest.mark.parametrize("C,N", [(3, 16), (1, 8), (3, 8), (1, 16)])
+def test_inference_forward_equals_training_forward_bitwise(af, C, N):
+    """af_cnn_forward without the positions (d_arg NULL, inference: b2 added
+    after the max-pool) gives the logits and pooled maxima of the forward
+    with them bit for bit, on inputs with ties, zero and negative maxima, on
+    more patches than resident CTAs (several patches per CTA)."""
+    from paper_2205_07572_gb300.tagger import Tagger
+    P = 2500
+    X, level, params, _, _ = _problem(C, N, P, seed=7 * C + N)
+    X[: P // 4] = OC.bf16(np.round(X[: P // 4]))          # many equal values: ties in the max-pool
+    X[P // 4: P // 2] = 0.0                               # constant patches: maxima b2 only
+    t = Tagger(C, N)
+    t.params.copy_(torch.from_numpy(params.astype(np.float32)))
+    x, lv = _bf16_bits(X), torch.from_numpy(level).cuda()
+    lg, M, arg = t.forward(x, lv)
+    lg_i, M_i = t.infer(x, lv)
+    torch.cuda.synchronize()
+    assert torch.isfinite(lg).all()
+    assert torch.equal(lg.view(torch.int32), lg_i.view(torch.int32))
+    assert torch.equal(M.view(torch.int32), M_i.view(torch.int32))
+    assert (M == 0).any() and (M > 0).any()
+
+
+@pytest.mark.parametrize("C,N", [(3, 16), (1, 8), (3, 8), (1, 16)])
 def test_forward_matches_oracle(af, C, N):
     X, level, params, _, _ = _problem(C, N, 64, seed=C * 10 + N)
     lg_r, M_r, arg_r, _ = OC.forward(X, level, params, C)
