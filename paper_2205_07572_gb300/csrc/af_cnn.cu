@@ -270,15 +270,18 @@ __device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const uint
 #pragma unroll
                 for (int g = 0; g < kF; ++g) a1[g * G::P1 + m] = rbf(fmaxf(z[g] + emb[g], 0.f));
             } else {
-                // the map A1m[kc][m][8 channels], row m = the layer-1 pixel
+                // the map A1m[kc][m][8 channels], row m = the layer-1 pixel;
+                // channel pairs added as packed FP32x2 and converted to a
+                // BF16 pair in one instruction (each value rounded as alone)
 #pragma unroll
                 for (int kc = 0; kc < 4; ++kc) {
                     uint32_t w[4];
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
                         const int g = kc * 8 + 2 * h;
-                        w[h] = (uint32_t)bf16_bits(fmaxf(z[g] + emb[g], 0.f)) |
-                               ((uint32_t)bf16_bits(fmaxf(z[g + 1] + emb[g + 1], 0.f)) << 16);
+                        const float2 a = __fadd2_rn(make_float2(z[g], z[g + 1]), make_float2(emb[g], emb[g + 1]));
+                        const __nv_bfloat162 r = __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
+                        w[h] = *reinterpret_cast<const uint32_t *>(&r);
                     }
                     *reinterpret_cast<uint4 *>(smem + G::reg + kc * G::a1_chunk + m * 16) =
                         make_uint4(w[0], w[1], w[2], w[3]);
