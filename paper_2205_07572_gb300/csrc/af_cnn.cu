@@ -9,9 +9,13 @@
 // FP32 with FP32 accumulation.  Both convolutions run on the tensor cores
 // (tcgen05.mma, BF16 operands in shared memory, FP32 accumulators in tensor
 // memory) as implicit GEMMs, one patch at a time per CTA:
-//   layer 1: D1[pixel][g] = sum_k Xim[pixel][k] W1[g][k], k = (c, ky, kx)
-//            (the patch's im2col, K = 9 C padded to 16 or 32), M = the
-//            (n+2)^2 pixels in tiles of 128, N = 32 channels;
+//   layer 1: D1[q][g] = sum_ky sum_{c,kx} Xh[q + ky (n+4)][(c, kx)] W1[g][c][ky][kx]
+//            as three accumulating GEMMs with K = 16, where Xh holds, for
+//            every flat pixel r of the input patch (row pitch n + 4), its
+//            horizontal taps X[c][r + kx] (3 C values, zero-padded): a
+//            third of an im2col's work.  Output position q = y (n+4) + x is
+//            layer-1 pixel (y, x) for x < n + 2; the others are computed and
+//            ignored.  M = (n+2)(n+4) positions in tiles of 128, N = 32;
 //   layer 2: D2[q][g] = sum_{ky,kx} sum_f A1[f][q + ky (n+2) + kx] W2[g][f][ky][kx]
 //            as nine accumulating GEMMs with K = 32 channels.  The layer-1
 //            map is stored once, pixel-major with its own row pitch n + 2,
@@ -24,7 +28,8 @@
 // The epilogues read the accumulators back (tcgen05.ld): layer 1 adds the
 // level embedding, applies relu and BF16 rounding and writes the map; layer
 // 2 adds b2 and reduces the global max-pool (value and first row-major
-// position per channel, by a butterfly exchange inside each warp).  The backward pass recomputes layer 1 the
+// position per channel, by a butterfly exchange inside each warp; without
+// the positions for inference).  The backward pass recomputes layer 1 the
 // same way, uses that the max-pool passes gradient to one pixel per channel
 // (a small fraction of the forward work), and accumulates per-CTA partial
 // gradients that a second kernel sums in a fixed order (deterministic).
@@ -103,27 +108,37 @@ __host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
 
 // Tensor-core geometry and shared-memory regions (bytes) of the two
 // convolutions for n x n patches (N = n, C components).  BWD: the backward
-// pass's layout (layer 1 only: no W2t, the region holds the im2col only).
+// pass's layout (layer 1 only: no W2t, the region holds Xh only).
+// Both layers are row-shifted GEMMs over pixel-major operands: output
+// position q = y P + x of a map with row pitch P reads input row q + ky P +
+// kx; the positions with x beyond the map's width are computed and ignored.
+//   layer 1: Xh[kc][r][kk] = X[c][r + kx] (r = y S + x, a flat pixel of the
+//            input patch; k = 8 kc + kk = 3 c + kx < 3 C, else 0), K = 16:
+//            three GEMMs (one per ky, A started ky S rows later), positions
+//            q = y S + x with y < n+2, in MT1 tiles of 128;
+//   layer 2: as described at the top of this file.
 template <int C, int N, bool BWD = false>
 struct TcGeo {
     static constexpr int S = N + 4, S1 = N + 2;
     static constexpr int P1 = S1 * S1;                // layer-1 pixels (= rows of the layer-1 map)
-    static constexpr int MT1 = (P1 + 127) / 128;      // layer-1 M tiles of 128 pixels
-    static constexpr int K1 = C * 9 <= 16 ? 16 : 32;  // layer-1 K: 9 C padded to the MMA's K step
-    static constexpr int KC1 = K1 / 8;                // 8-wide column blocks of Xim / W1t
+    static constexpr int Q1 = S1 * S;                 // layer-1 output positions y S + x, y < n+2
+    static constexpr int MT1 = (Q1 + 127) / 128;      // layer-1 M tiles
+    static constexpr int RH = MT1 * 128 + 2 * S;      // rows of Xh a layer-1 tile may read
     static constexpr int Q2 = N * S1;                 // layer-2 output positions y (n+2) + x, y < n
     static constexpr int MT2 = (Q2 + 127) / 128;      // layer-2 M tiles
     static constexpr int R1 = MT2 * 128 + 2 * S1 + 2;  // rows of the map a layer-2 tile may read (>= P1)
-    static constexpr int xim_chunk = MT1 * 128 * 16;  // Xim column block: MT1*128 rows of 16 bytes
+    static constexpr int xh_chunk = RH * 16;          // one 8-wide column block of Xh
     static constexpr int a1_chunk = R1 * 16;          // one 8-channel block of the layer-1 map
     static constexpr int xbytes = C * S * S * 2;                   // one input patch, BF16 [C][S][S]
     static constexpr int xs = 0;                                   // input patch (forward: two buffers)
-    static constexpr int w1t = align128((BWD ? 1 : 2) * xbytes);   // layer-1 B: [KC1][32 g][8 k] BF16
-    static constexpr int w2t = w1t + KC1 * 32 * 16;                // layer-2 B: [9][4][32 g][8 f] BF16
-    static constexpr int reg = w2t + (BWD ? 0 : 9 * 4 * 32 * 16);   // Xim, then (aliased) the map A1m
-    static constexpr int reg_bytes = BWD ? KC1 * xim_chunk : imax(KC1 * xim_chunk, 4 * a1_chunk);
+    static constexpr int w1t = align128((BWD ? 1 : 2) * xbytes);   // layer-1 B: [3 ky][2][32 g][8 k] BF16
+    static constexpr int w2t = w1t + 3 * 2 * 32 * 16;              // layer-2 B: [9][4][32 g][8 f] BF16
+    static constexpr int reg = w2t + (BWD ? 0 : 9 * 4 * 32 * 16);   // Xh, then (aliased) the map A1m
+    static constexpr int reg_bytes = BWD ? 2 * xh_chunk : imax(2 * xh_chunk, 4 * a1_chunk);
     static constexpr int end = reg + reg_bytes;
+    static_assert(3 * C <= 16, "the horizontal taps of every channel fit one K step of 16");
     static_assert(R1 >= P1, "the map holds every layer-1 pixel");
+    static_assert(32 * (MT1 > MT2 ? MT1 : MT2) <= 128, "the accumulators fit the tensor-memory columns");
     static_assert(xbytes % 16 == 0, "a patch is a whole number of 16-byte bulk-copy units");
 };
 constexpr int kTmemCols = 128;  // >= 32 x max(MT1, MT2) columns of FP32 accumulators
@@ -131,15 +146,16 @@ constexpr int kTmemCols = 128;  // >= 32 x max(MT1, MT2) columns of FP32 accumul
 __device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 
 // The tensor-core B operands (BF16, K-major core-matrix blocks) from the
-// FP32 parameters: W1t[kc][g][kk] = W1[g][k = 8 kc + kk] (zero for k >= 9C),
-// W2t[ky*3+kx][kc][g][kk] = W2[g][8 kc + kk][ky][kx].
+// FP32 parameters: W1t[ky][kc][g][kk] = W1[g][c][ky][kx] with 8 kc + kk =
+// 3 c + kx (zero beyond 3C), W2t[ky*3+kx][kc][g][kk] = W2[g][8 kc + kk][ky][kx].
 template <int C, int N, int NT, bool BWD>
 __device__ void tc_load_weights(const float *__restrict__ P, unsigned char *smem) {
     using G = TcGeo<C, N, BWD>;
     uint16_t *w1 = reinterpret_cast<uint16_t *>(smem + G::w1t);
-    for (int e = threadIdx.x; e < G::KC1 * 32 * 8; e += NT) {
-        const int kk = e & 7, g = (e >> 3) & 31, kc = e >> 8, k = kc * 8 + kk;
-        w1[e] = k < C * 9 ? bf16_bits(P[off_w1() + g * C * 9 + k]) : (uint16_t)0;
+    for (int e = threadIdx.x; e < 3 * 2 * 32 * 8; e += NT) {
+        const int kk = e & 7, g = (e >> 3) & 31, kc = (e >> 8) & 1, ky = e >> 9, k = kc * 8 + kk;
+        const int c = k / 3, kx = k - 3 * c;
+        w1[e] = k < 3 * C ? bf16_bits(P[off_w1() + g * C * 9 + c * 9 + ky * 3 + kx]) : (uint16_t)0;
     }
     if (BWD) return;
     uint16_t *w2 = reinterpret_cast<uint16_t *>(smem + G::w2t);
@@ -149,8 +165,8 @@ __device__ void tc_load_weights(const float *__restrict__ P, unsigned char *smem
     }
 }
 
-// Issue (one thread) layer 1's MMAs for the im2col in the Xim region and
-// commit them to *bar.
+// Issue (one thread) layer 1's MMAs (three row shifts per M tile) on Xh
+// in the tensor-core region and commit them to *bar.
 template <int C, int N, bool BWD>
 __device__ __forceinline__ void tc_issue_layer1(unsigned char *smem, uint32_t tmem, uint64_t *bar) {
     using G = TcGeo<C, N, BWD>;
@@ -159,9 +175,9 @@ __device__ __forceinline__ void tc_issue_layer1(unsigned char *smem, uint32_t tm
 #pragma unroll
     for (int mt = 0; mt < G::MT1; ++mt)
 #pragma unroll
-        for (int ks = 0; ks < G::KC1 / 2; ++ks)
-            tc::mma_bf16(tmem + 32 * mt, tc::smem_desc(a0 + ks * 2 * G::xim_chunk + mt * 128 * 16, G::xim_chunk, 128),
-                         tc::smem_desc(b0 + ks * 2 * 32 * 16, 32 * 16, 128), id, ks > 0);
+        for (int ky = 0; ky < 3; ++ky)
+            tc::mma_bf16(tmem + 32 * mt, tc::smem_desc(a0 + (mt * 128 + ky * G::S) * 16, G::xh_chunk, 128),
+                         tc::smem_desc(b0 + ky * 2 * 32 * 16, 32 * 16, 128), id, ky > 0);
     tc::mma_commit(bar);
 }
 
@@ -226,29 +242,20 @@ __device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const uint
         __syncthreads();
         xs = xw;
     }
-    // im2col, one pixel (all KC1 16-byte rows of it) per item:
-    // Xim[kc][m][kk] = X[c][y + ky][x + kx] with k = 8 kc + kk = 9 c + 3 ky + kx
-    // (zero for k >= 9 C or m >= P1), m = y S1 + x; the offsets of the nine
-    // taps are compile-time constants
-    for (int m = threadIdx.x; m < G::MT1 * 128; m += NT) {
-        const bool in = m < G::P1;
-        const int y = m / S1, x = m - y * S1;
-        const uint16_t *src = xs + (in ? y * S + x : 0);
+    // Xh, one row (both 16-byte column blocks) per item: the horizontal taps
+    // X[c][r + kx] of flat pixel r of every channel (zero beyond the patch)
+    for (int r = threadIdx.x; r < G::RH; r += NT) {
+        uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int kc = 0; kc < G::KC1; ++kc) {
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
+        for (int c = 0; c < C; ++c)
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const int k = kc * 8 + kk;
-                if (k < C * 9) {
-                    const int c = k / 9, q = k - 9 * c, ky = q / 3, kx = q - 3 * ky;
-                    const uint32_t v = in ? (uint32_t)src[(c * S + ky) * S + kx] : 0u;
-                    w[kk >> 1] |= v << (16 * (kk & 1));
-                }
+            for (int kx = 0; kx < 3; ++kx) {
+                const int k = 3 * c + kx;
+                const uint32_t v = r + kx < S * S ? (uint32_t)xs[c * S * S + r + kx] : 0u;
+                w[k >> 1] |= v << (16 * (k & 1));
             }
-            *reinterpret_cast<uint4 *>(smem + G::reg + (kc * G::MT1 * 128 + m) * 16) =
-                make_uint4(w[0], w[1], w[2], w[3]);
-        }
+        *reinterpret_cast<uint4 *>(smem + G::reg + r * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(smem + G::reg + G::xh_chunk + r * 16) = make_uint4(w[4], w[5], w[6], w[7]);
     }
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -264,8 +271,10 @@ __device__ bool tc_layer1(const __nv_bfloat16 *__restrict__ X, int b, const uint
     for (int mt = warp >> 2; mt < G::MT1; mt += NT / 128) {
         float z[32];
         tc::tmem_ld32(tmem + lanes + 32 * mt, z);
-        const int m = mt * 128 + 32 * (warp & 3) + lane;
-        if (m < G::P1) {
+        // output position q = y S + x: layer-1 pixel m = y (n+2) + x if x < n+2
+        const int q = mt * 128 + 32 * (warp & 3) + lane, y = q / S, x = q - y * S;
+        const int m = y * S1 + x;
+        if (y < S1 && x < S1) {
             if constexpr (F32OUT) {
 #pragma unroll
                 for (int g = 0; g < kF; ++g) a1[g * G::P1 + m] = rbf(fmaxf(z[g] + emb[g], 0.f));
