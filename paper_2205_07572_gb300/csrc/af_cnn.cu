@@ -223,7 +223,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity) {
     return true;
 }
 
-// Layer 1 of sample b on the tensor cores: input patch, im2col, MMAs, and
+// Layer 1 of sample b on the tensor cores: input patch, its horizontal taps (Xh), MMAs, and
 // the epilogue A1 = bf16(relu(D1 + emb[level])) written either as the BF16
 // map layer 2 reads (F32OUT false) or as an FP32 map a1[f][y][x] (F32OUT
 // true, the backward pass).  xin: the patch already in shared memory, or
