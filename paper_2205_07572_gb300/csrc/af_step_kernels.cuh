@@ -455,9 +455,9 @@ __device__ __forceinline__ void tile_nodes(const StepArgs<T> &A, const typename 
                 ST[(o * 3 + 1) * TSZ + so] = tx[o];
                 ST[(o * 3 + 2) * TSZ + so] = ty[o];
                 T *po = ob + o * kPlanes * plane;
-                if (st_x && st_y) po[kCorner * plane] = nc[o];
-                if (st_x && hx) po[kXmid * plane] = nx[o];
-                if (hy && st_y) po[kYmid * plane] = ny[o];
+                if (st_x && st_y) __stcs(po + kCorner * plane, nc[o]);
+                if (st_x && hx) __stcs(po + kXmid * plane, nx[o]);
+                if (hy && st_y) __stcs(po + kYmid * plane, ny[o]);
             }
         } else {
             const int own = rj * WX + qi;
@@ -555,7 +555,7 @@ __device__ __forceinline__ void tile_fluxes(const StepArgs<T> &A, const T *Sin, 
             // Q - dt/dx (F_r - F_l) - dt/dy (G_t - G_b), the multiply-adds
             // written out so every instantiation rounds alike
             const T q = Sin[(c * kPlanes + kAvg) * WSZ + sa];
-            ob[c * kPlanes * plane] = fma(-A.dtdy, gt[c] - gb[c], fma(-A.dtdx, fr[c] - fl[c], q));
+            __stcs(ob + c * kPlanes * plane, fma(-A.dtdy, gt[c] - gb[c], fma(-A.dtdx, fr[c] - fl[c], q)));
         }
         if (FREG) {
             // dt_l = dt0 / 2^level, scaled exactly by the power of two (no FP64
@@ -933,7 +933,7 @@ __device__ __forceinline__ void write_ghost_columns(const StepArgs<T> &A, const 
         T *o = out + (int64_t)(y0 + row + kGhost) * WX + (li + kGhost);
         const T *sp = Sin + (row + 1) * WX + (li + 1);
 #pragma unroll
-        for (int cp = 0; cp < ncp; ++cp) o[cp * plane] = sp[cp * WSZ];
+        for (int cp = 0; cp < ncp; ++cp) __stcs(o + cp * plane, sp[cp * WSZ]);
     }
 }
 
