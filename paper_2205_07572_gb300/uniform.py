@@ -86,6 +86,11 @@ class UniformRun:
                 self.step()
             return
         k = 0
+        # the graph bakes in the step's arguments: capture again if any changed
+        key = (self.dt, self.dx, self.dy, None if self.freg is None else self.freg.data_ptr(),
+               self.a.data_ptr(), self.b.data_ptr(), self.tiling)
+        if self._graph is not None and self._graph[2] != key and self._graph[2] != self._swapped(key):
+            self._graph = None
         if self._graph is None and steps >= 4:
             self.step()
             self.step()
@@ -99,9 +104,9 @@ class UniformRun:
                 self.step()
             torch.cuda.current_stream().wait_stream(side)
             self.a, self.b, self.t = a0, b0, t0  # the capture ran nothing
-            self._graph = (g, a0)
+            self._graph = (g, a0, key)
         if self._graph is not None:
-            g, a0 = self._graph
+            g, a0, _ = self._graph
             if self.a is not a0 and steps - k >= 3:
                 self.step()
                 k += 1
@@ -111,6 +116,12 @@ class UniformRun:
                 k += 2
         for _ in range(steps - k):
             self.step()
+
+    @staticmethod
+    def _swapped(key):
+        """The graph key with the two state buffers exchanged (after an odd
+        number of steps)."""
+        return key[:4] + (key[5], key[4]) + key[6:]
 
     def _band_setup(self, bands: int):
         """Work lists of `bands` bands of patch rows, and three streams."""

@@ -303,7 +303,8 @@ def test_host_state_step_matches_device_step(af, bands):
 def test_graph_replayed_steps_equal_eager_steps(af, prec, steps):
     """UniformRun.advance (pairs of steps replayed from one captured CUDA
     graph, an odd last step eagerly) gives the state of the same number of
-    step() calls bit for bit, and a second advance replays the same graph."""
+    step() calls bit for bit; a second advance replays the same graph (from
+    either buffer), and one after a change of the time step captures again."""
     from paper_2205_07572_gb300.uniform import UniformRun
     n, px = 32, 4
     grid = S.UniformGrid(S.Layout(n, 3), px, px)
@@ -316,6 +317,11 @@ def test_graph_replayed_steps_equal_eager_steps(af, prec, steps):
     graph.advance(steps)
     assert graph._graph is not None
     graph.advance(steps)
+    # a changed time step is captured again, not replayed with the old one
+    eager.dt = graph.dt = 0.3 * grid.dx
+    for _ in range(6):
+        eager.step()
+    graph.advance(6)
     torch.cuda.synchronize()
     assert abs(graph.t - eager.t) < 1e-12
     a, b = eager.state.cpu().numpy(), graph.state.cpu().numpy()
